@@ -1,0 +1,285 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+exact rational arithmetic (brute force), closed forms, integer arithmetic,
+library routines for the special cases, and the mathematics of the digit
+split.  All CPU-only."""
+from fractions import Fraction
+import math
+
+import numpy as np
+import pytest
+
+from paper_1706_10086_gb300 import inputs
+
+U = 2.0 ** -53
+
+
+def exact_gemm(alpha, A, B, beta, C):
+    """alpha*A*B + beta*C in exact rationals (no rounding anywhere)."""
+    M, K = A.shape
+    N = B.shape[1]
+    out = [[None] * N for _ in range(M)]
+    fa, fb = Fraction(alpha), Fraction(beta)
+    for i in range(M):
+        for j in range(N):
+            s = sum((Fraction(A[i, k]) * Fraction(B[k, j]) for k in range(K)), Fraction(0))
+            v = fa * s
+            if beta != 0.0:
+                v += fb * Fraction(C[i, j])
+            out[i][j] = v
+    return out
+
+
+def ulp(x: float) -> float:
+    return math.ulp(x) if x != 0 else 2.0 ** -1074
+
+
+SHAPES_TINY = [(1, 1, 1), (2, 3, 4), (3, 1, 5), (8, 8, 8), (5, 7, 3), (1, 8, 2)]
+SHAPES_RESIDUE = [(17, 3, 31), (3, 33, 16), (15, 2, 33), (33, 17, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES_TINY + SHAPES_RESIDUE)
+def test_gemm_matches_exact_rational(orc, shape):
+    """Long-double triple loop vs exact rationals: within the rounding of the
+    result plus the long-double accumulation error (never a dropped term,
+    sign flip or transposed operand, which all miss by O(1))."""
+    M, N, K = shape
+    seed = 7000 + M * 1000 + N * 10 + K
+    A, B, C = inputs.gemm_operands(seed, M, N, K)
+    alpha, beta = 1.5, 0.5
+    D = orc.gemm(alpha, A, B, beta, C)
+    E = exact_gemm(alpha, A, B, beta, C)
+    absAB = np.abs(A) @ np.abs(B)
+    eps_ld = 2.0 ** (-orc.long_double_digits() + 1)
+    for i in range(M):
+        for j in range(N):
+            ex = float(E[i][j])                # correctly rounded exact value
+            err = abs(Fraction(D[i, j]) - E[i][j])
+            budget = Fraction(ulp(ex)) / 2 + Fraction(
+                (K + 2) * eps_ld * (abs(alpha) * absAB[i, j] + abs(beta * C[i, j])))
+            assert err <= budget, (i, j, D[i, j], ex)
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 6), (16, 9, 33)])
+def test_gemm_dyadic_inputs_exact(orc, shape):
+    """Inputs with few significant bits: every operation is exact, so the
+    oracle must equal the rational result exactly."""
+    M, N, K = shape
+    A = inputs.integers(11, 0, (M, K)) / 8.0
+    B = inputs.integers(12, 0, (K, N)) / 4.0
+    C = inputs.integers(13, 0, (M, N)) / 2.0
+    D = orc.gemm(2.0, A, B, 0.5, C)
+    E = exact_gemm(2.0, A, B, 0.5, C)
+    for i in range(M):
+        for j in range(N):
+            assert Fraction(D[i, j]) == E[i][j]
+
+
+def test_integer_config_equals_int64_matmul(orc):
+    """Integer entries in {-8..8}, K = 512: every partial sum fits FP64 exactly,
+    so the result equals numpy's exact int64 matrix product."""
+    M, N, K = 48, 40, 512
+    A, B, _ = inputs.gemm_operands(inputs.workload_seed("dgemm_512"), M, N, K, kind="int",
+                                   with_c=False)
+    D = orc.gemm(1.0, A, B, 0.0)
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    assert np.array_equal(D, ref.astype(np.float64))
+
+
+def test_identity_and_permutation(orc):
+    M = 24
+    rng_perm = np.argsort(inputs.uniform(5, 0, (M,)))
+    B = inputs.uniform(6, 0, (M, 17))
+    C = inputs.uniform(7, 0, (M, 17))
+    eye = np.eye(M)
+    # A = I: C = alpha*B + beta*C (one rounding each side, long double sum exact)
+    D = orc.gemm(1.0, eye, B, 0.0, C)
+    assert np.array_equal(D, B)
+    # A = permutation: rows of B permuted, bit for bit
+    P = eye[rng_perm]
+    D = orc.gemm(1.0, P, B, 0.0)
+    assert np.array_equal(D, B[rng_perm])
+    # alpha = 2, beta = 0.5 are powers of two: exact
+    D = orc.gemm(2.0, eye, B, 0.5, C)
+    assert np.array_equal(D, 2.0 * B + 0.5 * C)
+
+
+def test_rank_one(orc):
+    """A_ik = x_i, B_kj = y_j  =>  C_ij = alpha*K*x_i*y_j + beta*C_ij (small integers: exact)."""
+    M, N, K = 9, 11, 37
+    x = inputs.integers(21, 0, (M,))
+    y = inputs.integers(22, 0, (N,))
+    A = np.repeat(x[:, None], K, axis=1)
+    B = np.repeat(y[None, :], K, axis=0)
+    C = inputs.integers(23, 0, (M, N))
+    D = orc.gemm(3.0, A, B, -2.0, C)
+    assert np.array_equal(D, 3.0 * K * np.outer(x, y) - 2.0 * C)
+
+
+def test_alpha_beta_edge_cases(orc):
+    M, N, K = 6, 5, 4
+    A, B, C = inputs.gemm_operands(31, M, N, K)
+    # B = 0: C = beta*C
+    D = orc.gemm(1.5, A, np.zeros((K, N)), 0.5, C)
+    assert np.array_equal(D, 0.5 * C)
+    # alpha = 0 reads neither A nor B: NaN there must not appear
+    An = np.full_like(A, np.nan)
+    Bn = np.full_like(B, np.nan)
+    D = orc.gemm(0.0, An, Bn, 0.5, C)
+    assert np.array_equal(D, 0.5 * C)
+    # beta = 0 reads no C
+    Cn = np.full_like(C, np.nan)
+    D = orc.gemm(1.0, A, B, 0.0, Cn)
+    assert not np.isnan(D).any()
+    # K = 0
+    D = orc.gemm(1.0, np.zeros((M, 0)), np.zeros((0, N)), 2.0, C)
+    assert np.array_equal(D, 2.0 * C)
+
+
+def test_row_sampling_matches_full(orc):
+    M, N, K = 20, 13, 21
+    A, B, C = inputs.gemm_operands(41, M, N, K)
+    full = orc.gemm(1.5, A, B, 0.5, C)
+    rows = np.array([19, 0, 7, 7])
+    part = orc.gemm(1.5, A, B, 0.5, C, rows=rows)
+    assert np.array_equal(part, full[rows])
+
+
+def test_absgemm(orc):
+    A, B, _ = inputs.gemm_operands(43, 7, 9, 12)
+    D = orc.absgemm(A, B)
+    E = exact_gemm(1.0, np.abs(A), np.abs(B), 0.0, None)
+    for i in range(7):
+        for j in range(9):
+            assert abs(Fraction(D[i, j]) - E[i][j]) <= Fraction(ulp(float(E[i][j])))
+
+
+def test_bound_holds_for_fp64_recursive_sum(orc):
+    """The acceptance bound 2 K u |alpha| (|A||B|) + u |beta C| holds for a
+    plain FP64 recursive summation (a textbook result, Higham Thm 3.1), here
+    computed with Python floats, measured against the oracle."""
+    M, N, K = 5, 6, 200
+    A, B, C = inputs.gemm_operands(47, M, N, K)
+    alpha, beta = 1.5, 0.5
+    D = orc.gemm(alpha, A, B, beta, C)
+    absAB = orc.absgemm(A, B)
+    bound = orc.error_bound(alpha, absAB, beta, C, K)
+    for i in range(M):
+        for j in range(N):
+            s = 0.0
+            for k in range(K):
+                s = s + A[i, k] * B[k, j]
+            v = alpha * s + beta * C[i, j]
+            assert abs(v - D[i, j]) <= bound[i, j]
+
+
+# ---------------------------------------------------------------------------
+# Emulated-GEMM model.
+# ---------------------------------------------------------------------------
+
+def test_row_exponents_follow_frexp(orc):
+    A = inputs.scaled(51, 0, (9, 13), phi=20)
+    A[3] = 0.0
+    A[5, 4] = 2.0 ** -1070          # subnormal row maximum is fine
+    A[5, :4] = 0.0
+    A[5, 5:] = 0.0
+    e, bad = orc.row_exponents(A)
+    assert not bad
+    for i in range(9):
+        m = np.max(np.abs(A[i]))
+        assert e[i] == (math.frexp(m)[1] if m != 0 else 0)
+        if m != 0:
+            assert 2.0 ** (e[i] - 1) <= m < 2.0 ** e[i]
+    f, bad = orc.col_exponents(A.T.copy())
+    assert np.array_equal(f, e)
+    A[2, 2] = np.inf
+    assert orc.row_exponents(A)[1]
+    A[2, 2] = np.nan
+    assert orc.row_exponents(A)[1]
+
+
+@pytest.mark.parametrize("phi", [0, 8, 32])
+def test_split_reconstructs_exactly(orc, phi):
+    """sum_p d_p 2^(-p b) + r_s 2^(-s b) = A 2^-e exactly; digit bounds; each
+    digit is the round-half-even of the exact scaled remainder."""
+    s, b = 8, orc.BF16_DIGIT_BITS
+    A = inputs.scaled(60 + phi, 0, (6, 10), phi)
+    A[0, 0] = 0.5 * 2.0 ** 3        # exact ties appear for short dyadics
+    A[0, 1] = -0.75 * 2.0 ** 3
+    e, _ = orc.row_exponents(A)
+    d, rem = orc.split(A, e, s, b)
+    for i in range(6):
+        for k in range(10):
+            r = Fraction(A[i, k]) / Fraction(2) ** int(e[i])
+            assert abs(r) < 1
+            for p in range(s):
+                x = r * 2 ** b
+                q = round(x)                      # Fraction.__round__: half to even
+                assert d[p, i, k] == q
+                assert abs(q) <= (2 ** b if p == 0 else 2 ** (b - 1))
+                r = x - q
+            assert Fraction(rem[i, k]) == r
+            recon = sum(Fraction(int(d[p, i, k])) / Fraction(2) ** (b * (p + 1)) for p in range(s))
+            recon += Fraction(rem[i, k]) / Fraction(2) ** (b * s)
+            assert recon * Fraction(2) ** int(e[i]) == Fraction(A[i, k])
+
+
+def emul_budget(alpha, beta, C, e, f, K, s, b, out):
+    """Error of the emulated GEMM against the exact product: digit truncation
+    and dropped pairs (<= 2^(e_i+f_j) K 2^(-s b) (1 + 0.26 s)), the s FP64
+    additions of the recombination (<= 1.02 (s+1) u 2^(e_i+f_j) K) and the
+    final roundings (u |out| + u |beta C|)."""
+    scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
+    t = scale * K * (2.0 ** (-s * b) * (1 + 0.26 * s) + 1.02 * (s + 1) * U) * abs(alpha)
+    return t + U * np.abs(out) + (U * np.abs(beta * C) if beta != 0 else 0.0) + 1e-300
+
+
+@pytest.mark.parametrize("s", [3, 5, 8])
+@pytest.mark.parametrize("phi", [0, 8])
+def test_emul_gemm_within_derived_bound(orc, s, phi):
+    M, N, K = 5, 4, 23
+    A, B, C = inputs.gemm_operands(70 + s + phi, M, N, K, kind="scaled", phi=phi)
+    alpha, beta = 1.5, 0.5
+    D, rc = orc.emul_gemm(alpha, A, B, beta, C, s)
+    assert rc == 0
+    E = exact_gemm(alpha, A, B, beta, C)
+    e, _ = orc.row_exponents(A)
+    f, _ = orc.col_exponents(B)
+    bud = emul_budget(alpha, beta, C, e, f, K, s, orc.BF16_DIGIT_BITS, D)
+    for i in range(M):
+        for j in range(N):
+            assert abs(Fraction(D[i, j]) - E[i][j]) <= Fraction(bud[i, j]), (i, j, s, phi)
+
+
+def test_emul_gemm_integer_inputs_bit_exact(orc):
+    """Entries in {-8..8}: one 7-bit digit holds each exactly, so any s gives
+    the exact integer product."""
+    M, N, K = 12, 10, 64
+    A, B, _ = inputs.gemm_operands(81, M, N, K, kind="int", with_c=False)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    for s in (3, 8):
+        D, rc = orc.emul_gemm(1.0, A, B, 0.0, None, s)
+        assert rc == 0 and np.array_equal(D, ref)
+
+
+def test_emul_gemm_special_cases(orc):
+    M, N, K = 4, 3, 5
+    A, B, C = inputs.gemm_operands(83, M, N, K)
+    D, rc = orc.emul_gemm(0.0, np.full_like(A, np.nan), B, 0.5, C, 4)
+    assert rc == 0 and np.array_equal(D, 0.5 * C)
+    D, rc = orc.emul_gemm(1.0, A, B, 0.0, np.full_like(C, np.nan), 4)
+    assert rc == 0 and not np.isnan(D).any()
+    A2 = A.copy()
+    A2[1, 1] = np.inf
+    _, rc = orc.emul_gemm(1.0, A2, B, 0.0, None, 4)
+    assert rc == 2
+    Z = A.copy()
+    Z[2] = 0.0                                          # zero row -> zero output row
+    D, rc = orc.emul_gemm(1.0, Z, B, 0.0, None, 4)
+    assert rc == 0 and np.all(D[2] == 0.0)
+
+
+def test_emul_gemm_rows_match_full(orc):
+    A, B, C = inputs.gemm_operands(85, 9, 7, 30, kind="scaled", phi=8)
+    full, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 6)
+    part, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 6, rows=np.array([8, 2]))
+    assert np.array_equal(part, full[[8, 2]])
