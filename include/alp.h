@@ -1,0 +1,183 @@
+/*
+ * alp.h -- C-ABI of the GB300 (sm_103a) double-precision GEMM library.
+ *
+ * The operation is the general matrix multiplication of Matthes, Widera,
+ * Zenker, Worpitz, Huebl and Bussmann, "Tuning and optimization for a variety
+ * of many-core architectures without changing a single line of implementation
+ * code using the Alpaka library" (P^3MA 2017), Eq. 1:
+ *
+ *        C = alpha * A * B + beta * C
+ *
+ * generalised from the paper's square N x N matrices (Sect. 2) to
+ *   A: M x K, row-major, leading dimension lda >= K   (element (i,k) at A[i*lda+k])
+ *   B: K x N, row-major, leading dimension ldb >= N   (element (k,j) at B[k*ldb+j])
+ *   C: M x N, row-major, leading dimension ldc >= N   (element (i,j) at C[i*ldc+j])
+ * all IEEE binary64.  The tile parameters the paper tunes (tile size T and the
+ * per-thread element block, Sect. 2.1, Listing 1, Table 4) are the fields of
+ * alp_config below.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers: A, B, C, workspaces and the batched pointer/size arrays are DEVICE
+ *   pointers owned by the caller; the library never frees them.  "h"-prefixed
+ *   arrays and alp_config / out-parameters are HOST pointers.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  GEMM calls are asynchronous and enqueue work only on `stream`.
+ * BLAS semantics (the paper does not say): beta == 0 reads no C (NaN in C does
+ *   not propagate); alpha == 0 or K == 0 reads neither A nor B and sets
+ *   C = beta*C; M == 0 or N == 0 returns ALP_OK without launching anything.
+ *   A and B must not overlap C.
+ * Errors: argument errors are returned synchronously before anything is
+ *   launched.  Faults found by a kernel (an operand with Inf/NaN on the
+ *   emulated path, a wait that timed out) are recorded in a device error word
+ *   that alp_get_device_error() reads and clears; no C++ exception crosses the
+ *   ABI and no kernel traps.
+ */
+#ifndef ALP_H
+#define ALP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum alp_status {
+    ALP_OK = 0,
+    ALP_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or config */
+    ALP_ERR_UNSUPPORTED = 2,   /* valid request this build cannot do (see each call) */
+    ALP_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    ALP_ERR_TIMEOUT = 4,       /* a device-side wait ran past its limit */
+    ALP_ERR_WORKSPACE = 5,     /* workspace NULL or smaller than the *_workspace query */
+    ALP_ERR_NOT_TUNED = 6      /* PREDICT asked for but no trained cost model loaded */
+} alp_status;
+
+typedef enum alp_slice_kind {
+    ALP_SLICE_INT8 = 0,        /* not available on sm_103a: tcgen05 has no kind::i8 there */
+    ALP_SLICE_BF16 = 1         /* digits of 7 bits held exactly in bf16 */
+} alp_slice_kind;
+
+typedef enum alp_path { ALP_PATH_NATIVE = 0, ALP_PATH_EMUL = 1 } alp_path;
+
+typedef enum alp_tune_mode {
+    ALP_TUNE_EXHAUSTIVE = 0,   /* time every valid config on the GPU, keep the fastest */
+    ALP_TUNE_PREDICT = 1,      /* argmin of the loaded cost model over valid configs */
+    ALP_TUNE_LOOKUP = 2        /* tuned-config cache only (ALP_ERR_NOT_TUNED if absent) */
+} alp_tune_mode;
+
+/*
+ * Tile configuration of the native kernel (the paper's tuning knobs, Sect. 2.1
+ * and Table 4, on a GPU re-read as one C tile per thread block):
+ *   bm, bn  C tile of one thread block, in {64, 128, 256}
+ *   bk      K step of one pipeline stage, in {16, 32, 64}
+ *   tm, tn  per-thread register tile (the element layer), in {2, 4, 8};
+ *           a warp covers (8*tm) x (4*tn) of C, the block (bm/tm)*(bn/tn) threads
+ *   stages  depth of the shared-memory ring; 0 = as many as fit (at most 4)
+ * Its shared memory per stage is (bm + bn) * bk * 8 bytes, the block version of
+ * the tile cache model K(S,T) = 2 T^2 S of Eq. 3.
+ */
+typedef struct alp_config {
+    int32_t bm, bn, bk, tm, tn, stages;
+} alp_config;
+
+/* Human-readable name of a status code (static storage). */
+const char* alp_status_string(alp_status s);
+
+/*
+ * Native FP64 GEMM, Eq. 1 (Sect. 2, Fig. 2): TMA-staged A and B tiles in a
+ * multi-stage mbarrier ring, FP64 DMMA tensor-core MMAs into per-thread
+ * register tiles, alpha/beta epilogue.  cfg == NULL selects the config from the
+ * tuned cache, else the loaded cost model, else the built-in default.
+ * Operands whose base address is not 16-byte aligned, or whose lda/ldb is odd,
+ * run through a non-TMA variant of the same kernel.
+ * Returns ALP_ERR_INVALID_ARG for negative sizes, ld < row width, NULL
+ * operands that would be read, or an invalid cfg.
+ */
+alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha,
+                        const double* A, int64_t lda, const double* B, int64_t ldb,
+                        double beta, double* C, int64_t ldc,
+                        const alp_config* cfg, void* stream);
+
+/*
+ * Emulated FP64 GEMM (not in the paper; error-free splitting after Ozaki,
+ * Ogita, Oishi and Rump 2012).  Per row i of A, e_i = frexp exponent of
+ * max_k |A_ik|; every A_ik * 2^-e_i is cut into `nslices` digits of 7 bits
+ * (round to nearest even, held exactly in bf16); likewise the columns of B
+ * with exponents f_j.  The slice products D_A^p (D_B^q)^T with p + q <=
+ * nslices + 1 run on tcgen05 tensor cores with exact integer-valued fp32
+ * partial sums (drained every 256-1024 k into int32), and are recombined in
+ * FP64 from the smallest scale up:
+ *   R = sum_{t = nslices+1 .. 2} 2^(-7t) S^t ;  C = alpha * 2^(e_i+f_j) R (+ beta*C).
+ * nslices in 3..8.  kind must be ALP_SLICE_BF16 (ALP_SLICE_INT8 returns
+ * ALP_ERR_UNSUPPORTED on sm_103a).  K <= 2^31.  Inf/NaN in A or B is reported
+ * as ALP_ERR_UNSUPPORTED through alp_get_device_error() and C is left
+ * unspecified.  workspace: device memory of at least
+ * alp_gemm_f64_emul_workspace(...) bytes, 256-byte aligned, owned by the caller.
+ */
+alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha,
+                             const double* A, int64_t lda, const double* B, int64_t ldb,
+                             double beta, double* C, int64_t ldc, int nslices,
+                             alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+/* Bytes of workspace alp_gemm_f64_emul needs (0 for invalid arguments). */
+size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind);
+
+/*
+ * Stages of the emulated GEMM, exposed for testing (same semantics as inside
+ * alp_gemm_f64_emul).  alp_emul_exponents: e[i] (int32, device) for the M rows
+ * of A (transB == 0) or f[j] for the N columns of a K x N row-major B
+ * (transB == 1, M is then N and K the row count).  alp_emul_split: digits of a
+ * row-major R x K matrix given its per-row exponents, written as bf16 to
+ * out[p][r][k] (p = 0..nslices-1, row stride kpad elements, kpad >= K, zero
+ * filled beyond K); for a K x N row-major B pass trans = 1, R = N and the
+ * result is the transposed digit matrix out[p][n][k].
+ */
+alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx,
+                              int trans, int32_t* exps, void* stream);
+alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+                          const int32_t* exps, int nslices, void* out_bf16, int64_t kpad,
+                          void* stream);
+
+/*
+ * Batched variable-size native GEMM: `count` independent problems
+ *   C_p = alpha_p * A_p * B_p + beta_p * C_p,  p = 0..count-1,
+ * all arrays (sizes, scalars, pointers, leading dims) in DEVICE memory, plus
+ * HOST copies hM, hN, hK used only to plan tile classes and grid sizes.
+ * Every tile of every problem is taken from a device work list by a persistent
+ * kernel per size class; the whole call is stream-ordered and capturable in a
+ * CUDA graph (see alp_batched_graph_*).  workspace >= alp_gemm_batched_workspace().
+ */
+alp_status alp_gemm_batched_varsize(int64_t count, const int64_t* dM, const int64_t* dN,
+                                    const int64_t* dK, const double* dalpha,
+                                    const double* const* dA, const int64_t* dlda,
+                                    const double* const* dB, const int64_t* dldb,
+                                    const double* dbeta, double* const* dC,
+                                    const int64_t* dldc, const int64_t* hM,
+                                    const int64_t* hN, const int64_t* hK, void* workspace,
+                                    size_t workspace_bytes, void* stream);
+size_t alp_gemm_batched_workspace(int64_t count, const int64_t* hM, const int64_t* hN,
+                                  const int64_t* hK);
+
+/*
+ * Autotuner (Sect. 3 "Parameter Tuning": the paper sweeps T per architecture
+ * at N = 10240 and keeps the best).  EXHAUSTIVE: times every valid config of
+ * `path` on the current GPU (10 CUDA-event-timed runs after warm-up, best
+ * kept), appends each timing to the JSONL database (env ALP_TUNE_DB, if set),
+ * and caches the winner for (M,N,K,path).  PREDICT: the cost model's argmin
+ * over valid configs (ALP_ERR_NOT_TUNED without a loaded model).  LOOKUP:
+ * cached winner only.  out: the chosen config; out_tflops: its measured (or
+ * for PREDICT, predicted) TFLOP/s, may be NULL.  Allocates its own scratch.
+ */
+alp_status alp_tune(int64_t M, int64_t N, int64_t K, alp_path path, alp_tune_mode mode,
+                    alp_config* out, double* out_tflops);
+
+/* Reads and clears the device error word (synchronises `stream`). */
+alp_status alp_get_device_error(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALP_H */

@@ -1,0 +1,245 @@
+"""Python binding of the C-ABI in ``include/alp.h`` / ``include/alp_ext.h``.
+
+Argument marshalling only: every function forwards to the ``extern "C"`` entry
+point of the same name in ``libalp.so`` (built from ``csrc/`` for sm_103a).
+Device buffers may be given as torch CUDA tensors (their ``data_ptr()`` is
+passed) or as raw integer addresses; ``stream`` is a ``torch.cuda.Stream``, a
+raw ``cudaStream_t`` integer, or None for the current torch stream.  There is
+no fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libalp.so")
+
+# alp_status
+ALP_OK = 0
+ALP_ERR_INVALID_ARG = 1
+ALP_ERR_UNSUPPORTED = 2
+ALP_ERR_CUDA = 3
+ALP_ERR_TIMEOUT = 4
+ALP_ERR_WORKSPACE = 5
+ALP_ERR_NOT_TUNED = 6
+# alp_slice_kind
+ALP_SLICE_INT8 = 0
+ALP_SLICE_BF16 = 1
+# alp_path
+ALP_PATH_NATIVE = 0
+ALP_PATH_EMUL = 1
+# alp_tune_mode
+ALP_TUNE_EXHAUSTIVE = 0
+ALP_TUNE_PREDICT = 1
+ALP_TUNE_LOOKUP = 2
+
+
+class alp_config(ctypes.Structure):
+    _fields_ = [("bm", ctypes.c_int32), ("bn", ctypes.c_int32), ("bk", ctypes.c_int32),
+                ("tm", ctypes.c_int32), ("tn", ctypes.c_int32), ("stages", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.bm, self.bn, self.bk, self.tm, self.tn, self.stages)
+
+    def __repr__(self):
+        return "alp_config(bm=%d, bn=%d, bk=%d, tm=%d, tn=%d, stages=%d)" % self.astuple()
+
+
+class AlpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_i64, _f64, _vp, _int = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+_SIGS = {
+    "alp_status_string": ([_int], ctypes.c_char_p),
+    "alp_gemm_f64": ([_i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp, _i64,
+                      ctypes.POINTER(alp_config), _vp], _int),
+    "alp_gemm_f64_emul": ([_i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp, _i64,
+                           _int, _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f64_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_emul_exponents": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
+    "alp_emul_split": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _vp, _i64, _vp], _int),
+    "alp_gemm_batched_varsize": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_batched_workspace": ([_i64, _vp, _vp, _vp], ctypes.c_size_t),
+    "alp_tune": ([_i64, _i64, _i64, _int, _int, ctypes.POINTER(alp_config),
+                  ctypes.POINTER(_f64)], _int),
+    "alp_get_device_error": ([_vp], _int),
+    "alp_config_valid": ([ctypes.POINTER(alp_config), _int], _int),
+    "alp_config_smem_bytes": ([ctypes.POINTER(alp_config)], _i64),
+    "alp_config_threads": ([ctypes.POINTER(alp_config)], _int),
+    "alp_config_count": ([_int], _int),
+    "alp_config_at": ([_int, _int, ctypes.POINTER(alp_config)], _int),
+    "alp_set_wait_timeout_ms": ([_f64], _int),
+    "alp_debug_inject_skip": ([_int], _int),
+    "alp_probe_fp64_peak": ([_int, _i64, _int, _int, ctypes.POINTER(_f64), _vp], _int),
+}
+
+
+def lib():
+    """The loaded ``libalp.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                                   "(the CUDA library is required; there is no fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of _SIGS found in the library."""
+    L = lib()
+    return [n for n in _SIGS if getattr(L, n, None) is not None]
+
+
+def _p(x):
+    """Device address of a torch tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _s(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, where: str, raise_on_error: bool):
+    if raise_on_error and status != ALP_OK:
+        raise AlpError(status, where)
+    return status
+
+
+def status_string(status: int) -> str:
+    return lib().alp_status_string(int(status)).decode()
+
+
+def alp_gemm_f64(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None, stream=None,
+                 raise_on_error=True):
+    c = None
+    if cfg is not None:
+        c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    st = lib().alp_gemm_f64(M, N, K, float(alpha), _p(A), lda, _p(B), ldb, float(beta), _p(C),
+                            ldc, ctypes.byref(c) if c is not None else None, _s(stream))
+    return _check(st, "alp_gemm_f64", raise_on_error)
+
+
+def alp_gemm_f64_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices, kind, workspace,
+                      workspace_bytes, stream=None, raise_on_error=True):
+    st = lib().alp_gemm_f64_emul(M, N, K, float(alpha), _p(A), lda, _p(B), ldb, float(beta),
+                                 _p(C), ldc, int(nslices), int(kind), _p(workspace),
+                                 int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f64_emul", raise_on_error)
+
+
+def alp_gemm_f64_emul_workspace(M, N, K, nslices, kind=ALP_SLICE_BF16):
+    return int(lib().alp_gemm_f64_emul_workspace(M, N, K, int(nslices), int(kind)))
+
+
+def alp_emul_exponents(rows, cols, X, ldx, trans, exps, stream=None, raise_on_error=True):
+    st = lib().alp_emul_exponents(rows, cols, _p(X), ldx, int(trans), _p(exps), _s(stream))
+    return _check(st, "alp_emul_exponents", raise_on_error)
+
+
+def alp_emul_split(R, K, X, ldx, trans, exps, nslices, out, kpad, stream=None,
+                   raise_on_error=True):
+    st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices), _p(out),
+                              kpad, _s(stream))
+    return _check(st, "alp_emul_split", raise_on_error)
+
+
+def alp_gemm_batched_varsize(count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC, dldc,
+                             hM, hN, hK, workspace, workspace_bytes, stream=None,
+                             raise_on_error=True):
+    st = lib().alp_gemm_batched_varsize(count, _p(dM), _p(dN), _p(dK), _p(dalpha), _p(dA),
+                                        _p(dlda), _p(dB), _p(dldb), _p(dbeta), _p(dC),
+                                        _p(dldc), _host(hM), _host(hN), _host(hK),
+                                        _p(workspace), int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_batched_varsize", raise_on_error)
+
+
+def alp_gemm_batched_workspace(count, hM, hN, hK):
+    return int(lib().alp_gemm_batched_workspace(count, _host(hM), _host(hN), _host(hK)))
+
+
+def _host(a):
+    """Host address of a contiguous int64 numpy array (kept alive by the caller)."""
+    if a is None:
+        return None
+    return a.ctypes.data
+
+
+def alp_tune(M, N, K, path=ALP_PATH_NATIVE, mode=ALP_TUNE_EXHAUSTIVE, raise_on_error=True):
+    out = alp_config()
+    tf = ctypes.c_double(0.0)
+    st = lib().alp_tune(M, N, K, int(path), int(mode), ctypes.byref(out), ctypes.byref(tf))
+    _check(st, "alp_tune", raise_on_error)
+    return st, out, tf.value
+
+
+def alp_get_device_error(stream=None):
+    return int(lib().alp_get_device_error(_s(stream)))
+
+
+def alp_config_valid(cfg, path=ALP_PATH_NATIVE) -> bool:
+    c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    return bool(lib().alp_config_valid(ctypes.byref(c), int(path)))
+
+
+def alp_config_smem_bytes(cfg) -> int:
+    c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    return int(lib().alp_config_smem_bytes(ctypes.byref(c)))
+
+
+def alp_config_threads(cfg) -> int:
+    c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    return int(lib().alp_config_threads(ctypes.byref(c)))
+
+
+def alp_config_count(path=ALP_PATH_NATIVE) -> int:
+    return int(lib().alp_config_count(int(path)))
+
+
+def alp_config_at(path, idx) -> alp_config:
+    c = alp_config()
+    st = lib().alp_config_at(int(path), int(idx), ctypes.byref(c))
+    _check(st, "alp_config_at", True)
+    return c
+
+
+def alp_set_wait_timeout_ms(ms):
+    return _check(lib().alp_set_wait_timeout_ms(float(ms)), "alp_set_wait_timeout_ms", True)
+
+
+def alp_debug_inject_skip(kt):
+    return _check(lib().alp_debug_inject_skip(int(kt)), "alp_debug_inject_skip", True)
+
+
+def alp_probe_fp64_peak(kind=0, iters=20000, blocks_per_sm=2, threads=256, stream=None):
+    """Measured FP64 TFLOP/s (kind 0: DMMA chains, 1: DFMA chains)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().alp_probe_fp64_peak(int(kind), int(iters), int(blocks_per_sm), int(threads),
+                                     ctypes.byref(out), _s(stream)), "alp_probe_fp64_peak", True)
+    return out.value

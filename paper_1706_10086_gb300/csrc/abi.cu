@@ -1,0 +1,230 @@
+// C-ABI entry points, argument validation, per-device state (error word, SM
+// count, tensor-map encoder) and config selection for alp_gemm_f64.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "alp_internal.cuh"
+#include "alp_ext.h"
+#include "native_cfg.h"
+
+namespace alp {
+
+alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t N, int64_t K,
+                         double alpha, const double* A, int64_t lda, const double* B,
+                         int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t stream,
+                         int inject_skip_kt);
+alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ldc,
+                        cudaStream_t stream);
+// tune.cu: tuned cache, then cost model, then default.
+bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out);
+
+// ----------------------------------------------------------------------------
+// Per-device state.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int* g_err_word[kMaxDevices];
+int g_sm_count[kMaxDevices];
+uint64_t g_timeout_ns = 0;
+int g_inject_skip_kt = -1;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+void init_device_locked(int d) {
+    if (d < 0 || d >= kMaxDevices || g_err_word[d]) return;
+    int* w = nullptr;
+    // One-time allocation of the 4-byte error word of this device.
+    if (cudaMalloc(&w, sizeof(int)) == cudaSuccess) {
+        cudaMemset(w, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        g_err_word[d] = w;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+    g_sm_count[d] = sms > 0 ? sms : 1;
+}
+}  // namespace
+
+int* device_error_word() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_device_locked(d);
+    return (d >= 0 && d < kMaxDevices) ? g_err_word[d] : nullptr;
+}
+
+int device_sm_count() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    init_device_locked(d);
+    return (d >= 0 && d < kMaxDevices) ? g_sm_count[d] : 1;
+}
+
+uint64_t wait_timeout_ns() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_timeout_ns == 0) {
+        double ms = 4000.0;   // default: 4 s per wait; no legitimate wait comes close
+        if (const char* s = std::getenv("ALP_WAIT_TIMEOUT_MS")) {
+            double v = std::atof(s);
+            if (v > 0) ms = v;
+        }
+        g_timeout_ns = (uint64_t)(ms * 1e6);
+    }
+    return g_timeout_ns;
+}
+
+alp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ALP_OK : ALP_ERR_CUDA; }
+
+alp_status make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, int elem_bytes,
+                        const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                        uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                 cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fn)
+                return ALP_ERR_CUDA;
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    (void)elem_bytes;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ALP_OK : ALP_ERR_UNSUPPORTED;
+}
+
+static bool default_native_config(alp_config* out) {
+    *out = alp_config{128, 128, 16, 8, 8, 0};
+    return true;
+}
+
+bool default_config(alp_path path, alp_config* out) {
+    (void)path;
+    return default_native_config(out);
+}
+
+int inject_skip_kt() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_inject_skip_kt;
+}
+
+// Shared validation of one GEMM's arguments.
+alp_status validate_gemm(int64_t M, int64_t N, int64_t K, double alpha, const void* A,
+                         int64_t lda, const void* B, int64_t ldb, double beta, const void* C,
+                         int64_t ldc) {
+    if (M < 0 || N < 0 || K < 0) return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (lda < K || ldb < N || ldc < N) return ALP_ERR_INVALID_ARG;
+    if (!C) return ALP_ERR_INVALID_ARG;
+    const bool reads_ab = (alpha != 0.0 && K > 0);
+    if (reads_ab && (!A || !B)) return ALP_ERR_INVALID_ARG;
+    if (((uintptr_t)C & 7) || (reads_ab && (((uintptr_t)A & 7) || ((uintptr_t)B & 7))))
+        return ALP_ERR_INVALID_ARG;   // doubles must be naturally aligned
+    (void)beta;
+    return ALP_OK;
+}
+
+}  // namespace alp
+
+using namespace alp;
+
+extern "C" {
+
+const char* alp_status_string(alp_status s) {
+    switch (s) {
+        case ALP_OK: return "ALP_OK";
+        case ALP_ERR_INVALID_ARG: return "ALP_ERR_INVALID_ARG: invalid argument";
+        case ALP_ERR_UNSUPPORTED: return "ALP_ERR_UNSUPPORTED: not supported by this build or input";
+        case ALP_ERR_CUDA: return "ALP_ERR_CUDA: a CUDA runtime call failed";
+        case ALP_ERR_TIMEOUT: return "ALP_ERR_TIMEOUT: a device-side wait ran past its limit";
+        case ALP_ERR_WORKSPACE: return "ALP_ERR_WORKSPACE: workspace missing or too small";
+        case ALP_ERR_NOT_TUNED: return "ALP_ERR_NOT_TUNED: no tuned config or cost model";
+    }
+    return "unknown alp_status";
+}
+
+alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                        int64_t ldc, const alp_config* cfg, void* stream) {
+    alp_status st = validate_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (st != ALP_OK || M == 0 || N == 0) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (alpha == 0.0 || K == 0) return native_scale(M, N, beta, C, ldc, s);
+    alp_config c;
+    if (cfg) {
+        c = *cfg;
+        if (!native_config_valid(c.bm, c.bn, c.bk, c.tm, c.tn, c.stages)) return ALP_ERR_INVALID_ARG;
+    } else if (!select_config(M, N, K, ALP_PATH_NATIVE, &c)) {
+        default_config(ALP_PATH_NATIVE, &c);
+    }
+    if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    // TMA wants 16-byte aligned bases and row strides that are multiples of 16 bytes.
+    const bool tma_ok = (((uintptr_t)A & 15) == 0) && (((uintptr_t)B & 15) == 0) &&
+                        (lda % 2 == 0) && (ldb % 2 == 0);
+    return native_launch(c, tma_ok, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s,
+                         inject_skip_kt());
+}
+
+alp_status alp_get_device_error(void* stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* w = device_error_word();
+    if (!w) return ALP_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return ALP_ERR_CUDA;
+    if (cudaMemsetAsync(w, 0, sizeof(int), s) != cudaSuccess) return ALP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ALP_ERR_CUDA;
+    return (alp_status)h;
+}
+
+// ---- extensions (alp_ext.h) ----
+
+int alp_config_valid(const alp_config* cfg, alp_path path) {
+    if (!cfg) return 0;
+    if (path == ALP_PATH_NATIVE)
+        return native_config_valid(cfg->bm, cfg->bn, cfg->bk, cfg->tm, cfg->tn, cfg->stages) ? 1 : 0;
+    return 0;
+}
+
+int64_t alp_config_smem_bytes(const alp_config* cfg) {
+    if (!cfg) return -1;
+    const int s = cfg->stages > 0 ? cfg->stages : native_stages(cfg->bm, cfg->bn, cfg->bk, 0);
+    return native_stage_bytes(cfg->bm, cfg->bn, cfg->bk) * s;
+}
+
+int alp_config_threads(const alp_config* cfg) {
+    if (!cfg) return -1;
+    return native_threads(cfg->bm, cfg->bn, cfg->tm, cfg->tn);
+}
+
+alp_status alp_set_wait_timeout_ms(double ms) {
+    if (!(ms > 0)) return ALP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timeout_ns = (uint64_t)(ms * 1e6);
+    return ALP_OK;
+}
+
+alp_status alp_debug_inject_skip(int kt) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_inject_skip_kt = kt;
+    return ALP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+"""The C-ABI library builds, loads and exports every symbol its headers
+declare; host-side logic (config rules, argument checks) works without a GPU."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(alp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_headers_declare_the_boundary():
+    names = declared_symbols()
+    for n in ("alp_gemm_f64", "alp_gemm_f64_emul", "alp_gemm_batched_varsize", "alp_tune",
+              "alp_get_device_error", "alp_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(alp):
+    out = subprocess.run(["nm", "-D", "--defined-only", alp.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (alp_[a-z0-9_]+)", out))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+    # and the binding knows them all
+    assert set(declared_symbols()) <= set(alp._SIGS)
+
+
+def test_status_strings(alp):
+    assert alp.status_string(alp.ALP_OK) == "ALP_OK"
+    for s in range(1, 7):
+        assert alp.status_string(s).startswith("ALP_ERR_")
+
+
+def test_table4_tile_cache_model(alp):
+    """alp_config_smem_bytes for bm = bn = bk = T and one stage is 2 T^2 * 8,
+    the DP tile cache K(S,T) of Eq. 3; every DP row printed in Table 4 matches."""
+    units = {"B": 1, "KB": 1024, "MB": 1024 ** 2}
+    n = 0
+    for line in open(os.path.join(ROOT, "tests", "golden", "table4_tile_cache.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        arch, comp, prec, S, T, val, unit = line.split()
+        S, T = int(S), int(T)
+        printed = int(val) * units[unit]
+        assert 2 * T * T * S == printed, line
+        if S == 8:
+            cfg = alp.alp_config(T, T, T, 2, 2, 1)
+            assert alp.alp_config_smem_bytes(cfg) == printed, line
+            n += 1
+    assert n == 9
+
+
+def test_config_rules(alp):
+    P = alp.ALP_PATH_NATIVE
+    n = alp.alp_config_count(P)
+    assert 20 <= n <= 243
+    seen = set()
+    for i in range(n):
+        c = alp.alp_config_at(P, i)
+        assert alp.alp_config_valid(c, P)
+        t = c.astuple()
+        assert t not in seen
+        seen.add(t)
+        bm, bn, bk, tm, tn, st = t
+        assert bm in (64, 128, 256) and bn in (64, 128, 256) and bk in (16, 32, 64)
+        assert tm in (2, 4, 8) and tn in (2, 4, 8)
+        thr = alp.alp_config_threads(c)
+        assert thr == 32 * (1 + (bm // (8 * tm)) * (bn // (4 * tn))) and thr <= 1024
+        assert alp.alp_config_smem_bytes(c) <= 227 * 1024
+        assert alp.alp_config_smem_bytes(c) >= 2 * (bm + bn) * bk * 8
+    # independent enumeration of the rule set: count the raw sweep, then filter
+    count = 0
+    for bm in (64, 128, 256):
+        for bn in (64, 128, 256):
+            for bk in (16, 32, 64):
+                for tm in (2, 4, 8):
+                    for tn in (2, 4, 8):
+                        if alp.alp_config_valid((bm, bn, bk, tm, tn, 0), P):
+                            count += 1
+    assert count == n
+    assert not alp.alp_config_valid((256, 256, 64, 8, 8, 0), P)     # one stage would not fit
+    assert not alp.alp_config_valid((64, 64, 16, 2, 2, 0), P)       # 33 warps
+    assert not alp.alp_config_valid((96, 64, 16, 4, 4, 0), P)
+    with pytest.raises(alp.AlpError):
+        alp.alp_config_at(P, n)
+
+
+def test_argument_errors_return_before_launch(alp):
+    """Invalid arguments are reported synchronously, no GPU work involved."""
+    E = alp.ALP_ERR_INVALID_ARG
+    g = lambda *a: alp.alp_gemm_f64(*a, stream=0, raise_on_error=False)
+    assert g(-1, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4) == E
+    assert g(4, 4, 4, 1.0, 8, 3, 8, 4, 0.0, 8, 4) == E           # lda < K
+    assert g(4, 4, 4, 1.0, 8, 4, 8, 3, 0.0, 8, 4) == E           # ldb < N
+    assert g(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 3) == E           # ldc < N
+    assert g(4, 4, 4, 1.0, None, 4, 8, 4, 0.0, 8, 4) == E        # A read but NULL
+    assert g(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, None, 4) == E        # C NULL
+    assert g(4, 4, 4, 1.0, 12, 4, 8, 4, 0.0, 8, 4) == E          # misaligned double
+    assert alp.alp_gemm_f64(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, cfg=(96, 64, 16, 4, 4, 0),
+                            stream=0, raise_on_error=False) == E
+    # M == 0 or N == 0: nothing to do, nothing read
+    assert g(0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == alp.ALP_OK
+    assert g(4, 0, 4, 1.0, None, 4, None, 0, 0.0, None, 0) == alp.ALP_OK
