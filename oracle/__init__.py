@@ -9,11 +9,9 @@ Contents
 * ``alp_oracle.c`` (built here with gcc): the GEMM of Eq. 1 of Matthes et al.
   2017 as a long-double triple loop, ``|A||B|`` for the error bound, and the
   emulated FP64 GEMM (exponent scan, digit split in FP64 steps, exact integer
-  slice products, FP64 recombination in a fixed order).
+  slice products, exact recombination rounded once to FP64).
 * ``mlp.py``: the tile-config cost model (forward, backward, masked MSE, Adam)
   in float64 numpy.
-* ``tune.py``: plain restatements of the tile-model formulas of the paper
-  (Eq. 2-5) and of the validity rules of a tile configuration.
 """
 from __future__ import annotations
 
@@ -58,6 +56,8 @@ def lib():
             L.orc_split.argtypes = [i64, i64, vp, i64, vp, i32, i32, vp, vp]
             L.orc_emul_gemm.argtypes = [i64, i64, i64, f64, vp, i64, vp, i64, f64, vp, i64,
                                         vp, i64, i32, i32, vp, i64, i32]
+            L.orc_int128_to_double.argtypes = [i64, ctypes.c_uint64]
+            L.orc_int128_to_double.restype = ctypes.c_double
             for fn in ("orc_gemm_f64", "orc_absgemm", "orc_row_exponents", "orc_col_exponents",
                        "orc_split", "orc_emul_gemm", "orc_long_double_digits"):
                 getattr(L, fn).restype = ctypes.c_int
@@ -163,6 +163,15 @@ def emul_gemm(alpha, A, B, beta, C, s, b=BF16_DIGIT_BITS, rows=None, nthreads=No
                              _threads(nthreads))
     assert rc in (0, 2), rc
     return D, rc
+
+
+def int128_to_double(x: int) -> float:
+    """The C oracle's conversion of a 128-bit integer to double."""
+    x &= (1 << 128) - 1
+    hi, lo = x >> 64, x & ((1 << 64) - 1)
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return lib().orc_int128_to_double(hi, lo)
 
 
 U = 2.0 ** -53

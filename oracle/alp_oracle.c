@@ -138,8 +138,13 @@ int orc_absgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
 /*  digits   for p = 1..s:  x = r_{p-1} * 2^b,  d_p = nearest integer to x   */
 /*           (ties to even),  r_p = x - d_p.  All steps are exact in FP64.   */
 /*  products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..s+1, exact integers.  */
-/*  combine  R = 0; for t = s+1 down to 2: R = R + S^t * 2^(-t b)  (FP64),   */
-/*           v = R * 2^(e_i + f_j),  out = alpha*v (+ fma(beta, C_ij, .)).   */
+/*  combine  X = sum_t S^t 2^((s+1-t) b)  exactly (an integer below 2^100),  */
+/*           v = X rounded once to the nearest double (ties to even),        */
+/*           w = v * 2^(e_i + f_j - (s+1) b)  (one rounding if subnormal),   */
+/*           out = alpha*w, then fma(beta, C_ij, out) when beta != 0.        */
+/*  So the FP64 result is the correctly rounded value of the kept digit      */
+/*  products; the only error besides the last three roundings is the digits */
+/*  that were cut off.                                                       */
 
 /* Exponent of max_k |X[i, k]| (frexp convention).  Returns 1 if an Inf or
  * NaN is present, else 0. */
@@ -229,9 +234,9 @@ static void emul_row(void* p, int64_t r) {
             d[j] = (g->beta == 0.0) ? 0.0 : g->beta * g->C[i * g->ldc + j];
             continue;
         }
-        double R = 0.0;
-        for (int t = s + 1; t >= 2; --t) {
-            int64_t S = 0;                                  /* exact */
+        __int128 X = 0;                                     /* exact */
+        for (int t = 2; t <= s + 1; ++t) {
+            int64_t S = 0;
             for (int pa = 1; pa <= s; ++pa) {
                 int qb = t - pa;
                 if (qb < 1 || qb > s) continue;
@@ -239,23 +244,24 @@ static void emul_row(void* p, int64_t r) {
                 const int32_t* bb = g->dB + ((int64_t)(qb - 1) * g->N + j) * g->K;
                 for (int64_t k = 0; k < g->K; ++k) S += (int64_t)a[k] * (int64_t)bb[k];
             }
-            R = R + ldexp((double)S, -t * b);              /* one rounding */
+            X += (__int128)S * ((__int128)1 << ((s + 1 - t) * b));
         }
-        double v = ldexp(R, g->e[i] + g->f[j]);
+        double v = ldexp((double)X, g->e[i] + g->f[j] - (s + 1) * b);   /* (double) rounds once */
         double out = g->alpha * v;
         if (g->beta != 0.0) out = fma(g->beta, g->C[i * g->ldc + j], out);
         d[j] = out;
     }
 }
 
-/* Emulated GEMM with s digits of b bits.  Returns 0, or 2 when A or B holds
- * an Inf or NaN (the emulated path does not support them), 1 on bad sizes. */
+/* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range).
+ * Returns 0, or 2 when A or B holds an Inf or NaN (the emulated path does not
+ * support them), 1 on bad sizes. */
 int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb,
                   double beta, const double* C, int64_t ldc,
                   double* D, int64_t ldd, int s, int b,
                   const int64_t* rows, int64_t nrows, int nthreads) {
-    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 24) return 1;
+    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || s * b > 90) return 1;
     int32_t* e = (int32_t*)calloc((size_t)(M > 0 ? M : 1), sizeof(int32_t));
     int32_t* f = (int32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
     int bad = orc_row_exponents(M, K, A, lda, e) | orc_col_exponents(K, N, B, ldb, f);
@@ -278,3 +284,10 @@ int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
 /* Significand bits of long double on this host (64 on x86_64, 113 on aarch64),
  * for the tests' error budget. */
 int orc_long_double_digits(void) { return LDBL_MANT_DIG; }
+
+/* Nearest double of a 128-bit integer given as hi*2^64 + lo (two's
+ * complement), for the tests' check of the conversion above. */
+double orc_int128_to_double(int64_t hi, uint64_t lo) {
+    __int128 x = ((__int128)hi << 64) | (__int128)lo;
+    return (double)x;
+}

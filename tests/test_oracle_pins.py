@@ -224,13 +224,12 @@ def test_split_reconstructs_exactly(orc, phi):
 
 
 def emul_budget(alpha, beta, C, e, f, K, s, b, out):
-    """Error of the emulated GEMM against the exact product: digit truncation
-    and dropped pairs (<= 2^(e_i+f_j) K 2^(-s b) (1 + 0.26 s)), the s FP64
-    additions of the recombination (<= 1.02 (s+1) u 2^(e_i+f_j) K) and the
-    final roundings (u |out| + u |beta C|)."""
+    """Error of the emulated GEMM against the exact product: cut-off digits and
+    dropped pairs (<= 2^(e_i+f_j) K 2^(-s b) (1 + 0.26 s)) plus the roundings
+    of the conversion, the alpha product and the beta fma (<= 3 u |out| + u |beta C|)."""
     scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
-    t = scale * K * (2.0 ** (-s * b) * (1 + 0.26 * s) + 1.02 * (s + 1) * U) * abs(alpha)
-    return t + U * np.abs(out) + (U * np.abs(beta * C) if beta != 0 else 0.0) + 1e-300
+    t = scale * K * 2.0 ** (-s * b) * (1 + 0.26 * s) * abs(alpha)
+    return t + 3 * U * np.abs(out) + (U * np.abs(beta * C) if beta != 0 else 0.0) + 1e-300
 
 
 @pytest.mark.parametrize("s", [3, 5, 8])
@@ -248,6 +247,67 @@ def test_emul_gemm_within_derived_bound(orc, s, phi):
     for i in range(M):
         for j in range(N):
             assert abs(Fraction(D[i, j]) - E[i][j]) <= Fraction(bud[i, j]), (i, j, s, phi)
+
+
+def fraction_digits(x: float, e: int, s: int, b: int):
+    """Digits of x * 2^-e by exact rational arithmetic, round half to even."""
+    r = Fraction(x) / Fraction(2) ** e
+    out = []
+    for _ in range(s):
+        y = r * 2 ** b
+        q = round(y)
+        out.append(q)
+        r = y - q
+    return out
+
+
+def fraction_emul(alpha, A, B, beta, C, s, b):
+    """The emulated GEMM evaluated independently of the C oracle: digits and
+    products in exact rationals, the kept sum rounded by Python's correctly
+    rounded int -> float, scalings with math.ldexp, the fma in rationals."""
+    M, K = A.shape
+    N = B.shape[1]
+    e = [math.frexp(float(np.max(np.abs(A[i]))))[1] if np.any(A[i]) else 0 for i in range(M)]
+    f = [math.frexp(float(np.max(np.abs(B[:, j]))))[1] if np.any(B[:, j]) else 0
+         for j in range(N)]
+    dA = [[fraction_digits(A[i, k], e[i], s, b) for k in range(K)] for i in range(M)]
+    dB = [[fraction_digits(B[k, j], f[j], s, b) for k in range(K)] for j in range(N)]
+    out = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            X = 0
+            for p in range(1, s + 1):
+                for q in range(1, s + 2 - p):
+                    X += sum(dA[i][k][p - 1] * dB[j][k][q - 1] for k in range(K)) \
+                        * 2 ** ((s + 1 - p - q) * b)
+            w = math.ldexp(float(X), e[i] + f[j] - (s + 1) * b)
+            v = alpha * w
+            if beta != 0.0:
+                v = float(Fraction(beta) * Fraction(C[i, j]) + Fraction(v))
+            out[i, j] = v
+    return out
+
+
+@pytest.mark.parametrize("s,phi", [(3, 0), (6, 8), (8, 0), (8, 32)])
+def test_emul_gemm_bit_exact_against_rationals(orc, s, phi):
+    M, N, K = 4, 3, 9
+    A, B, C = inputs.gemm_operands(90 + s + phi, M, N, K, kind="scaled", phi=phi)
+    D, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s)
+    assert rc == 0
+    ref = fraction_emul(1.5, A, B, 0.5, C, s, orc.BF16_DIGIT_BITS)
+    assert np.array_equal(D, ref)
+
+
+def test_int128_conversion_rounds_to_nearest_even(orc):
+    vals = [0, 1, -1, 2 ** 53 + 1, 2 ** 53 + 3, -(2 ** 80) - 2 ** 27, 2 ** 100 + 2 ** 47,
+            2 ** 100 + 2 ** 47 + 1, (1 << 126) - 1, -(1 << 127)]
+    x = inputs.splitmix64(5, 0, 64)
+    for i in range(0, 64, 2):
+        v = (int(x[i]) << 64) | int(x[i + 1])
+        vals.append(v >> int(x[i] % 60))
+        vals.append(-(v >> int(x[i + 1] % 60)))
+    for v in vals:
+        assert orc.int128_to_double(v) == float(v), v
 
 
 def test_emul_gemm_integer_inputs_bit_exact(orc):
