@@ -220,7 +220,8 @@ typedef struct {
     int64_t ldd;
     const int64_t* rows;
     int s, b;
-    const int32_t *dA, *dB;   /* [s][M][K], [s][N][K] */
+    const int16_t *dA, *dB;   /* [s][nrows][K] (row r of the output), [s][N][K] */
+    int64_t nra;
     const int32_t *e, *f;
 } emul_ctx;
 
@@ -240,8 +241,8 @@ static void emul_row(void* p, int64_t r) {
             for (int pa = 1; pa <= s; ++pa) {
                 int qb = t - pa;
                 if (qb < 1 || qb > s) continue;
-                const int32_t* a = g->dA + ((int64_t)(pa - 1) * g->M + i) * g->K;
-                const int32_t* bb = g->dB + ((int64_t)(qb - 1) * g->N + j) * g->K;
+                const int16_t* a = g->dA + ((int64_t)(pa - 1) * g->nra + r) * g->K;
+                const int16_t* bb = g->dB + ((int64_t)(qb - 1) * g->N + j) * g->K;
                 for (int64_t k = 0; k < g->K; ++k) S += (int64_t)a[k] * (int64_t)bb[k];
             }
             X += (__int128)S * ((__int128)1 << ((s + 1 - t) * b));
@@ -253,6 +254,26 @@ static void emul_row(void* p, int64_t r) {
     }
 }
 
+typedef struct {
+    const double* X;
+    int64_t K, ldx;
+    const int32_t* e;
+    const int64_t* rows;
+    int s, b;
+    int16_t* out;     /* [s][nrows][K] */
+    int64_t nrows;
+} split_ctx;
+
+static void split_row(void* p, int64_t r) {
+    split_ctx* c = (split_ctx*)p;
+    const int64_t i = c->rows ? c->rows[r] : r;
+    int32_t d[16];
+    for (int64_t k = 0; k < c->K; ++k) {
+        split_value(c->X[i * c->ldx + k], c->e[i], c->s, c->b, d, NULL);
+        for (int q = 0; q < c->s; ++q) c->out[((int64_t)q * c->nrows + r) * c->K + k] = (int16_t)d[q];
+    }
+}
+
 /* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range).
  * Returns 0, or 2 when A or B holds an Inf or NaN (the emulated path does not
  * support them), 1 on bad sizes. */
@@ -261,22 +282,25 @@ int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
                   double beta, const double* C, int64_t ldc,
                   double* D, int64_t ldd, int s, int b,
                   const int64_t* rows, int64_t nrows, int nthreads) {
-    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || s * b > 90) return 1;
+    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 15 || s * b > 90) return 1;
+    const int64_t nra = rows ? nrows : M;
     int32_t* e = (int32_t*)calloc((size_t)(M > 0 ? M : 1), sizeof(int32_t));
     int32_t* f = (int32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
     int bad = orc_row_exponents(M, K, A, lda, e) | orc_col_exponents(K, N, B, ldb, f);
     if (bad && alpha != 0.0) { free(e); free(f); return 2; }
-    size_t na = (size_t)s * (size_t)M * (size_t)K, nb = (size_t)s * (size_t)N * (size_t)K;
-    int32_t* dA = (int32_t*)malloc((na ? na : 1) * sizeof(int32_t));
-    int32_t* dB = (int32_t*)malloc((nb ? nb : 1) * sizeof(int32_t));
+    size_t na = (size_t)s * (size_t)nra * (size_t)K, nb = (size_t)s * (size_t)N * (size_t)K;
+    int16_t* dA = (int16_t*)malloc((na ? na : 1) * sizeof(int16_t));
+    int16_t* dB = (int16_t*)malloc((nb ? nb : 1) * sizeof(int16_t));
     size_t nt = (size_t)N * (size_t)K;
     double* Bt = (double*)malloc((nt ? nt : 1) * sizeof(double));
     for (int64_t k = 0; k < K; ++k)
         for (int64_t j = 0; j < N; ++j) Bt[j * K + k] = B[k * ldb + j];
-    orc_split(M, K, A, lda, e, s, b, dA, NULL);
-    orc_split(N, K, Bt, K, f, s, b, dB, NULL);
-    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, dA, dB, e, f};
-    for_rows(rows ? nrows : M, nthreads, emul_row, &g);
+    split_ctx sa = {A, K, lda, e, rows, s, b, dA, nra};
+    for_rows(nra, nthreads, split_row, &sa);
+    split_ctx sb = {Bt, K, K, f, NULL, s, b, dB, N};
+    for_rows(N, nthreads, split_row, &sb);
+    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, dA, dB, nra, e, f};
+    for_rows(nra, nthreads, emul_row, &g);
     free(Bt); free(dA); free(dB); free(e); free(f);
     return 0;
 }

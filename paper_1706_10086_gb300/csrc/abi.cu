@@ -110,6 +110,33 @@ alp_status make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, int elem_by
     return r == CUDA_SUCCESS ? ALP_OK : ALP_ERR_UNSUPPORTED;
 }
 
+// 3-D bf16 map (d0 innermost, contiguous rows of d0 elements, d1 rows per
+// plane), 128-byte swizzle, box {box0, box1, 1}.
+alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1,
+                             uint64_t d2, uint32_t box0, uint32_t box1) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                 cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fn)
+                return ALP_ERR_CUDA;
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+    cuuint32_t box[3] = {box0, box1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ALP_OK : ALP_ERR_UNSUPPORTED;
+}
+
 static bool default_native_config(alp_config* out) {
     *out = alp_config{128, 128, 16, 8, 8, 0};
     return true;

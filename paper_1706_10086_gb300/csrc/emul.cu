@@ -1,0 +1,387 @@
+// Emulated FP64 GEMM (error-free splitting after Ozaki, Ogita, Oishi and Rump,
+// Numer. Algorithms 59, 2012) on BF16 tensor cores:
+//
+//   1. exponent scan: e_i = frexp exponent of max_k |A_ik|, f_j of max_k |B_kj|
+//      (integer max over the IEEE bit patterns; Inf/NaN -> ALP_ERR_UNSUPPORTED);
+//   2. split: each A_ik * 2^-e_i is cut into s digits of b = 7 bits with round
+//      half to even (|d_1| <= 128, |d_p| <= 64), stored exactly as bf16,
+//      K-major for both operands (B is transposed on the way);
+//   3. slice products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..s+1, on tcgen05
+//      (emul_gemm.cu) as exact int32 per group;
+//   4. recombination: X = sum_t S^t 2^((s+1-t) b) exactly (128-bit integer),
+//      rounded once to the nearest double, scaled by 2^(e_i+f_j-(s+1)b),
+//      C = alpha * that (+ fma(beta, C, .)).
+//
+// Steps 1, 2 and 4 use integer arithmetic on the IEEE encodings and reproduce
+// the FP64 definition bit for bit (FP64 arithmetic runs at ~1.1 TFLOP/s on
+// this GPU, integer arithmetic far faster).
+#include "alp_ext.h"
+#include "alp_internal.cuh"
+#include "emul.cuh"
+
+namespace alp {
+
+alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ldc,
+                        cudaStream_t stream);
+alp_status validate_gemm(int64_t M, int64_t N, int64_t K, double alpha, const void* A,
+                         int64_t lda, const void* B, int64_t ldb, double beta, const void* C,
+                         int64_t ldc);
+
+// ---------------------------------------------------------------------------
+// 1. exponent scan
+// ---------------------------------------------------------------------------
+constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ int frexp_exponent_of_bits(uint64_t mb) {
+    if (mb == 0) return 0;
+    const int ex = (int)(mb >> 52);
+    if (ex == 0) return (63 - __clzll((long long)mb)) - 1073;   // subnormal
+    return ex - 1022;
+}
+
+// One warp per row of a row-major R x K matrix.
+__global__ void scan_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K, int64_t ldx,
+                                 int32_t* __restrict__ e, int* err) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= R) return;
+    const uint64_t* p = reinterpret_cast<const uint64_t*>(X + row * ldx);
+    uint64_t mx = 0;
+    bool bad = false;
+    for (int64_t k = lane; k < K; k += 32) {
+        const uint64_t v = __ldg(p + k) & kAbsMask;
+        if ((v >> 52) == 0x7FF) bad = true;
+        else mx = v > mx ? v : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_device_error(err, ALP_ERR_UNSUPPORTED);
+    if (lane == 0) e[row] = frexp_exponent_of_bits(mx);
+}
+
+// Columns of a row-major K x N matrix: blocks of 32 columns x (8 threads x
+// kColChunk rows).  The frexp exponent grows with |x|, so the column exponent
+// is the atomic max of the blocks' exponents; f starts at kNoExp (memset to
+// 0x80 bytes) and all-zero columns are set to 0 afterwards.
+constexpr int kColChunk = 256;
+constexpr int32_t kNoExp = (int32_t)0x80808080;
+
+__global__ void scan_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N, int64_t ldx,
+                                 int32_t* __restrict__ f, int* err) {
+    __shared__ uint64_t red[8][32];
+    const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * kColChunk;
+    const int64_t k1 = (k0 + kColChunk < K) ? k0 + kColChunk : K;
+    uint64_t mx = 0;
+    bool bad = false;
+    if (j < N) {
+        const uint64_t* p = reinterpret_cast<const uint64_t*>(X);
+        for (int64_t k = k0 + threadIdx.y; k < k1; k += 8) {
+            const uint64_t v = __ldg(p + k * ldx + j) & kAbsMask;
+            if ((v >> 52) == 0x7FF) bad = true;
+            else mx = v > mx ? v : mx;
+        }
+    }
+    red[threadIdx.y][threadIdx.x] = mx;
+    if (bad) set_device_error(err, ALP_ERR_UNSUPPORTED);
+    __syncthreads();
+    if (threadIdx.y == 0 && j < N) {
+        for (int r = 1; r < 8; ++r) mx = red[r][threadIdx.x] > mx ? red[r][threadIdx.x] : mx;
+        if (mx) atomicMax(f + j, frexp_exponent_of_bits(mx));
+    }
+}
+
+__global__ void zero_empty_columns_kernel(int64_t N, int32_t* __restrict__ f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N && f[j] == kNoExp) f[j] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// 2. split
+// ---------------------------------------------------------------------------
+// Digits of a * 2^-e.  r0 = a * 2^-e is held as a 64-bit fixed-point number
+// with 62 fraction bits, rounded to odd (truncate, then set the last bit if
+// anything was cut off): every later rounding happens at least 2 bits above
+// that last bit, so the digits equal those of the exact value (s*7 <= 56).
+// Each step is d = round-half-even(X / 2^55), X = (X - d 2^55) * 2^7, which is
+// x = r * 2^7, d = nearest integer (ties to even), r = x - d in fixed point.
+__device__ __forceinline__ void split_digits(double a, int e, int s, int (&d)[kMaxSlices]) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(a);
+    const bool neg = (bits >> 63) != 0;
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    uint64_t m = bits & ((1ull << 52) - 1);
+    int E;
+    if (ex == 0x7FF) {
+        m = 0;
+        E = 0;   // Inf/NaN: reported by the scan; digits 0
+    } else if (ex == 0) {
+        E = -1074;
+    } else {
+        m |= 1ull << 52;
+        E = ex - 1075;
+    }
+    const int sh = E - e + 62;
+    uint64_t Y;
+    if (m == 0) Y = 0;
+    else if (sh >= 0) Y = m << (sh > 63 ? 63 : sh);
+    else if (sh > -64) {
+        const int r = -sh;
+        Y = (m >> r) | ((m & ((1ull << r) - 1)) != 0 ? 1ull : 0ull);
+    } else Y = 1;   // nonzero but below 2^-62: sticky bit only
+    uint64_t X = neg ? (0ull - Y) : Y;   // two's complement of the signed value
+#pragma unroll
+    for (int p = 0; p < kMaxSlices; ++p) {
+        if (p < s) {
+            const int64_t q = ((int64_t)X) >> 55;
+            const uint64_t rem = X & ((1ull << 55) - 1);
+            const int64_t dd = q + ((rem > (1ull << 54)) || (rem == (1ull << 54) && (q & 1)) ? 1 : 0);
+            d[p] = (int)dd;
+            X = (X - ((uint64_t)dd << 55)) << 7;
+        } else {
+            d[p] = 0;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
+    // integers with |v| <= 256 are exact in bf16
+    const __nv_bfloat16 a = __int2bfloat16_rn(lo), b = __int2bfloat16_rn(hi);
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
+// thread handles two consecutive k.
+__global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K,
+                                  int64_t ldx, const int32_t* __restrict__ e, int s,
+                                  __nv_bfloat16* __restrict__ out, int64_t kpad) {
+    const int64_t half = kpad >> 1;
+    const int64_t total = R * half;
+    const int64_t plane = R * kpad;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / half;
+        const int64_t k = (idx - r * half) * 2;
+        const int er = e[r];
+        int d0[kMaxSlices], d1[kMaxSlices];
+        split_digits(k < K ? __ldg(X + r * ldx + k) : 0.0, er, s, d0);
+        split_digits(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, s, d1);
+        uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
+#pragma unroll
+        for (int p = 0; p < kMaxSlices; ++p)
+            if (p < s) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+    }
+}
+
+// B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
+// shared memory so that reads run along j and writes along k.
+__global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N,
+                                  int64_t ldx, const int32_t* __restrict__ f, int s,
+                                  __nv_bfloat16* __restrict__ out, int64_t kpad) {
+    __shared__ double t[32][65];
+    const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 warps
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int64_t k = k0 + ty + 8 * r, j = j0 + tx;
+        t[tx][ty + 8 * r] = (k < K && j < N) ? __ldg(X + k * ldx + j) : 0.0;
+    }
+    __syncthreads();
+    const int64_t plane = N * kpad;
+#pragma unroll
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int64_t j = j0 + jj;
+        if (j >= N) continue;
+        const int fj = f[j];
+        int d0[kMaxSlices], d1[kMaxSlices];
+        split_digits(t[jj][2 * tx], fj, s, d0);
+        split_digits(t[jj][2 * tx + 1], fj, s, d1);
+        const int64_t k = k0 + 2 * tx;
+        if (k >= kpad) continue;
+        uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
+#pragma unroll
+        for (int p = 0; p < kMaxSlices; ++p)
+            if (p < s) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. recombination + alpha/beta epilogue
+// ---------------------------------------------------------------------------
+// Nearest double (ties to even) of a 128-bit two's-complement integer.
+__device__ __forceinline__ double int128_to_double_rn(unsigned __int128 x) {
+    const bool neg = (x >> 127) != 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)0 - x : x;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    double v;
+    if (hi == 0) {
+        v = __ull2double_rn(lo);
+    } else {
+        const int msb = 127 - __clzll((long long)hi);
+        const int shift = msb - 52;   // >= 12
+        uint64_t m = (uint64_t)(u >> shift);
+        const unsigned __int128 rem = u & (((unsigned __int128)1 << shift) - 1);
+        const unsigned __int128 halfw = (unsigned __int128)1 << (shift - 1);
+        int ex = msb;
+        if (rem > halfw || (rem == halfw && (m & 1))) ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++ex;
+        }
+        v = __longlong_as_double((long long)(((uint64_t)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
+    }
+    return neg ? -v : v;
+}
+
+__global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, int64_t ldg,
+                                 int s, const int32_t* __restrict__ e,
+                                 const int32_t* __restrict__ f, int64_t M, int64_t N,
+                                 double alpha, double beta, double* __restrict__ C, int64_t ldc) {
+    const int64_t total = M * N;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / N, j = idx - i * N;
+        unsigned __int128 X = 0;
+        for (int t = 2; t <= s + 1; ++t) {
+            const int64_t S = __ldg(G + (int64_t)(t - 2) * gplane + i * ldg + j);
+            X += ((unsigned __int128)(__int128)S) << ((s + 1 - t) * kDigitBits);
+        }
+        const double v = int128_to_double_rn(X);
+        const double w = ldexp(v, e[i] + f[j] - (s + 1) * kDigitBits);
+        double out = alpha * w;
+        double* c = C + i * ldc + j;
+        if (beta != 0.0) out = __fma_rn(beta, *c, out);
+        *c = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s) {
+    EmulLayout L;
+    L.kpad = (K + kEmulBK - 1) / kEmulBK * kEmulBK;
+    if (L.kpad == 0) L.kpad = kEmulBK;
+    L.ldg = (N + 255) / 256 * 256;   // whole 256-column tiles per row (emul_gemm stores)
+    size_t off = 0;
+    L.off_da = off; off += up256((size_t)s * M * L.kpad * 2);
+    L.off_db = off; off += up256((size_t)s * N * L.kpad * 2);
+    L.off_g = off;  off += up256((size_t)s * M * L.ldg * 4);
+    L.off_e = off; off += up256((size_t)M * 4);
+    L.off_f = off; off += up256((size_t)N * 4);
+    L.bytes = off;
+    return L;
+}
+
+static int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+alp_status emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx, int trans,
+                          int32_t* exps, cudaStream_t st) {
+    int* err = device_error_word();
+    if (!trans) {
+        const int wpb = 8;
+        scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), 32 * wpb, 0, st>>>(X, rows, cols,
+                                                                                  ldx, exps, err);
+        return cuda_status(cudaGetLastError());
+    }
+    // trans: X is cols x rows row-major (K x N); exponents per column (rows = N)
+    const int64_t N = rows, K = cols;
+    if (cudaMemsetAsync(exps, 0x80, (size_t)N * 4, st) != cudaSuccess) return ALP_ERR_CUDA;
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + kColChunk - 1) / kColChunk));
+    if (K > 0) scan_cols_kernel<<<grid, dim3(32, 8), 0, st>>>(X, K, N, ldx, exps, err);
+    zero_empty_columns_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, exps);
+    return cuda_status(cudaGetLastError());
+}
+
+alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+                      const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
+                      cudaStream_t st) {
+    if (!trans) {
+        split_rows_kernel<<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(X, R, K, ldx, exps, s,
+                                                                        out, kpad);
+    } else {
+        dim3 grid((unsigned)((R + 31) / 32), (unsigned)(kpad / 64));
+        split_cols_kernel<<<grid, 256, 0, st>>>(X, K, R, ldx, exps, s, out, kpad);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace alp
+
+using namespace alp;
+
+extern "C" {
+
+size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind) {
+    if (M < 0 || N < 0 || K < 0 || nslices < kMinSlices || nslices > kMaxSlices ||
+        kind != ALP_SLICE_BF16)
+        return 0;
+    return emul_layout(M, N, K, nslices).bytes;
+}
+
+alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx,
+                              int trans, int32_t* exps, void* stream) {
+    if (rows < 0 || cols < 0 || !exps || (rows > 0 && cols > 0 && !X)) return ALP_ERR_INVALID_ARG;
+    if (rows == 0) return ALP_OK;
+    if (!trans && ldx < cols) return ALP_ERR_INVALID_ARG;
+    if (trans && ldx < rows) return ALP_ERR_INVALID_ARG;
+    return emul_exponents(rows, cols, X, ldx, trans, exps, reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+                          const int32_t* exps, int nslices, void* out_bf16, int64_t kpad,
+                          void* stream) {
+    if (R < 0 || K < 0 || nslices < 1 || nslices > kMaxSlices || kpad < K || kpad % 64 ||
+        !exps || !out_bf16 || (R > 0 && K > 0 && !X))
+        return ALP_ERR_INVALID_ARG;
+    if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
+    if (trans && ldx < R) return ALP_ERR_INVALID_ARG;
+    if (R == 0 || kpad == 0) return ALP_OK;
+    return emul_split(R, K, X, ldx, trans, exps, nslices,
+                      reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                             int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                             int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,
+                             size_t workspace_bytes, void* stream) {
+    alp_status st = validate_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (st != ALP_OK) return st;
+    if (nslices < kMinSlices || nslices > kMaxSlices) return ALP_ERR_INVALID_ARG;
+    if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
+    if (kind != ALP_SLICE_BF16) return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (alpha == 0.0 || K == 0) return native_scale(M, N, beta, C, ldc, s);
+    if (K > kEmulMaxK || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    const EmulLayout L = emul_layout(M, N, K, nslices);
+    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
+        return ALP_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
+    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
+    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
+    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
+    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
+    if ((st = emul_exponents(M, K, A, lda, 0, e, s)) != ALP_OK) return st;
+    if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
+    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s)) != ALP_OK) return st;
+    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s)) != ALP_OK) return st;
+    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s)) != ALP_OK) return st;
+    recombine_kernel<<<grid_for(M * N, 256), 256, 0, s>>>(G, M * L.ldg, L.ldg, nslices, e, f, M,
+                                                          N, alpha, beta, C, ldc);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Slice products of the emulated FP64 GEMM on tcgen05 tensor cores.
+//
+// One thread block per 128 x 256 tile of C.  For every digit pair (p, q) with
+// p + q = t <= s + 1 (groups t ascending, p ascending) the block multiplies the
+// bf16 digit slices D_A^p (128 x K) and D_B^q (256 x K, K-major) in K chunks:
+//
+//   warp 0      TMA producer: 128x64 A and 256x64 B tiles (128-byte swizzle)
+//               into a 4-stage shared-memory ring ("full"/"empty" mbarriers);
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 f32 accumulators)
+//               and issues tcgen05.mma kind::f16 (M=128, N=256, K=16) from one
+//               thread, committing each stage back to the producer and each
+//               finished chunk to the epilogue;
+//   warps 2-9   drain a finished chunk from TMEM (tcgen05.ld) while the other
+//               accumulator fills, and add it exactly into int32 registers.
+//
+// Exactness: digits satisfy |d_1| <= 2^7, |d_p| <= 2^6 (p >= 2), so a chunk of
+// 256 (pair 1,1), 512 (one first digit) or 1024 (no first digit) products has
+// |partial sum| <= 2^22: every partial sum is an integer that f32 holds
+// exactly.  The drain adds 1.5 * 2^23 to the f32 value, whose bit pattern then
+// is 0x4B400000 + x for |x| <= 2^22; the int32 sum of those patterns minus
+// (chunks * 0x4B400000) is the exact group sum S^t (mod 2^32 arithmetic, and
+// |S^t| < 2^31 for K <= 32768).  At the end of each group the block writes S^t
+// to G[t-2] (int32).
+#include "emul.cuh"
+#include "tc.cuh"
+
+namespace alp {
+
+alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1,
+                             uint64_t d2, uint32_t box0, uint32_t box1);
+
+namespace {
+
+constexpr int kTM = 128, kTN = 256, kTK = kEmulBK;
+constexpr int kStages = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kATile = kTM * kTK * 2;
+constexpr uint32_t kBTile = kTN * kTK * 2;
+constexpr uint32_t kStageBytes = kATile + kBTile;
+constexpr uint32_t kTmemCols = 2 * kTN;
+constexpr uint32_t kMagicBits = 0x4B400000u;   // bit pattern of 1.5 * 2^23 (see tmem_drain8_magic)
+constexpr int kMaxJobs = 2048;   // >= jobs of one tile at s = 8, K = 32768 (1696)
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/ + 4 * kMaxJobs;
+
+struct EmulGemmParams {
+    int64_t M, N, K;
+    int s;
+    int32_t* G;
+    int64_t ldg, gplane;
+    int tiles_n;
+    uint64_t timeout_ns;
+    int* err;
+};
+
+// K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^22.
+__device__ __forceinline__ int chunk_of(int p, int q) {
+    return (p == 1 && q == 1) ? 256 : (p == 1 || q == 1) ? 512 : 1024;
+}
+
+// The fixed job order of one tile: groups t = 2..s+1, pairs p ascending
+// (q = t - p), K chunks ascending.  One 32-bit word per job: first k-block
+// (bits 0..9), end k-block (10..19), p-1 (20..22), q-1 (23..25), last chunk
+// of its group (26).  Thread 0 writes the table into shared memory; every role
+// walks it.  Returns the number of jobs.
+__device__ int build_jobs(int s, int K, uint32_t* jobs) {
+    int n = 0;
+    const int kblocks = (K + kTK - 1) / kTK;
+    for (int t = 2; t <= s + 1; ++t) {
+        const int plo = (t - s > 1) ? t - s : 1, phi = (s < t - 1) ? s : t - 1;
+        for (int p = plo; p <= phi; ++p) {
+            const int q = t - p;
+            const int cb = chunk_of(p, q) / kTK;
+            for (int kb = 0; kb < kblocks; kb += cb) {
+                const int ke = (kb + cb < kblocks) ? kb + cb : kblocks;
+                const uint32_t last = (ke == kblocks && p == phi) ? 1u : 0u;
+                jobs[n++] = (uint32_t)kb | ((uint32_t)ke << 10) | ((uint32_t)(p - 1) << 20) |
+                            ((uint32_t)(q - 1) << 23) | (last << 26);
+            }
+        }
+    }
+    return n;
+}
+__device__ __forceinline__ int job_kb(uint32_t j) { return (int)(j & 1023u); }
+__device__ __forceinline__ int job_ke(uint32_t j) { return (int)((j >> 10) & 1023u); }
+__device__ __forceinline__ int job_p(uint32_t j) { return (int)((j >> 20) & 7u) + 1; }
+__device__ __forceinline__ int job_q(uint32_t j) { return (int)((j >> 23) & 7u) + 1; }
+__device__ __forceinline__ bool job_last(uint32_t j) { return (j >> 26) & 1u; }
+
+// g[0..3] = a[0..3] - bias (if do_store), then a[0..3] = 0.
+__device__ __forceinline__ void store4_sub_and_zero(int32_t* g, uint32_t bias, uint32_t do_store,
+                                                    uint32_t& a0, uint32_t& a1, uint32_t& a2,
+                                                    uint32_t& a3) {
+    asm volatile(
+        "{\n"
+        " .reg .b32 t<4>;\n .reg .pred p;\n"
+        " setp.ne.u32 p, %6, 0;\n"
+        " sub.u32 t0, %0, %5;\n sub.u32 t1, %1, %5;\n sub.u32 t2, %2, %5;\n sub.u32 t3, %3, %5;\n"
+        " @p st.global.v4.b32 [%4], {t0, t1, t2, t3};\n"
+        " mov.b32 %0, 0;\n mov.b32 %1, 0;\n mov.b32 %2, 0;\n mov.b32 %3, 0;\n"
+        "}\n"
+        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
+        : "l"(g), "r"(bias), "r"(do_store)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    emul_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
+    unsigned char* tiles = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* accf = empty + kStages;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* njobs_slot = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag + 1));
+    uint32_t* jobs = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes + 256);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kEpiWarps);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, jobs);
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int njobs = *njobs_slot;
+
+    const int m0 = (int)(blockIdx.x / prm.tiles_n) * kTM;
+    const int n0 = (int)(blockIdx.x % prm.tiles_n) * kTN;
+    const uint64_t tmo = prm.timeout_ns;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int j = 0; j < njobs && ok; ++j) {
+                const uint32_t jd = jobs[j];
+                for (int kb = job_kb(jd); kb < job_ke(jd); ++kb, ++it) {
+                    const uint32_t st = it % kStages, round = it / kStages;
+                    if (it >= (uint32_t)kStages &&
+                        !mbar_wait_bounded(&empty[st], (round - 1) & 1, tmo, abort_flag, prm.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kStageBytes);
+                    unsigned char* a = tiles + st * kStageBytes;
+                    tma_load_3d(a, &tmA, &full[st], kb * kTK, m0, job_p(jd) - 1);
+                    tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
+                }
+            }
+            // every copy issued must land before the block may exit
+            for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
+                mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = idesc_bf16_f32(kTM, kTN);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int job = 0; job < njobs && ok; ++job) {
+                const uint32_t jd = jobs[job];
+                const uint32_t b = job & 1;
+                if (job >= 2 &&
+                    !mbar_wait_bounded(&acce[b], ((job >> 1) - 1) & 1, tmo, abort_flag, prm.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + b * kTN;
+                uint32_t accumulate = 0;
+                for (int kb = job_kb(jd); kb < job_ke(jd); ++kb, ++it) {
+                    const uint32_t st = it % kStages, round = it / kStages;
+                    if (!mbar_wait_bounded(&full[st], round & 1, tmo, abort_flag, prm.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(tiles + st * kStageBytes);
+                    const uint64_t adesc = sw128_kmajor_desc(a_addr);
+                    const uint64_t bdesc = sw128_kmajor_desc(a_addr + kATile);
+#pragma unroll
+                    for (int kk = 0; kk < kTK / 16; ++kk) {
+                        // +32 bytes along K inside the 128-byte swizzled row
+                        umma_bf16(d_tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, accumulate);
+                        accumulate = 1;
+                    }
+                    umma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                umma_commit(&accf[b]);
+            }
+            // all MMAs must have completed before TMEM and shared memory go away
+            umma_commit(done);
+            mbar_wait_bounded(done, 0, tmo, nullptr, prm.err);
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> exact int32 group sums ----------------
+        const int quarter = warp & 3;          // TMEM lanes this warp may access
+        const int half = (warp - 2) >> 2;      // columns [128*half, 128*half + 128)
+        const int row = quarter * 32 + lane;
+        const int gm = m0 + row;
+        uint32_t acc[128];
+#pragma unroll
+        for (int i = 0; i < 128; ++i) acc[i] = 0;
+        uint32_t nchunks = 0;
+        int t_group = 2;
+        for (int job = 0; job < njobs; ++job) {
+            const uint32_t b = job & 1;
+            if (!mbar_wait_bounded(&accf[b], (job >> 1) & 1, tmo, abort_flag, prm.err)) break;
+            tc_fence_after();
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                tmem_drain8_magic(taddr + c * 8, acc[c * 8 + 0], acc[c * 8 + 1], acc[c * 8 + 2],
+                                  acc[c * 8 + 3], acc[c * 8 + 4], acc[c * 8 + 5], acc[c * 8 + 6],
+                                  acc[c * 8 + 7]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+            ++nchunks;
+            const uint32_t jd = jobs[job];
+            if (job_last(jd)) {
+                t_group = job_p(jd) + job_q(jd);
+                const uint32_t bias = nchunks * kMagicBits;
+                // G rows are padded to whole 256-column tiles, so the strip is in
+                // bounds; rows past M are not stored.  Each asm block stores
+                // (acc - bias) and zeroes acc in place.
+                int32_t* g = prm.G + (int64_t)(t_group - 2) * prm.gplane + (int64_t)gm * prm.ldg +
+                             n0 + half * 128;
+                const uint32_t do_store = gm < prm.M ? 1u : 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    store4_sub_and_zero(g + 4 * i, bias, do_store, acc[4 * i], acc[4 * i + 1],
+                                        acc[4 * i + 2], acc[4 * i + 3]);
+                nchunks = 0;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+}  // namespace
+
+alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
+                           const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
+                           cudaStream_t stream) {
+    {   // the job table of one tile must fit its shared-memory slot
+        const int64_t kblocks = (K + kTK - 1) / kTK;
+        int64_t njobs = 0;
+        for (int t = 2; t <= s + 1; ++t)
+            for (int pp = (t - s > 1 ? t - s : 1); pp <= (s < t - 1 ? s : t - 1); ++pp) {
+                const int qq = t - pp;
+                const int64_t cb = ((pp == 1 && qq == 1) ? 256 : (pp == 1 || qq == 1) ? 512 : 1024) / kTK;
+                njobs += (kblocks + cb - 1) / cb;
+            }
+        if (njobs > kMaxJobs || kblocks > 1023) return ALP_ERR_UNSUPPORTED;
+    }
+    CUtensorMap ta, tb;
+    alp_status st = make_tmap_3d_bf16(&ta, da, (uint64_t)kpad, (uint64_t)M, (uint64_t)s, kTK, kTM);
+    if (st != ALP_OK) return st;
+    st = make_tmap_3d_bf16(&tb, db, (uint64_t)kpad, (uint64_t)N, (uint64_t)s, kTK, kTN);
+    if (st != ALP_OK) return st;
+    EmulGemmParams p;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.s = s;
+    p.G = G;
+    p.ldg = ldg;
+    p.gplane = M * ldg;
+    const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
+    if (tiles_m * tiles_n > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
+    p.tiles_n = (int)tiles_n;
+    p.timeout_ns = wait_timeout_ns();
+    p.err = device_error_word();
+    cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    emul_gemm_kernel<<<(unsigned)(tiles_m * tiles_n), kThreads, kSmemBytes, stream>>>(ta, tb, p);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace alp

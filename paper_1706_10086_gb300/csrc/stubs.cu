@@ -3,19 +3,6 @@
 
 extern "C" {
 
-alp_status alp_gemm_f64_emul(int64_t, int64_t, int64_t, double, const double*, int64_t,
-                             const double*, int64_t, double, double*, int64_t, int,
-                             alp_slice_kind, void*, size_t, void*) {
-    return ALP_ERR_UNSUPPORTED;
-}
-size_t alp_gemm_f64_emul_workspace(int64_t, int64_t, int64_t, int, alp_slice_kind) { return 0; }
-alp_status alp_emul_exponents(int64_t, int64_t, const double*, int64_t, int, int32_t*, void*) {
-    return ALP_ERR_UNSUPPORTED;
-}
-alp_status alp_emul_split(int64_t, int64_t, const double*, int64_t, int, const int32_t*, int,
-                          void*, int64_t, void*) {
-    return ALP_ERR_UNSUPPORTED;
-}
 alp_status alp_gemm_batched_varsize(int64_t, const int64_t*, const int64_t*, const int64_t*,
                                     const double*, const double* const*, const int64_t*,
                                     const double* const*, const int64_t*, const double*,

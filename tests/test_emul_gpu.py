@@ -1,0 +1,197 @@
+"""Parity of the emulated FP64 GEMM (alp_gemm_f64_emul and its stages, through
+the C-ABI) with the oracle's emulated-GEMM model: bit-exact exponents, digits
+and results (every product and partial sum is exact and the single rounding
+is fixed), plus its error against the long-double GEMM next to the native
+path's."""
+import numpy as np
+import pytest
+
+from paper_1706_10086_gb300 import inputs
+
+from .gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run_emul(alp, A, B, C, alpha, beta, s, lda=None, ldc=None, raise_on_error=True):
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    dA, lda = dev(A, lda)
+    dB, ldb = dev(B)
+    dC, ldc = dev(C if C is not None else np.full((M, N), np.nan), ldc)
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, s, alp.ALP_SLICE_BF16)
+    work = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
+    st = alp.alp_gemm_f64_emul(M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, s,
+                               alp.ALP_SLICE_BF16, work, ws, raise_on_error=raise_on_error)
+    torch.cuda.synchronize()
+    err = alp.alp_get_device_error()
+    return dC.cpu().numpy()[:M, :N], st, err
+
+
+def test_exponents_match_oracle(alp, orc):
+    import torch
+    A = inputs.scaled(3001, 0, (300, 200), phi=32)
+    A[7] = 0.0
+    A[11] = 0.0
+    A[11, 5] = -2.0 ** -1060          # subnormal row maximum
+    A[12, 3] = 2.0 ** 1000
+    dA = torch.from_numpy(A).cuda()
+    e = torch.empty(300, dtype=torch.int32, device="cuda")
+    alp.alp_emul_exponents(300, 200, dA, 200, 0, e)
+    ref, bad = orc.row_exponents(A)
+    assert not bad and np.array_equal(e.cpu().numpy(), ref)
+    B = inputs.scaled(3002, 0, (700, 130), phi=32)     # K = 700 spans several column chunks
+    B[:, 4] = 0.0
+    B[:, 9] = 0.0
+    B[650, 9] = 2.0 ** -1070
+    dB = torch.from_numpy(B).cuda()
+    f = torch.empty(130, dtype=torch.int32, device="cuda")
+    alp.alp_emul_exponents(130, 700, dB, 130, 1, f)
+    torch.cuda.synchronize()
+    ref, bad = orc.col_exponents(B)
+    assert not bad and np.array_equal(f.cpu().numpy(), ref)
+    assert alp.alp_get_device_error() == alp.ALP_OK
+
+
+@pytest.mark.parametrize("phi", [0, 8, 32])
+def test_split_matches_oracle(alp, orc, phi):
+    import torch
+    s, R, K = 8, 70, 150
+    kpad = 192
+    X = inputs.scaled(3010 + phi, 0, (R, K), phi)
+    X[0, :8] = [0.5, -0.5, 0.75, 1.0 / 256, 3.0 / 512, -2.0 ** -9, 2.0 ** -60, 0.0]  # ties, tiny
+    X[1] = 0.0
+    e, _ = orc.row_exponents(X)
+    ref, _ = orc.split(X, e, s)
+    dX = torch.from_numpy(X).cuda()
+    de = torch.from_numpy(e).cuda()
+    out = torch.full((s, R, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(R, K, dX, K, 0, de, s, out, kpad)
+    got = out.float().cpu().numpy()
+    assert np.array_equal(got[:, :, :K], ref.astype(np.float32))
+    assert np.all(got[:, :, K:] == 0.0)
+    # transposed input: a K x R row-major matrix whose columns are split
+    XT = np.ascontiguousarray(X.T)
+    out2 = torch.full((s, R, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(R, K, torch.from_numpy(XT).cuda(), R, 1, de, s, out2, kpad)
+    got2 = out2.float().cpu().numpy()
+    assert np.array_equal(got2[:, :, :K], ref.astype(np.float32))
+    assert np.all(got2[:, :, K:] == 0.0)
+
+
+SHAPES = [(128, 256, 64), (200, 300, 130), (1, 1, 1), (257, 513, 1000), (64, 40, 2049)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("s,phi", [(3, 0), (8, 0), (8, 32), (5, 8)])
+def test_emul_bit_exact_vs_model(alp, orc, shape, s, phi):
+    M, N, K = shape
+    A, B, C = inputs.gemm_operands(3100 + M + N + K + s + phi, M, N, K, kind="scaled", phi=phi)
+    got, st, err = run_emul(alp, A, B, C, 1.5, 0.5, s)
+    assert st == alp.ALP_OK and err == alp.ALP_OK
+    ref, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s)
+    assert rc == 0
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("K", [255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 4097])
+def test_emul_chunk_boundaries(alp, orc, K):
+    """K around the drain chunks (256, 512, 1024) and the 64-wide k-blocks."""
+    M, N = 130, 260
+    A, B, _ = inputs.gemm_operands(3200 + K, M, N, K, kind="scaled", phi=4, with_c=False)
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 8)
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8)
+    assert np.array_equal(got, ref)
+
+
+def test_emul_worst_case_digits_exact(alp, orc):
+    """Entries whose digits are all at their bounds (|d_1| = 128 and |d_p| = 64
+    would need a tie, so near-maximal values): the largest partial sums the
+    chunking allows, still exact."""
+    M, N, K = 128, 256, 1024
+    A = np.full((M, K), 1.0 - 2.0 ** -53)
+    A[:, 1::2] *= -1
+    B = np.full((K, N), 1.0 - 2.0 ** -53)
+    B[1::2, :] *= -1
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 8)
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8)
+    assert np.array_equal(got, ref)
+
+
+def test_emul_integer_inputs_exact(alp, orc):
+    M = N = K = 512
+    A, B, _ = inputs.gemm_operands(inputs.workload_seed("dgemm_512"), M, N, K, kind="int",
+                                   with_c=False)
+    got, _, _ = run_emul(alp, A, B, None, 1.0, 0.0, 3)
+    assert np.array_equal(got, orc.gemm(1.0, A, B, 0.0))
+
+
+def test_emul_alpha_beta_and_padding(alp, orc):
+    M, N, K = 100, 70, 90
+    A, B, C = inputs.gemm_operands(3300, M, N, K)
+    got, _, _ = run_emul(alp, np.full_like(A, np.nan), np.full_like(B, np.nan), C, 0.0, 0.5, 6)
+    assert np.array_equal(got, 0.5 * C)
+    got, _, _ = run_emul(alp, A, B, np.full_like(C, np.nan), 1.0, 0.0, 6)
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 6)
+    assert np.array_equal(got, ref)
+    got, _, _ = run_emul(alp, A, B, C, -2.0, 0.25, 6, lda=K + 3, ldc=N + 5)
+    ref, _ = orc.emul_gemm(-2.0, A, B, 0.25, C, 6)
+    assert np.array_equal(got, ref)
+
+
+def test_emul_inf_nan_and_unsupported(alp, orc):
+    M, N, K = 64, 64, 64
+    A, B, C = inputs.gemm_operands(3400, M, N, K)
+    A[3, 4] = np.inf
+    _, st, err = run_emul(alp, A, B, C, 1.0, 0.0, 8)
+    assert st == alp.ALP_OK and err == alp.ALP_ERR_UNSUPPORTED
+    B[5, 6] = np.nan
+    A[3, 4] = 1.0
+    _, st, err = run_emul(alp, A, B, C, 1.0, 0.0, 8)
+    assert err == alp.ALP_ERR_UNSUPPORTED
+    assert alp.alp_get_device_error() == alp.ALP_OK      # read-and-clear
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_INT8,
+                                 None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_UNSUPPORTED
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 9, alp.ALP_SLICE_BF16,
+                                 None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_BF16,
+                                 None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_WORKSPACE
+
+
+def componentwise_ratio(got, ref, absAB, alpha, beta, C):
+    den = abs(alpha) * absAB + (np.abs(beta * C) if beta != 0 else 0.0)
+    return float(np.max(np.abs(got - ref) / np.maximum(den, 1e-300)))
+
+
+def test_emul_error_no_worse_than_native(alp, orc):
+    """phi = 0, s = 8: the emulated result's largest componentwise error,
+    relative to |alpha||A||B| + |beta C|, is at most the native kernel's."""
+    from .test_native_gpu import run_gemm
+    M = N = K = 1024
+    A, B, C = inputs.gemm_operands(inputs.workload_seed("emul_8192"), M, N, K, kind="scaled",
+                                   phi=0)
+    rows = np.arange(0, M, 16)
+    ref = orc.gemm(1.5, A, B, 0.5, C, rows=rows)
+    absAB = orc.absgemm(A, B, rows=rows)
+    emul, _, _ = run_emul(alp, A, B, C, 1.5, 0.5, 8)
+    nat, _ = run_gemm(alp, A, B, C, 1.5, 0.5)
+    r_emul = componentwise_ratio(emul[rows], ref, absAB, 1.5, 0.5, C[rows])
+    r_nat = componentwise_ratio(nat[rows], ref, absAB, 1.5, 0.5, C[rows])
+    assert r_emul <= r_nat, (r_emul, r_nat)
+    # and within the acceptance bound of the native path
+    bound = orc.error_bound(1.5, absAB, 0.5, C[rows], K)
+    assert np.all(np.abs(emul[rows] - ref) <= bound)
+
+
+def test_emul_full_size_sampled_rows(alp, orc):
+    """M = N = K = 8192, phi = 8, s = 8, in the bench's launch configuration:
+    sampled rows bit-exact against the model."""
+    M = N = K = 8192
+    A, B, _ = inputs.gemm_operands(inputs.workload_seed("emul_8192"), M, N, K, kind="scaled",
+                                   phi=8, with_c=False)
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 8)
+    assert err == alp.ALP_OK
+    rows = np.array([0, 4097, 8191])
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8, rows=rows)
+    assert np.array_equal(got[rows], ref)
