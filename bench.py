@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""FP64-accurate GEMM throughput on one GB300 (and N independent replicas).
+
+Workload (default): C = alpha*A*B + beta*C with M = N = K = 8192, FP64
+row-major operands u * 2^e (u uniform in [-1,1), e uniform in [-phi, phi],
+phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path with 8
+BF16 digit slices (the slice count whose error is no worse than native FP64).
+One step = one full emulated GEMM: exponent scans, digit splits, the
+tensor-core slice products and the exact recombination -- the same kernels
+alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
+bracket the tensor-core kernel.  Inputs (1.5 GB) are larger than L2, so no
+flush is needed between steps.  The native DMMA path is measured on the same
+matrices in the same run (its own object), as is the end-to-end call with
+host buffers and the CPU oracle on a bounded sample of rows.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl alp|reference]
+
+Under torchrun (N > 1) every rank runs the same replica on its own GPU
+(the paths share nothing across GPUs); the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64-accurate GEMM TFLOP/s (native vs emulated) and % of peak at N=8192"
+UNIT = "TFLOP/s"
+KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_gb300/csrc/tc.cuh",
+                  "paper_1706_10086_gb300/csrc/emul.cuh")
+TRAFFIC_PROFILE = "profiles/emul_gemm_kernel_8192.md"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--nslices", type=int, default=8)
+    ap.add_argument("--phi", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-native", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (no API check, native, e2e or CPU legs): for ncu")
+    a = ap.parse_args()
+    if a.profile:
+        a.no_native = a.no_e2e = a.no_cpu = True
+    return a
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_sample(A_rows, B, alpha, target_s):
+    """Times the long-double oracle on a bounded number of rows of the product
+    (all host cores).  Returns (TFLOP/s, rows, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n_threads = os.cpu_count() or 1
+    K = B.shape[0]
+    N = B.shape[1]
+    probe = min(len(A_rows), max(2, n_threads // 4))
+    t0 = time.perf_counter()
+    oracle.gemm(alpha, A_rows[:probe], B, 0.0, nthreads=n_threads)
+    dt = time.perf_counter() - t0
+    rows = int(max(1, min(len(A_rows), probe * target_s / max(dt, 1e-3))))
+    rows = max(n_threads, rows // n_threads * n_threads) if rows >= n_threads else rows
+    rows = min(rows, len(A_rows))
+    t0 = time.perf_counter()
+    oracle.gemm(alpha, A_rows[:rows], B, 0.0, nthreads=n_threads)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows * N * K
+    return flops / dt / 1e12, rows, dt, n_threads
+
+
+def make_inputs(torch, n, phi, seed, device):
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+
+    def mat():
+        u = torch.rand(n, n, dtype=torch.float64, device=device, generator=g) * 2 - 1
+        if phi == 0:
+            return u
+        e = torch.randint(-phi, phi + 1, (n, n), device=device, generator=g,
+                          dtype=torch.int32).to(torch.float64)
+        return torch.ldexp(u, e)
+    return mat(), mat()
+
+
+def run_alp(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1706_10086_gb300 import alp
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    n, s, phi = args.n, args.nslices, args.phi
+    M = N = K = n
+    seed = 1706 + 2
+    A, B = make_inputs(torch, n, phi, seed, dev)
+    C = torch.empty(n, n, dtype=torch.float64, device=dev)
+    alpha, beta = 1.0, 0.0
+    stream = torch.cuda.current_stream(dev)
+    # workspace carved exactly as alp_gemm_f64_emul does
+    kpad = (K + 63) // 64 * 64
+    ldg = (N + 255) // 256 * 256
+    da = torch.empty(s * M * kpad, dtype=torch.bfloat16, device=dev)
+    db = torch.empty(s * N * kpad, dtype=torch.bfloat16, device=dev)
+    G = torch.empty(s * M * ldg, dtype=torch.int32, device=dev)
+    e = torch.empty(M, dtype=torch.int32, device=dev)
+    f = torch.empty(N, dtype=torch.int32, device=dev)
+    launches_per_step = 7   # scan rows, scan cols (2), split A, split B, slice products, recombine
+
+    def step(ev_k0=None, ev_k1=None):
+        alp.alp_emul_exponents(M, K, A, K, 0, e, stream)
+        alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
+        alp.alp_emul_split(M, K, A, K, 0, e, s, da, kpad, stream)
+        alp.alp_emul_split(N, K, B, N, 1, f, s, db, kpad, stream)
+        if ev_k0 is not None:
+            ev_k0.record(stream)
+        alp.alp_emul_slice_products(M, N, K, s, da, db, kpad, G, ldg, stream)
+        if ev_k1 is not None:
+            ev_k1.record(stream)
+        alp.alp_emul_recombine(M, N, s, G, ldg, e, f, alpha, beta, C, N, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error(stream) == alp.ALP_OK
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(ev[i][1], ev[i][2])
+        ev[i][3].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [ev[i][0].elapsed_time(ev[i][3]) for i in range(args.steps)]
+    kern_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    assert alp.alp_get_device_error(stream) == alp.ALP_OK
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    flops_step = 2.0 * M * N * K
+    value = ws * args.steps * flops_step / (total_ms * 1e-3) / 1e12
+    pairs = s * (s + 1) // 2
+    kern_avg = statistics.mean(kern_ms)
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = pairs * 2.0 * M * N * K / (kern_avg * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "kernel": "emul_gemm_kernel (tcgen05 bf16 slice products)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
+                "algorithmic_flops_per_launch": pairs * 2.0 * M * N * K,
+                "kernel_ms": round(kern_avg, 3),
+                "traffic": profiled_traffic()}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic (seeded torch generator on the GPU; u*2^e, u~U[-1,1), e~U{-phi..phi})",
+           "config": {"workload": f"emulated_dgemm_{n}_bf16x{s}slices_phi{phi}", "M": M, "N": N,
+                      "K": K, "nslices": s, "phi": phi, "alpha": alpha, "beta": beta,
+                      "result_dtype": "f64", "parallelism": f"replicas{ws}",
+                      "l2": "inputs 1.5 GB > 129 MB L2; no flush"},
+           "step_ms_median": round(statistics.median(step_ms), 3),
+           "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
+           "clocks": clk}
+
+    if args.profile:
+        print(json.dumps(out), flush=True)
+        return
+    # public single-call API on the same device buffers (same kernels, one call)
+    wsb = alp.alp_gemm_f64_emul_workspace(M, N, K, s, alp.ALP_SLICE_BF16)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, alp.ALP_SLICE_BF16, work,
+                          wsb, stream)
+    e0.record(stream)
+    for _ in range(3):
+        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, alp.ALP_SLICE_BF16,
+                              work, wsb, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["api_call_ms"] = round(e0.elapsed_time(e1) / 3, 3)
+    del da, db, G
+
+    if not args.no_e2e:
+        # end to end through the public call with host buffers: H2D of A and B
+        # from pinned memory, the call, D2H of C, all inside the timed region
+        hA = A.cpu().pin_memory()
+        hB = B.cpu().pin_memory()
+        hC = torch.empty(n, n, dtype=torch.float64).pin_memory()
+        dA = torch.empty_like(A)
+        dB = torch.empty_like(B)
+        dC = torch.empty_like(C)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            alp.alp_gemm_f64_emul(M, N, K, alpha, dA, K, dB, N, beta, dC, N, s,
+                                  alp.ALP_SLICE_BF16, work, wsb, stream)
+            hC.copy_(dC, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        ksteps = max(2, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / ksteps
+        out["e2e"] = {"value": round(flops_step / (e2e_ms * 1e-3) / 1e12, 3), "unit": UNIT,
+                      "ms_per_step": round(e2e_ms, 3),
+                      "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+                      "d2h_bytes_per_step": int(hC.numel() * 8)}
+        del dA, dB, dC
+
+    if not args.no_native:
+        # native DMMA path, alpha = 1.5, beta = 0.5 on the same operands
+        C2 = torch.rand(n, n, dtype=torch.float64, device=dev) * 2 - 1
+        alp.alp_gemm_f64(M, N, K, 1.5, A, K, B, N, 0.5, C2, N, stream=stream)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            alp.alp_gemm_f64(M, N, K, 1.5, A, K, B, N, 0.5, C2, N, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nat_ms = e0.elapsed_time(e1) / reps
+        nat_tf = flops_step / (nat_ms * 1e-3) / 1e12
+        fp64_peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
+        out["native"] = {"tflops": round(nat_tf, 4), "ms": round(nat_ms, 2),
+                         "roofline": {"bound": "fp64_dmma", "achieved": round(nat_tf, 4),
+                                      "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                                      "frac": round(nat_tf / fp64_peak, 4),
+                                      "peak_source": "alp_probe_fp64_peak (DMMA chains on all "
+                                                     "SMs, measured in this run)"},
+                         "emulated_speedup": round(value / ws / nat_tf, 2)}
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        # CPU baseline: the long-double oracle on a bounded sample of rows
+        rows = 64
+        A_rows = A[:rows].cpu().numpy()
+        Bh = B.cpu().numpy()
+        tf, r, dt, thr = cpu_oracle_sample(A_rows, Bh, alpha, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": tf, "unit": UNIT, "cores": thr, "kind": "oracle",
+                               "sample": f"{r} of {M} rows of the {n}^3 product "
+                                         f"(long-double triple loop, {dt:.1f} s, "
+                                         f"{os.cpu_count()} host cores)"}
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: K timed steps, each a bounded
+    sample of rows of the same 8192^3 product, on the host cores."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1706_10086_gb300 import inputs
+    oracle.build()
+    n = args.n
+    thr = os.cpu_count() or 1
+    seed = inputs.workload_seed("emul_8192")
+    B = inputs.uniform(seed, n * n, (n, n))
+    rows_per_step = max(1, thr // 2)
+    A_rows = inputs.uniform(seed, 0, (rows_per_step, n))
+    for _ in range(max(1, args.warmup)):
+        oracle.gemm(1.0, A_rows[:1], B, 0.0, nthreads=thr)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gemm(1.0, A_rows, B, 0.0, nthreads=thr)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows_per_step * n * n * args.steps
+    v = flops / dt / 1e12
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double accumulation)",
+           "data": "synthetic (seeded SplitMix64, uniform [-1,1))",
+           "config": {"workload": f"emulated_dgemm_{n}_bf16x8slices_phi0", "M": n, "N": n,
+                      "K": n, "sample_rows_per_step": rows_per_step},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                            "sample": f"{rows_per_step} rows of the {n}^3 product per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_alp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -66,6 +66,9 @@ _SIGS = {
     "alp_gemm_f64_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
     "alp_emul_exponents": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
     "alp_emul_split": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _vp, _i64, _vp], _int),
+    "alp_emul_slice_products": ([_i64, _i64, _i64, _int, _vp, _vp, _i64, _vp, _i64, _vp], _int),
+    "alp_emul_recombine": ([_i64, _i64, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64, _vp],
+                           _int),
     "alp_gemm_batched_varsize": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_batched_workspace": ([_i64, _vp, _vp, _vp], ctypes.c_size_t),
@@ -168,6 +171,20 @@ def alp_emul_split(R, K, X, ldx, trans, exps, nslices, out, kpad, stream=None,
     st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices), _p(out),
                               kpad, _s(stream))
     return _check(st, "alp_emul_split", raise_on_error)
+
+
+def alp_emul_slice_products(M, N, K, nslices, da, db, kpad, G, ldg, stream=None,
+                            raise_on_error=True):
+    st = lib().alp_emul_slice_products(M, N, K, int(nslices), _p(da), _p(db), kpad, _p(G), ldg,
+                                       _s(stream))
+    return _check(st, "alp_emul_slice_products", raise_on_error)
+
+
+def alp_emul_recombine(M, N, nslices, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
+                       raise_on_error=True):
+    st = lib().alp_emul_recombine(M, N, int(nslices), _p(G), ldg, _p(e), _p(f), float(alpha),
+                                  float(beta), _p(C), ldc, _s(stream))
+    return _check(st, "alp_emul_recombine", raise_on_error)
 
 
 def alp_gemm_batched_varsize(count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC, dldc,

@@ -352,6 +352,31 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
+alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
+                                   const void* da_bf16, const void* db_bf16, int64_t kpad,
+                                   int32_t* G, int64_t ldg, void* stream) {
+    if (M < 0 || N < 0 || K < 0 || nslices < 1 || nslices > kMaxSlices || kpad < K ||
+        kpad % kEmulBK || ldg < N || ldg % 256 || K > kEmulMaxK)
+        return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0 || K == 0) return ALP_OK;
+    if (!da_bf16 || !db_bf16 || !G) return ALP_ERR_INVALID_ARG;
+    return emul_slice_gemm(M, N, K, nslices, reinterpret_cast<const __nv_bfloat16*>(da_bf16),
+                           reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, G, ldg,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, const int32_t* G, int64_t ldg,
+                              const int32_t* e, const int32_t* f, double alpha, double beta,
+                              double* C, int64_t ldc, void* stream) {
+    if (M < 0 || N < 0 || nslices < 1 || nslices > kMaxSlices || ldg < N || ldc < N)
+        return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
+    recombine_kernel<<<grid_for(M * N, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        G, M * ldg, ldg, nslices, e, f, M, N, alpha, beta, C, ldc);
+    return cuda_status(cudaGetLastError());
+}
+
 alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                              int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                              int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,

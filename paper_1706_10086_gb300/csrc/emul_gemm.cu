@@ -21,6 +21,8 @@
 // (chunks * 0x4B400000) is the exact group sum S^t (mod 2^32 arithmetic, and
 // |S^t| < 2^31 for K <= 32768).  At the end of each group the block writes S^t
 // to G[t-2] (int32).
+#include <cstdlib>
+
 #include "emul.cuh"
 #include "tc.cuh"
 
@@ -28,6 +30,20 @@ namespace alp {
 
 alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1,
                              uint64_t d2, uint32_t box0, uint32_t box1);
+
+// Tile-rows per raster group (env ALP_EMUL_GROUP_M overrides; default 8, the
+// fastest of {1, 4, 8, 16, 32, 64} at 8192^3 on GB300).
+static int emul_group_m() {
+    static int g = 0;
+    if (g == 0) {
+        g = 8;
+        if (const char* s = std::getenv("ALP_EMUL_GROUP_M")) {
+            const int v = std::atoi(s);
+            if (v >= 1 && v <= 4096) g = v;
+        }
+    }
+    return g;
+}
 
 namespace {
 
@@ -48,7 +64,7 @@ struct EmulGemmParams {
     int s;
     int32_t* G;
     int64_t ldg, gplane;
-    int tiles_n;
+    int tiles_m, tiles_n, group_m;
     uint64_t timeout_ns;
     int* err;
 };
@@ -146,8 +162,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
     const int njobs = *njobs_slot;
 
-    const int m0 = (int)(blockIdx.x / prm.tiles_n) * kTM;
-    const int n0 = (int)(blockIdx.x % prm.tiles_n) * kTN;
+    // grouped raster: blocks run down group_m tile-rows before moving one
+    // tile-column right, so a wave of blocks shares a compact set of A and B
+    // digit panels in L2
+    int m0, n0;
+    {
+        const int pid = (int)blockIdx.x, in_group = prm.group_m * prm.tiles_n;
+        const int first_m = (pid / in_group) * prm.group_m;
+        const int gsz = min(prm.tiles_m - first_m, prm.group_m);
+        const int local = pid % in_group;
+        m0 = (first_m + local % gsz) * kTM;
+        n0 = (local / gsz) * kTN;
+    }
     const uint64_t tmo = prm.timeout_ns;
 
     if (warp == 0) {
@@ -302,7 +328,9 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.gplane = M * ldg;
     const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
     if (tiles_m * tiles_n > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
+    p.tiles_m = (int)tiles_m;
     p.tiles_n = (int)tiles_n;
+    p.group_m = emul_group_m();
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
     cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel,
