@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--no-native", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", choices=("emul8192", "batched"), default="emul8192",
+                    help="emul8192 (default, the headline) or batched (4096 variable-size "
+                         "problems, persistent graph launch vs a loop of launches)")
+    ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no API check, native, e2e or CPU legs): for ncu")
     a = ap.parse_args()
@@ -420,10 +424,106 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """4096 independent problems, M, N, K log-uniform in [16, 1024], alpha =
+    1.5, beta = 0.5: one replay of the persistent batched CUDA graph per step,
+    against a loop of single-problem launches (plain, and captured in a graph)."""
+    import numpy as np
+    import torch
+
+    from paper_1706_10086_gb300 import alp, inputs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    shapes = inputs.shapes(inputs.workload_seed("batched_4096"), args.count, 16, 1024)
+    M, N, K = (np.ascontiguousarray(shapes[:, i]) for i in range(3))
+    sizeA, sizeB, sizeC = M * K, K * N, M * N
+    pad = lambda x: (x + 1) // 2 * 2            # 16-byte aligned starts
+    offA = np.concatenate([[0], np.cumsum(pad(sizeA))])
+    offB = np.concatenate([[0], np.cumsum(pad(sizeB))])
+    offC = np.concatenate([[0], np.cumsum(pad(sizeC))])
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.workload_seed("batched_4096"))
+    bufA = torch.rand(int(offA[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+    bufB = torch.rand(int(offB[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+    bufC = torch.rand(int(offC[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+    bufC0 = bufC.clone()
+    pA = bufA.data_ptr() + 8 * offA[:-1]
+    pB = bufB.data_ptr() + 8 * offB[:-1]
+    pC = bufC.data_ptr() + 8 * offC[:-1]
+    t = lambda a, dt=torch.int64: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    n = args.count
+    dM, dN, dK = t(M), t(N), t(K)
+    dal, dbe = t(np.full(n, 1.5), torch.float64), t(np.full(n, 0.5), torch.float64)
+    dA, dB, dC = t(pA), t(pB), t(pC)
+    dlda, dldb, dldc = t(K), t(N), t(N)
+    flops = float(np.sum(2.0 * M * N * K))
+    ws = alp.alp_gemm_batched_workspace(n, M, N, K)
+    work = torch.empty(ws, dtype=torch.uint8, device=dev)
+    graph = alp.alp_batched_graph_create(n, dM, dN, dK, dal, dA, dlda, dB, dldb, dbe, dC, dldc,
+                                         M, N, K, work, ws)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_graph = timed(lambda: alp.alp_batched_graph_launch(graph, stream), args.steps,
+                     max(3, args.warmup))
+    clk = clocks.stop()
+
+    def loop(st=stream):
+        for p in range(n):
+            alp.alp_gemm_f64(int(M[p]), int(N[p]), int(K[p]), 1.5, int(pA[p]), int(K[p]),
+                             int(pB[p]), int(N[p]), 0.5, int(pC[p]), int(N[p]), stream=st)
+    ms_loop = timed(loop, max(1, args.steps // 2), 1)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    gl = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gl, stream=side):
+        loop(side)
+    stream.wait_stream(side)
+    ms_loop_graph = timed(gl.replay, max(1, args.steps // 2), 1)
+    alp.alp_batched_graph_destroy(graph)
+    fp64_peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
+    value = flops / (ms_graph * 1e-3) / 1e12
+    out = {"metric": "batched FP64 GEMM TFLOP/s", "value": round(value, 4), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": round(ms_graph, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded: sizes SplitMix64 log-uniform, entries torch generator)",
+           "config": {"workload": f"batched_dgemm_{n}_loguniform_16_1024", "count": n,
+                      "flops_per_step": flops, "alpha": 1.5, "beta": 0.5,
+                      "l2": "operands 4.6 GB > L2; no flush"},
+           "roofline": {"bound": "fp64_dmma", "achieved": round(value, 4),
+                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                        "frac": round(value / fp64_peak, 4),
+                        "peak_source": "alp_probe_fp64_peak (measured in this run)"},
+           "loop_of_launches": {"ms": round(ms_loop, 3),
+                                "tflops": round(flops / (ms_loop * 1e-3) / 1e12, 4)},
+           "loop_of_launches_graph": {"ms": round(ms_loop_graph, 3),
+                                      "tflops": round(flops / (ms_loop_graph * 1e-3) / 1e12, 4)},
+           "speedup_vs_loop": round(ms_loop / ms_graph, 3),
+           "speedup_vs_loop_graph": round(ms_loop_graph / ms_graph, 3),
+           "gpu_launches": 2 * args.steps, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_alp(args)
 

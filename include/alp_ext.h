@@ -47,6 +47,89 @@ alp_status alp_set_wait_timeout_ms(double ms);
  * kernel returns.  kt = -1 switches it off.  No copy is left in flight. */
 alp_status alp_debug_inject_skip(int kt);
 
+/* ---- autotuner helpers --------------------------------------------------- */
+
+/* Time of one config for (M, N, K) on `path`, in ms: the best of `runs`
+ * CUDA-event-timed launches after one warm-up.  use_proxy = 1 times one wave
+ * of blocks with K capped at 256 and scales by the waves and by K / 256 (the
+ * estimate alp_tune records); use_proxy = 0 times the whole problem.  For the
+ * emulated path the tensor-core stage is timed.  Allocates its own scratch. */
+alp_status alp_tune_time_config(int64_t M, int64_t N, int64_t K, alp_path path,
+                                const alp_config* cfg, int use_proxy, int runs, double* est_ms);
+/* Puts cfg into the tuned cache for (M, N, K, path) (what alp_tune(EXHAUSTIVE)
+ * does with its winner), and empties the cache. */
+alp_status alp_tune_set_cached(int64_t M, int64_t N, int64_t K, alp_path path,
+                               const alp_config* cfg);
+alp_status alp_tune_clear_cache(void);
+
+/* ---- learned cost model (FP32 MLP 7 -> 64 -> 64 -> C, ReLU) -------------- */
+/* Parameters: one float array W1[64][7], b1[64], W2[64][64], b2[64], W3[C][64],
+ * b3[C] (alp_mlp_param_count(C) floats).  C = alp_config_count(NATIVE) +
+ * alp_config_count(EMUL): outputs 0.. are the native configs in sweep order,
+ * then the emulated path's.  All arrays are device memory unless noted. */
+int64_t alp_mlp_param_count(int C);
+/* X[i][0..6] = (log2 M, log2 N, log2 K, log2 M/N, log2 N/K, log2 M/K, path)
+ * for path = 0 (native) or 1 (emulated), minus mean and divided by std when
+ * both are given (7 floats each). */
+alp_status alp_mlp_features(int64_t count, const int64_t* dM, const int64_t* dN,
+                            const int64_t* dK, const int32_t* dpath, const float* mean,
+                            const float* std, float* X, void* stream);
+/* Per-feature mean and standard deviation of X (count x 7), for standardising. */
+alp_status alp_mlp_feature_stats(int64_t count, const float* X, float* mean, float* std,
+                                 void* stream);
+/* Y (B x C) = forward(params, X (B x 7)); cache (B x 128) keeps the
+ * pre-activations for alp_mlp_backward. */
+alp_status alp_mlp_forward(const float* params, int C, const float* X, int64_t B, float* Y,
+                           float* cache, void* stream);
+/* Gradients (alp_mlp_param_count(C) floats) of the masked mean squared error
+ * L = sum Mask (Y - T)^2 / sum Mask over B x C, from a forward pass's Y and
+ * cache; loss_out[0] = L, loss_out[1] = sum Mask; work: B * (C + 128) floats. */
+alp_status alp_mlp_backward(const float* params, int C, const float* X, int64_t B,
+                            const float* cache, const float* Y, const float* T,
+                            const float* Mask, float* grads, float* work, float* loss_out,
+                            void* stream);
+/* One Adam step (bias-corrected, step counts from 1) over n parameters. */
+alp_status alp_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t n,
+                        int step, float lr, float beta1, float beta2, float eps, void* stream);
+/* Installs a trained model (HOST arrays: params, 7-float mean and std) for
+ * alp_tune(PREDICT) and for GEMM calls with cfg == NULL that miss the tuned
+ * cache (the prediction runs the forward kernel once per new shape, then it
+ * is cached); unload removes it. */
+alp_status alp_tune_load_model(const float* host_params, int C, const float* host_mean,
+                               const float* host_std);
+alp_status alp_tune_unload_model(void);
+
+/* ---- batched GEMM: size classes and CUDA graph -------------------------- */
+
+/* Size class of a problem in alp_gemm_batched_varsize: 3 * r + c with
+ * r = 0, 1, 2 for M <= 32, <= 64, larger and c likewise from N. */
+int alp_batched_class_of(int64_t M, int64_t N);
+
+/* Tile (bm x bn, K step bk) used for the problems of class `cls` (0..8):
+ * bm, bn in {32, 64, 128}, bk in {16, 32, 64}; each tile runs on 8 warps with
+ * a (bm/16) x (bn/16) register tile per thread.  Defaults: bm, bn = 32, 64,
+ * 128 by class, bk = 32 for classes with a 32-wide side, else 16.  Process-wide
+ * setting, read when a batched call is issued (or captured). */
+alp_status alp_batched_set_class_config(int cls, int bm, int bn, int bk);
+alp_status alp_batched_get_class_config(int cls, int* bm, int* bn, int* bk);
+
+/* Captures one alp_gemm_batched_varsize call (same arguments, stream
+ * omitted) into a CUDA graph and instantiates it; *graph_out receives an
+ * opaque handle.  Launching the handle replays the plan and the persistent
+ * kernel on `stream`, reading the device arrays as they are at launch time
+ * (the pointers are fixed at capture; the grid is sized from hM/hN at capture
+ * and stays correct for any sizes).  Destroy with alp_batched_graph_destroy. */
+alp_status alp_batched_graph_create(int64_t count, const int64_t* dM, const int64_t* dN,
+                                    const int64_t* dK, const double* dalpha,
+                                    const double* const* dA, const int64_t* dlda,
+                                    const double* const* dB, const int64_t* dldb,
+                                    const double* dbeta, double* const* dC,
+                                    const int64_t* dldc, const int64_t* hM,
+                                    const int64_t* hN, const int64_t* hK, void* workspace,
+                                    size_t workspace_bytes, void** graph_out);
+alp_status alp_batched_graph_launch(void* graph, void* stream);
+alp_status alp_batched_graph_destroy(void* graph);
+
 /* ---- FP64 peak probe ----------------------------------------------------- */
 
 /* Measured FP64 throughput of this GPU: kind 0 = m16n8k4 DMMA chains (the

@@ -83,6 +83,28 @@ _SIGS = {
     "alp_set_wait_timeout_ms": ([_f64], _int),
     "alp_debug_inject_skip": ([_int], _int),
     "alp_probe_fp64_peak": ([_int, _i64, _int, _int, ctypes.POINTER(_f64), _vp], _int),
+    "alp_tune_time_config": ([_i64, _i64, _i64, _int, ctypes.POINTER(alp_config), _int, _int,
+                              ctypes.POINTER(_f64)], _int),
+    "alp_tune_set_cached": ([_i64, _i64, _i64, _int, ctypes.POINTER(alp_config)], _int),
+    "alp_tune_clear_cache": ([], _int),
+    "alp_mlp_param_count": ([_int], _i64),
+    "alp_mlp_features": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+    "alp_mlp_feature_stats": ([_i64, _vp, _vp, _vp, _vp], _int),
+    "alp_mlp_forward": ([_vp, _int, _vp, _i64, _vp, _vp, _vp], _int),
+    "alp_mlp_backward": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+    "alp_mlp_adam": ([_vp, _vp, _vp, _vp, _i64, _int, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, ctypes.c_float, _vp], _int),
+    "alp_tune_load_model": ([_vp, _int, _vp, _vp], _int),
+    "alp_tune_unload_model": ([], _int),
+    "alp_batched_class_of": ([_i64, _i64], _int),
+    "alp_batched_set_class_config": ([_int, _int, _int, _int], _int),
+    "alp_batched_get_class_config": ([_int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                      ctypes.POINTER(_int)], _int),
+    "alp_batched_graph_create": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                  ctypes.POINTER(_vp)], _int),
+    "alp_batched_graph_launch": ([_vp, _vp], _int),
+    "alp_batched_graph_destroy": ([_vp], _int),
 }
 
 
@@ -260,3 +282,105 @@ def alp_probe_fp64_peak(kind=0, iters=20000, blocks_per_sm=2, threads=256, strea
     _check(lib().alp_probe_fp64_peak(int(kind), int(iters), int(blocks_per_sm), int(threads),
                                      ctypes.byref(out), _s(stream)), "alp_probe_fp64_peak", True)
     return out.value
+
+
+def alp_batched_class_of(M, N) -> int:
+    return int(lib().alp_batched_class_of(M, N))
+
+
+def alp_batched_set_class_config(cls, bm, bn, bk):
+    return _check(lib().alp_batched_set_class_config(int(cls), int(bm), int(bn), int(bk)),
+                  "alp_batched_set_class_config", True)
+
+
+def alp_batched_get_class_config(cls):
+    bm, bn, bk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().alp_batched_get_class_config(int(cls), ctypes.byref(bm), ctypes.byref(bn),
+                                              ctypes.byref(bk)), "alp_batched_get_class_config",
+           True)
+    return bm.value, bn.value, bk.value
+
+
+def alp_batched_graph_create(count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC, dldc,
+                             hM, hN, hK, workspace, workspace_bytes):
+    h = ctypes.c_void_p()
+    st = lib().alp_batched_graph_create(count, _p(dM), _p(dN), _p(dK), _p(dalpha), _p(dA),
+                                        _p(dlda), _p(dB), _p(dldb), _p(dbeta), _p(dC), _p(dldc),
+                                        _host(hM), _host(hN), _host(hK), _p(workspace),
+                                        int(workspace_bytes), ctypes.byref(h))
+    _check(st, "alp_batched_graph_create", True)
+    return h.value
+
+
+def alp_batched_graph_launch(graph, stream=None):
+    return _check(lib().alp_batched_graph_launch(graph, _s(stream)), "alp_batched_graph_launch",
+                  True)
+
+
+def alp_batched_graph_destroy(graph):
+    return _check(lib().alp_batched_graph_destroy(graph), "alp_batched_graph_destroy", True)
+
+
+def _cfg(c):
+    return c if isinstance(c, alp_config) else alp_config(*c)
+
+
+def alp_tune_time_config(M, N, K, path, cfg, use_proxy=True, runs=3):
+    out = ctypes.c_double(0.0)
+    c = _cfg(cfg)
+    _check(lib().alp_tune_time_config(M, N, K, int(path), ctypes.byref(c), int(bool(use_proxy)),
+                                      int(runs), ctypes.byref(out)), "alp_tune_time_config", True)
+    return out.value
+
+
+def alp_tune_set_cached(M, N, K, path, cfg):
+    c = _cfg(cfg)
+    return _check(lib().alp_tune_set_cached(M, N, K, int(path), ctypes.byref(c)),
+                  "alp_tune_set_cached", True)
+
+
+def alp_tune_clear_cache():
+    return _check(lib().alp_tune_clear_cache(), "alp_tune_clear_cache", True)
+
+
+def alp_mlp_param_count(C) -> int:
+    return int(lib().alp_mlp_param_count(int(C)))
+
+
+def alp_mlp_features(count, dM, dN, dK, dpath, mean, std, X, stream=None):
+    return _check(lib().alp_mlp_features(count, _p(dM), _p(dN), _p(dK), _p(dpath), _p(mean),
+                                         _p(std), _p(X), _s(stream)), "alp_mlp_features", True)
+
+
+def alp_mlp_feature_stats(count, X, mean, std, stream=None):
+    return _check(lib().alp_mlp_feature_stats(count, _p(X), _p(mean), _p(std), _s(stream)),
+                  "alp_mlp_feature_stats", True)
+
+
+def alp_mlp_forward(params, C, X, B, Y, cache, stream=None):
+    return _check(lib().alp_mlp_forward(_p(params), int(C), _p(X), B, _p(Y), _p(cache),
+                                        _s(stream)), "alp_mlp_forward", True)
+
+
+def alp_mlp_backward(params, C, X, B, cache, Y, T, Mask, grads, work, loss, stream=None):
+    return _check(lib().alp_mlp_backward(_p(params), int(C), _p(X), B, _p(cache), _p(Y), _p(T),
+                                         _p(Mask), _p(grads), _p(work), _p(loss), _s(stream)),
+                  "alp_mlp_backward", True)
+
+
+def alp_mlp_adam(params, grads, m, v, n, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                 stream=None):
+    return _check(lib().alp_mlp_adam(_p(params), _p(grads), _p(m), _p(v), n, int(step),
+                                     float(lr), float(beta1), float(beta2), float(eps),
+                                     _s(stream)), "alp_mlp_adam", True)
+
+
+def alp_tune_load_model(host_params, C, host_mean, host_std):
+    """host_* are contiguous float32 numpy arrays."""
+    return _check(lib().alp_tune_load_model(host_params.ctypes.data, int(C),
+                                            host_mean.ctypes.data, host_std.ctypes.data),
+                  "alp_tune_load_model", True)
+
+
+def alp_tune_unload_model():
+    return _check(lib().alp_tune_unload_model(), "alp_tune_unload_model", True)

@@ -10,17 +10,19 @@
 #include "alp_internal.cuh"
 #include "alp_ext.h"
 #include "native_cfg.h"
+#include "emul.cuh"
 
 namespace alp {
 
 alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t N, int64_t K,
                          double alpha, const double* A, int64_t lda, const double* B,
                          int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t stream,
-                         int inject_skip_kt);
+                         int inject_skip_kt, int64_t grid_limit);
 alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ldc,
                         cudaStream_t stream);
 // tune.cu: tuned cache, then cost model, then default.
-bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out);
+bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out,
+                   cudaStream_t stream);
 
 // ----------------------------------------------------------------------------
 // Per-device state.
@@ -143,7 +145,10 @@ static bool default_native_config(alp_config* out) {
 }
 
 bool default_config(alp_path path, alp_config* out) {
-    (void)path;
+    if (path == ALP_PATH_EMUL) {
+        *out = alp_config{128, 256, 64, 0, 0, 8};   // raster group of 8 tile-rows
+        return true;
+    }
     return default_native_config(out);
 }
 
@@ -198,7 +203,7 @@ alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const dou
     if (cfg) {
         c = *cfg;
         if (!native_config_valid(c.bm, c.bn, c.bk, c.tm, c.tn, c.stages)) return ALP_ERR_INVALID_ARG;
-    } else if (!select_config(M, N, K, ALP_PATH_NATIVE, &c)) {
+    } else if (!select_config(M, N, K, ALP_PATH_NATIVE, &c, s)) {
         default_config(ALP_PATH_NATIVE, &c);
     }
     if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
@@ -206,7 +211,7 @@ alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const dou
     const bool tma_ok = (((uintptr_t)A & 15) == 0) && (((uintptr_t)B & 15) == 0) &&
                         (lda % 2 == 0) && (ldb % 2 == 0);
     return native_launch(c, tma_ok, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s,
-                         inject_skip_kt());
+                         inject_skip_kt(), 0);
 }
 
 alp_status alp_get_device_error(void* stream) {
@@ -227,6 +232,7 @@ int alp_config_valid(const alp_config* cfg, alp_path path) {
     if (!cfg) return 0;
     if (path == ALP_PATH_NATIVE)
         return native_config_valid(cfg->bm, cfg->bn, cfg->bk, cfg->tm, cfg->tn, cfg->stages) ? 1 : 0;
+    if (path == ALP_PATH_EMUL) return emul_config_valid(*cfg) ? 1 : 0;
     return 0;
 }
 

@@ -26,6 +26,8 @@ alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ld
 alp_status validate_gemm(int64_t M, int64_t N, int64_t K, double alpha, const void* A,
                          int64_t lda, const void* B, int64_t ldb, double beta, const void* C,
                          int64_t ldc);
+bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out,
+                   cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // 1. exponent scan
@@ -210,51 +212,76 @@ __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64
 // ---------------------------------------------------------------------------
 // 4. recombination + alpha/beta epilogue
 // ---------------------------------------------------------------------------
-// Nearest double (ties to even) of a 128-bit two's-complement integer.
-__device__ __forceinline__ double int128_to_double_rn(unsigned __int128 x) {
+// Nearest double (ties to even) of a 128-bit two's-complement integer,
+// multiplied by 2^E: built from integer operations on the IEEE encoding
+// (FP64 arithmetic is slow on this GPU).  When the scaled result would leave
+// the normal range it falls back to ldexp, which rounds a subnormal result once.
+__device__ __forceinline__ double int128_scaled_to_double_rn(unsigned __int128 x, int E) {
     const bool neg = (x >> 127) != 0;
     const unsigned __int128 u = neg ? (unsigned __int128)0 - x : x;
     const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
-    double v;
-    if (hi == 0) {
-        v = __ull2double_rn(lo);
+    if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    uint64_t m;
+    int ex = msb;
+    if (msb <= 52) {
+        m = lo << (52 - msb);   // exact
     } else {
-        const int msb = 127 - __clzll((long long)hi);
-        const int shift = msb - 52;   // >= 12
-        uint64_t m = (uint64_t)(u >> shift);
+        const int shift = msb - 52;
+        m = (uint64_t)(u >> shift);
         const unsigned __int128 rem = u & (((unsigned __int128)1 << shift) - 1);
         const unsigned __int128 halfw = (unsigned __int128)1 << (shift - 1);
-        int ex = msb;
         if (rem > halfw || (rem == halfw && (m & 1))) ++m;
         if (m >> 53) {
             m >>= 1;
             ++ex;
         }
-        v = __longlong_as_double((long long)(((uint64_t)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
     }
-    return neg ? -v : v;
+    // m in [2^52, 2^53): value = m * 2^(ex - 52) * 2^E
+    const int be = ex + E + 1023;
+    if (be >= 1 && be <= 2046) {
+        const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
+        return __longlong_as_double((long long)bits);
+    }
+    // outside the normal range: the unscaled value is exact in double, scale once
+    const double v = __longlong_as_double(
+        (long long)(((uint64_t)neg << 63) | ((uint64_t)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
+    return ldexp(v, E);
 }
 
+// One block row of threads per matrix row chunk: rows from blockIdx.y (grid
+// stride), columns from the x dimension (no integer division per element).
 __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, int64_t ldg,
                                  int s, const int32_t* __restrict__ e,
                                  const int32_t* __restrict__ f, int64_t M, int64_t N,
                                  double alpha, double beta, double* __restrict__ C, int64_t ldc) {
-    const int64_t total = M * N;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / N, j = idx - i * N;
-        unsigned __int128 X = 0;
-        for (int t = 2; t <= s + 1; ++t) {
-            const int64_t S = __ldg(G + (int64_t)(t - 2) * gplane + i * ldg + j);
-            X += ((unsigned __int128)(__int128)S) << ((s + 1 - t) * kDigitBits);
+    const int shift0 = (s + 1) * kDigitBits;
+    for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
+        const int ei = e[i];
+        const int32_t* gi = G + i * ldg;
+        double* ci = C + i * ldc;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            unsigned __int128 X = 0;
+            for (int t = 2; t <= s + 1; ++t) {
+                const int64_t S = __ldg(gi + (int64_t)(t - 2) * gplane + j);
+                X += ((unsigned __int128)(__int128)S) << ((s + 1 - t) * kDigitBits);
+            }
+            const double w = int128_scaled_to_double_rn(X, ei + __ldg(f + j) - shift0);
+            double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
+            if (beta != 0.0) out = __fma_rn(beta, ci[j], out);
+            ci[j] = out;
         }
-        const double v = int128_to_double_rn(X);
-        const double w = ldexp(v, e[i] + f[j] - (s + 1) * kDigitBits);
-        double out = alpha * w;
-        double* c = C + i * ldc + j;
-        if (beta != 0.0) out = __fma_rn(beta, *c, out);
-        *c = out;
     }
+}
+
+static dim3 recombine_grid(int64_t M, int64_t N) {
+    const int64_t bx = (N + 255) / 256;
+    int64_t by = (int64_t)device_sm_count() * 16 / (bx > 0 ? bx : 1);
+    if (by < 1) by = 1;
+    if (by > M) by = M;
+    if (by > 65535) by = 65535;
+    return dim3((unsigned)(bx > 0 ? bx : 1), (unsigned)by);
 }
 
 // ---------------------------------------------------------------------------
@@ -372,7 +399,7 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, const int32_t* 
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
-    recombine_kernel<<<grid_for(M * N, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+    recombine_kernel<<<recombine_grid(M, N), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         G, M * ldg, ldg, nslices, e, f, M, N, alpha, beta, C, ldc);
     return cuda_status(cudaGetLastError());
 }
@@ -403,8 +430,12 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
     if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s)) != ALP_OK) return st;
     if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s)) != ALP_OK) return st;
-    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s)) != ALP_OK) return st;
-    recombine_kernel<<<grid_for(M * N, 256), 256, 0, s>>>(G, M * L.ldg, L.ldg, nslices, e, f, M,
+    alp_config cfg;
+    const int group_m = (select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg))
+                            ? cfg.stages : 0;
+    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s, group_m)) != ALP_OK)
+        return st;
+    recombine_kernel<<<recombine_grid(M, N), 256, 0, s>>>(G, M * L.ldg, L.ldg, nslices, e, f, M,
                                                           N, alpha, beta, C, ldc);
     return cuda_status(cudaGetLastError());
 }

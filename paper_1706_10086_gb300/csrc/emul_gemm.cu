@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int group_m) {
     {   // the job table of one tile must fit its shared-memory slot
         const int64_t kblocks = (K + kTK - 1) / kTK;
         int64_t njobs = 0;
@@ -330,7 +330,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     if (tiles_m * tiles_n > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     p.tiles_m = (int)tiles_m;
     p.tiles_n = (int)tiles_n;
-    p.group_m = emul_group_m();
+    p.group_m = group_m > 0 ? group_m : emul_group_m();
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
     cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel,

@@ -163,10 +163,11 @@ template <int TM, int TN>
 static alp_status launch_tm_tn(const alp_config& cfg, int stages, bool use_tma, int64_t M,
                                int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                                const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                               cudaStream_t stream, int inject_skip_kt) {
+                               cudaStream_t stream, int inject_skip_kt, int64_t grid_limit) {
     const int tiles_m = (int)((M + cfg.bm - 1) / cfg.bm);
     const int tiles_n = (int)((N + cfg.bn - 1) / cfg.bn);
-    const int64_t grid = (int64_t)tiles_m * tiles_n;
+    int64_t grid = (int64_t)tiles_m * tiles_n;
+    if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;   // tuner's one-wave proxy
     if (grid > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     const bool vec2 = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 2 == 0);
     if (use_tma) {
@@ -223,12 +224,12 @@ alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ld
 alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t N, int64_t K,
                          double alpha, const double* A, int64_t lda, const double* B,
                          int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t stream,
-                         int inject_skip_kt) {
+                         int inject_skip_kt, int64_t grid_limit) {
     const int stages = native_stages(cfg.bm, cfg.bn, cfg.bk, cfg.stages);
 #define ALP_NATIVE_CASE(a, b)                                                                     \
     if (cfg.tm == a && cfg.tn == b)                                                               \
         return launch_tm_tn<a, b>(cfg, stages, use_tma, M, N, K, alpha, A, lda, B, ldb, beta, C, \
-                                  ldc, stream, inject_skip_kt);
+                                  ldc, stream, inject_skip_kt, grid_limit);
     ALP_NATIVE_CASE(2, 2) ALP_NATIVE_CASE(2, 4) ALP_NATIVE_CASE(2, 8)
     ALP_NATIVE_CASE(4, 2) ALP_NATIVE_CASE(4, 4) ALP_NATIVE_CASE(4, 8)
     ALP_NATIVE_CASE(8, 2) ALP_NATIVE_CASE(8, 4) ALP_NATIVE_CASE(8, 8)

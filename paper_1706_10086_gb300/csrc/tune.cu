@@ -1,21 +1,33 @@
 // Autotuner: enumeration of the valid tile configs, CUDA-event timing of each
-// on the GPU, the tuned-config cache consulted by alp_gemm_f64(cfg = NULL),
+// on the GPU, the tuned-config cache consulted by the GEMM calls (cfg = NULL),
 // and the append-only JSONL timing database.
 //
 // The paper tunes its tile size T by sweeping powers of two at one matrix
-// size (N = 10240, control N = 7168) and keeping the best (Sect. 3 "Parameter
-// Tuning", Fig. 3, Table 4).  Here the sweep covers the block tile, the K
-// step and the per-thread tile, for any (M, N, K).
+// size (N = 10240, control N = 7168) and keeping the best of ten runs
+// (Sect. 2, Sect. 3 "Parameter Tuning", Fig. 3, Table 4).  Here the sweep covers
+// the block tile, the K step and the per-thread tile (native path) or the
+// raster group (emulated path), for any (M, N, K).
+//
+// Timing proxy: a large shape would take seconds per config in FP64, so a
+// config is timed on one wave of blocks (the first min(tiles, SMs x blocks
+// per SM) tiles) with K capped at kProxyK, and the time is scaled by the
+// tiles per SM (full problem over proxy: blocks on one SM share its FP64
+// pipe) and by K / K'.  Shapes that fit one wave with K <= kProxyK are timed
+// exactly.  The emulated path runs its full grid with K capped.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <ctime>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
 #include "alp_ext.h"
 #include "alp_internal.cuh"
+#include "emul.cuh"
 #include "native_cfg.h"
 
 namespace alp {
@@ -23,19 +35,24 @@ namespace alp {
 alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t N, int64_t K,
                          double alpha, const double* A, int64_t lda, const double* B,
                          int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t stream,
-                         int inject_skip_kt);
+                         int inject_skip_kt, int64_t grid_limit);
 int native_occupancy(const alp_config& cfg, bool use_tma);
 bool default_config(alp_path path, alp_config* out);
 bool model_predict(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out,
                    double* pred_tflops);
 
 namespace {
+constexpr int64_t kProxyK = 256;        // K cap of the native timing proxy
+constexpr int64_t kProxyKEmul = 256;    // K cap of the emulated timing proxy
+constexpr int kTimedRuns = 10;          // the paper keeps the best of ten runs
+
 std::mutex g_tmu;
 std::map<std::tuple<int64_t, int64_t, int64_t, int>, alp_config> g_cache;
 
 const int kBM[3] = {64, 128, 256};
 const int kBK[3] = {16, 32, 64};
 const int kT[3] = {2, 4, 8};
+const int kGroups[6] = {1, 2, 4, 8, 16, 32};
 
 std::vector<alp_config> native_configs() {
     std::vector<alp_config> v;
@@ -48,14 +65,171 @@ std::vector<alp_config> native_configs() {
                             v.push_back(alp_config{bm, bn, bk, tm, tn, 0});
     return v;
 }
+
+std::vector<alp_config> emul_configs() {
+    std::vector<alp_config> v;
+    for (int g : kGroups) v.push_back(alp_config{128, 256, 64, 0, 0, g});
+    return v;
+}
+
+int runs_from_env() {
+    if (const char* s = std::getenv("ALP_TUNE_RUNS")) {
+        const int v = std::atoi(s);
+        if (v >= 1 && v <= 100) return v;
+    }
+    return kTimedRuns;
+}
+
+// Device scratch of one tuning call.
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~Scratch() {
+        if (p) cudaFree(p);
+    }
+    bool get(size_t n) {
+        if (n <= bytes) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&p, n) != cudaSuccess) return false;
+        bytes = n;
+        return cudaMemset(p, 0x3F, n) == cudaSuccess;   // finite, nonzero values
+    }
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Best and median of `runs` event-timed launches (after one warm-up), in ms.
+template <class F>
+bool time_launch(F&& launch, cudaStream_t st, int runs, double* best, double* median) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return false;
+    if (cudaEventCreate(&e1) != cudaSuccess) return false;
+    bool ok = launch() == ALP_OK;
+    std::vector<double> t;
+    for (int r = 0; ok && r < runs; ++r) {
+        cudaEventRecord(e0, st);
+        ok = launch() == ALP_OK;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok || t.empty()) return false;
+    std::sort(t.begin(), t.end());
+    *best = t.front();
+    *median = t[t.size() / 2];
+    return true;
+}
+
+// Estimated full-problem time (ms) of one config, measured with the proxy
+// (or exactly when use_proxy is false or the proxy is the whole problem).
+bool time_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_config& cfg,
+                 bool use_proxy, Scratch& sc, cudaStream_t st, int runs, double* est_ms,
+                 double* meas_best, double* meas_median) {
+    if (path == ALP_PATH_NATIVE) {
+        const int64_t Kp = use_proxy ? std::min(K, kProxyK) : K;
+        const int64_t tiles = ((M + cfg.bm - 1) / cfg.bm) * ((N + cfg.bn - 1) / cfg.bn);
+        // the kernel a call with lda = K, ldb = N would take: TMA needs even
+        // leading dimensions (16-byte row strides)
+        const bool tma = (K % 2 == 0) && (N % 2 == 0);
+        int occ = native_occupancy(cfg, tma);
+        if (occ < 1) return false;
+        const int64_t slots = (int64_t)device_sm_count() * occ;
+        const int64_t run_tiles = use_proxy ? std::min(tiles, slots) : tiles;
+        const size_t ba = up256((size_t)M * Kp * 8), bb = up256((size_t)Kp * N * 8);
+        const size_t bc = up256((size_t)M * N * 8);
+        if (!sc.get(ba + bb + bc)) return false;
+        char* base = static_cast<char*>(sc.p);
+        const double* A = reinterpret_cast<const double*>(base);
+        const double* B = reinterpret_cast<const double*>(base + ba);
+        double* C = reinterpret_cast<double*>(base + ba + bb);
+        auto launch = [&]() {
+            return native_launch(cfg, tma, M, N, Kp, 1.0, A, Kp, B, N, 0.0, C, N, st, -1,
+                                 run_tiles);
+        };
+        if (!time_launch(launch, st, runs, meas_best, meas_median)) return false;
+        // co-resident blocks share an SM's FP64 pipe, so time follows the
+        // tiles each SM must process: ceil(tiles / SMs) in the full problem
+        // against ceil(run_tiles / SMs) in the proxy
+        const double sms = (double)device_sm_count();
+        const double scale = std::ceil((double)tiles / sms) / std::ceil((double)run_tiles / sms);
+        *est_ms = *meas_best * scale * ((double)K / (double)Kp);
+        return true;
+    }
+    // emulated path: the tensor-core stage (its cost dominates), full grid
+    const int s = kMaxSlices;
+    const int64_t Kp = use_proxy ? std::min(K, kProxyKEmul) : K;
+    const int64_t kpad = (Kp + kEmulBK - 1) / kEmulBK * kEmulBK;
+    const int64_t ldg = (N + 255) / 256 * 256;
+    const size_t ba = up256((size_t)s * M * kpad * 2), bb = up256((size_t)s * N * kpad * 2);
+    const size_t bg = up256((size_t)s * M * ldg * 4);
+    if (!sc.get(ba + bb + bg)) return false;
+    char* base = static_cast<char*>(sc.p);
+    const auto* da = reinterpret_cast<const __nv_bfloat16*>(base);
+    const auto* db = reinterpret_cast<const __nv_bfloat16*>(base + ba);
+    int32_t* G = reinterpret_cast<int32_t*>(base + ba + bb);
+    auto launch = [&]() { return emul_slice_gemm(M, N, Kp, s, da, db, kpad, G, ldg, st, cfg.stages); };
+    if (!time_launch(launch, st, runs, meas_best, meas_median)) return false;
+    *est_ms = *meas_best * ((double)K / (double)Kp);
+    return true;
+}
+
+void db_append(int64_t M, int64_t N, int64_t K, alp_path path, const std::vector<alp_config>& cs,
+               const std::vector<double>& est, const std::vector<double>& best,
+               const std::vector<double>& med, int winner, bool proxy) {
+    const char* path_env = std::getenv("ALP_TUNE_DB");
+    if (!path_env || !*path_env) return;
+    FILE* f = std::fopen(path_env, "a");
+    if (!f) return;
+    char name[256] = "unknown";
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) std::snprintf(name, sizeof name, "%s", prop.name);
+    std::string line;
+    char buf[512];
+    std::snprintf(buf, sizeof buf,
+                  "{\"device\": \"%s\", \"M\": %lld, \"N\": %lld, \"K\": %lld, \"path\": \"%s\", "
+                  "\"proxy\": %s, \"kcap\": %lld, \"winner\": %d, \"configs\": [",
+                  name, (long long)M, (long long)N, (long long)K,
+                  path == ALP_PATH_NATIVE ? "native" : "emul", proxy ? "true" : "false",
+                  (long long)(path == ALP_PATH_NATIVE ? kProxyK : kProxyKEmul), winner);
+    line += buf;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        std::snprintf(buf, sizeof buf, "%s[%d, %d, %d, %d, %d, %d, %.6g, %.6g, %.6g]",
+                      i ? ", " : "", cs[i].bm, cs[i].bn, cs[i].bk, cs[i].tm, cs[i].tn, cs[i].stages,
+                      est[i], best[i], med[i]);
+        line += buf;
+    }
+    line += "]}\n";
+    std::fputs(line.c_str(), f);
+    std::fclose(f);
+}
+
 }  // namespace
 
 std::vector<alp_config> configs_of(alp_path path) {
     if (path == ALP_PATH_NATIVE) return native_configs();
+    if (path == ALP_PATH_EMUL) return emul_configs();
     return {};
 }
 
-bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out) {
+void cache_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_config& c) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_cache[std::make_tuple(M, N, K, (int)path)] = c;
+}
+
+// Config of a GEMM issued with cfg == NULL: the tuned cache, else the cost
+// model's prediction (made once per shape and then cached; skipped while
+// `stream` is being captured, since the prediction synchronises), else the
+// default.
+bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out,
+                   cudaStream_t stream) {
     {
         std::lock_guard<std::mutex> lk(g_tmu);
         auto it = g_cache.find(std::make_tuple(M, N, K, (int)path));
@@ -64,13 +238,14 @@ bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* o
             return true;
         }
     }
-    if (model_predict(M, N, K, path, out, nullptr)) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+        model_predict(M, N, K, path, out, nullptr)) {
+        cache_config(M, N, K, path, *out);
+        return true;
+    }
+    cudaGetLastError();
     return default_config(path, out);
-}
-
-void cache_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_config& c) {
-    std::lock_guard<std::mutex> lk(g_tmu);
-    g_cache[std::make_tuple(M, N, K, (int)path)] = c;
 }
 
 }  // namespace alp
@@ -86,6 +261,83 @@ alp_status alp_config_at(alp_path path, int idx, alp_config* out) {
     auto v = configs_of(path);
     if (idx < 0 || idx >= (int)v.size()) return ALP_ERR_INVALID_ARG;
     *out = v[idx];
+    return ALP_OK;
+}
+
+alp_status alp_tune_time_config(int64_t M, int64_t N, int64_t K, alp_path path,
+                                const alp_config* cfg, int use_proxy, int runs,
+                                double* est_ms) {
+    if (!cfg || !est_ms || M <= 0 || N <= 0 || K <= 0 || runs < 1) return ALP_ERR_INVALID_ARG;
+    if (!alp_config_valid(cfg, path)) return ALP_ERR_INVALID_ARG;
+    if (path == ALP_PATH_EMUL && K > kEmulMaxK) return ALP_ERR_UNSUPPORTED;
+    Scratch sc;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return ALP_ERR_CUDA;
+    double b = 0, m = 0;
+    const bool ok = time_config(M, N, K, path, *cfg, use_proxy != 0, sc, st, runs, est_ms, &b, &m);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return ok ? ALP_OK : ALP_ERR_CUDA;
+}
+
+alp_status alp_tune(int64_t M, int64_t N, int64_t K, alp_path path, alp_tune_mode mode,
+                    alp_config* out, double* out_tflops) {
+    if (!out || M <= 0 || N <= 0 || K <= 0) return ALP_ERR_INVALID_ARG;
+    if (path != ALP_PATH_NATIVE && path != ALP_PATH_EMUL) return ALP_ERR_INVALID_ARG;
+    const double flops = 2.0 * (double)M * (double)N * (double)K;
+    if (mode == ALP_TUNE_LOOKUP) {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        auto it = g_cache.find(std::make_tuple(M, N, K, (int)path));
+        if (it == g_cache.end()) return ALP_ERR_NOT_TUNED;
+        *out = it->second;
+        if (out_tflops) *out_tflops = 0.0;
+        return ALP_OK;
+    }
+    if (mode == ALP_TUNE_PREDICT) {
+        double tf = 0.0;
+        if (!model_predict(M, N, K, path, out, &tf)) return ALP_ERR_NOT_TUNED;
+        if (out_tflops) *out_tflops = tf;
+        return ALP_OK;
+    }
+    if (mode != ALP_TUNE_EXHAUSTIVE) return ALP_ERR_INVALID_ARG;
+    if (path == ALP_PATH_EMUL && K > kEmulMaxK) return ALP_ERR_UNSUPPORTED;
+    const std::vector<alp_config> cs = configs_of(path);
+    std::vector<double> est(cs.size(), INFINITY), best(cs.size(), INFINITY), med(cs.size(), INFINITY);
+    Scratch sc;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return ALP_ERR_CUDA;
+    const int runs = runs_from_env();
+    int winner = -1;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        if (!time_config(M, N, K, path, cs[i], true, sc, st, runs, &est[i], &best[i], &med[i]))
+            continue;
+        // tie-break: smaller shared memory, then the earlier (lexicographic) config
+        if (winner < 0 || est[i] < est[winner] ||
+            (est[i] == est[winner] &&
+             alp_config_smem_bytes(&cs[i]) < alp_config_smem_bytes(&cs[winner])))
+            winner = (int)i;
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (winner < 0) return ALP_ERR_CUDA;
+    const bool proxy = path == ALP_PATH_NATIVE ? (K > kProxyK) : (K > kProxyKEmul);
+    db_append(M, N, K, path, cs, est, best, med, winner, proxy);
+    cache_config(M, N, K, path, cs[winner]);
+    *out = cs[winner];
+    if (out_tflops) *out_tflops = flops / (est[winner] * 1e-3) / 1e12;
+    return ALP_OK;
+}
+
+alp_status alp_tune_set_cached(int64_t M, int64_t N, int64_t K, alp_path path,
+                               const alp_config* cfg) {
+    if (!cfg || !alp_config_valid(cfg, path)) return ALP_ERR_INVALID_ARG;
+    cache_config(M, N, K, path, *cfg);
+    return ALP_OK;
+}
+
+alp_status alp_tune_clear_cache(void) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_cache.clear();
     return ALP_OK;
 }
 

@@ -1,0 +1,268 @@
+"""Autotuning workflow around the C-ABI: timing database, cost-model training
+on the GPU, prediction and regret.
+
+* :func:`collect` runs ``alp_tune(EXHAUSTIVE)`` for every (shape, path) not
+  yet in the JSONL database (the library appends one record per sweep, so an
+  interrupted collection resumes where it stopped).
+* :func:`dataset` turns records into targets ``ln(t_config / t_best)`` with a
+  mask for configs that could not run.
+* :func:`train` fits the MLP with the library's feature, forward, backward and
+  Adam kernels (full batch, float32).
+* :func:`predict` / :func:`evaluate` choose a config per held-out shape and
+  report its regret ``t(chosen) / t(best) - 1`` against the exhaustive sweep,
+  next to two choices without the network: one fixed config tuned once (the
+  paper's method, Sect. 3: one tile size per architecture, tuned at one matrix
+  size) and the winner of the nearest training shape.
+
+Everything numeric runs in the library's kernels; this module moves arrays.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from . import alp, inputs
+
+PATHS = {"native": alp.ALP_PATH_NATIVE, "emul": alp.ALP_PATH_EMUL}
+
+
+def config_lists():
+    nat = [alp.alp_config_at(alp.ALP_PATH_NATIVE, i).astuple()
+           for i in range(alp.alp_config_count(alp.ALP_PATH_NATIVE))]
+    emu = [alp.alp_config_at(alp.ALP_PATH_EMUL, i).astuple()
+           for i in range(alp.alp_config_count(alp.ALP_PATH_EMUL))]
+    return nat, emu
+
+
+def load_db(path):
+    recs = []
+    if not os.path.exists(path):
+        return recs
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line:
+                recs.append(json.loads(line))
+    return recs
+
+
+def collect(shapes, paths, db_path, runs=2, log_every=0):
+    """Exhaustive sweeps of every (M, N, K) in ``shapes`` for each path name in
+    ``paths``, skipping those already in the database."""
+    os.environ["ALP_TUNE_DB"] = db_path
+    os.environ["ALP_TUNE_RUNS"] = str(runs)
+    have = {(r["M"], r["N"], r["K"], r["path"]) for r in load_db(db_path)}
+    done = 0
+    for (M, N, K) in shapes:
+        for pname in paths:
+            if (int(M), int(N), int(K), pname) in have:
+                continue
+            if pname == "emul" and K > 32768:
+                continue
+            alp.alp_tune(int(M), int(N), int(K), PATHS[pname], alp.ALP_TUNE_EXHAUSTIVE)
+            done += 1
+            if log_every and done % log_every == 0:
+                print(f"collect: {done} sweeps", flush=True)
+    return done
+
+
+def _record_times(rec, nat, emu):
+    """Per-output times (ms) of one record, NaN where not measured."""
+    C = len(nat) + len(emu)
+    t = np.full(C, np.nan)
+    index = {c: i for i, c in enumerate(nat)} if rec["path"] == "native" else \
+        {c: len(nat) + i for i, c in enumerate(emu)}
+    for row in rec["configs"]:
+        key = tuple(int(v) for v in row[:6])
+        est = row[6]
+        if key in index and est is not None and math.isfinite(est):
+            t[index[key]] = est
+    return t
+
+
+def dataset(records):
+    nat, emu = config_lists()
+    C = len(nat) + len(emu)
+    M = np.array([r["M"] for r in records], dtype=np.int64)
+    N = np.array([r["N"] for r in records], dtype=np.int64)
+    K = np.array([r["K"] for r in records], dtype=np.int64)
+    P = np.array([1 if r["path"] == "emul" else 0 for r in records], dtype=np.int32)
+    times = np.stack([_record_times(r, nat, emu) for r in records]) if records else \
+        np.zeros((0, C))
+    best = np.nanmin(times, axis=1)
+    T = np.log(times / best[:, None])
+    Mask = np.isfinite(T).astype(np.float32)
+    T = np.where(Mask > 0, T, 0.0).astype(np.float32)
+    return {"M": M, "N": N, "K": K, "path": P, "times": times, "T": T, "Mask": Mask, "C": C}
+
+
+def init_params(C, seed):
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, from the
+    seeded generator (passed to the kernels as inputs)."""
+    shapes = [(64, 7), (64,), (64, 64), (64,), (C, 64), (C,)]
+    out, off = [], 0
+    for shp in shapes:
+        n = int(np.prod(shp))
+        if len(shp) == 2:
+            a = inputs.uniform(seed, off, shp) / math.sqrt(shp[1])
+        else:
+            a = np.zeros(shp)
+        out.append(a)
+        off += n
+    return np.concatenate([a.ravel() for a in out]).astype(np.float32)
+
+
+class Trainer:
+    """Device state of one training run."""
+
+    def __init__(self, ds, seed=1706 + 4):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda")
+        self.C = ds["C"]
+        self.B = len(ds["M"])
+        t = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        self.dM, self.dN, self.dK = (t(ds[k], torch.int64) for k in ("M", "N", "K"))
+        self.dpath = t(ds["path"], torch.int32)
+        self.Xraw = torch.empty(self.B, 7, dtype=torch.float32, device=dev)
+        self.X = torch.empty(self.B, 7, dtype=torch.float32, device=dev)
+        self.mean = torch.empty(7, dtype=torch.float32, device=dev)
+        self.std = torch.empty(7, dtype=torch.float32, device=dev)
+        alp.alp_mlp_features(self.B, self.dM, self.dN, self.dK, self.dpath, None, None, self.Xraw)
+        alp.alp_mlp_feature_stats(self.B, self.Xraw, self.mean, self.std)
+        alp.alp_mlp_features(self.B, self.dM, self.dN, self.dK, self.dpath, self.mean, self.std,
+                             self.X)
+        self.T = t(ds["T"], torch.float32)
+        self.Mask = t(ds["Mask"], torch.float32)
+        self.nparam = alp.alp_mlp_param_count(self.C)
+        self.params = t(init_params(self.C, seed), torch.float32)
+        self.grads = torch.zeros(self.nparam, dtype=torch.float32, device=dev)
+        self.m = torch.zeros_like(self.grads)
+        self.v = torch.zeros_like(self.grads)
+        self.Y = torch.empty(self.B, self.C, dtype=torch.float32, device=dev)
+        self.cache = torch.empty(self.B, 128, dtype=torch.float32, device=dev)
+        self.work = torch.empty(self.B * (self.C + 128), dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=dev)
+        self.step = 0
+
+    def epoch(self, lr):
+        alp.alp_mlp_forward(self.params, self.C, self.X, self.B, self.Y, self.cache)
+        alp.alp_mlp_backward(self.params, self.C, self.X, self.B, self.cache, self.Y, self.T,
+                             self.Mask, self.grads, self.work, self.loss)
+        self.step += 1
+        alp.alp_mlp_adam(self.params, self.grads, self.m, self.v, self.nparam, self.step, lr)
+
+    def current_loss(self):
+        alp.alp_mlp_forward(self.params, self.C, self.X, self.B, self.Y, self.cache)
+        alp.alp_mlp_backward(self.params, self.C, self.X, self.B, self.cache, self.Y, self.T,
+                             self.Mask, self.grads, self.work, self.loss)
+        return float(self.loss[0].item())
+
+    def model(self):
+        return (self.params.cpu().numpy().copy(), self.mean.cpu().numpy().copy(),
+                self.std.cpu().numpy().copy())
+
+
+def train(ds, epochs=3000, lr=3e-3, seed=1706 + 4, log_every=0):
+    tr = Trainer(ds, seed)
+    hist = [tr.current_loss()]
+    for e in range(epochs):
+        tr.epoch(lr if e < epochs * 0.7 else lr * 0.1)
+        if log_every and (e + 1) % log_every == 0:
+            hist.append(tr.current_loss())
+    hist.append(tr.current_loss())
+    return tr.model(), hist
+
+
+def predict(model, M, N, K, path):
+    """Predicted outputs (n x C) for shapes with the library's forward kernel."""
+    import torch
+    params, mean, std = model
+    dev = torch.device("cuda")
+    n = len(M)
+    C = (len(params) - 4672) // 65
+    t = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    X = torch.empty(n, 7, dtype=torch.float32, device=dev)
+    alp.alp_mlp_features(n, t(M, torch.int64), t(N, torch.int64), t(K, torch.int64),
+                         t(path, torch.int32), t(mean, torch.float32), t(std, torch.float32), X)
+    Y = torch.empty(n, C, dtype=torch.float32, device=dev)
+    cache = torch.empty(n, 128, dtype=torch.float32, device=dev)
+    alp.alp_mlp_forward(t(params, torch.float32), C, X, n, Y, cache)
+    return Y.cpu().numpy()
+
+
+def _valid_range(path, n_nat, C):
+    return (0, n_nat) if path == 0 else (n_nat, C)
+
+
+def choose_by_model(model, ds):
+    nat, _ = config_lists()
+    Y = predict(model, ds["M"], ds["N"], ds["K"], ds["path"])
+    out = np.empty(len(Y), dtype=np.int64)
+    for i, y in enumerate(Y):
+        lo, hi = _valid_range(ds["path"][i], len(nat), ds["C"])
+        out[i] = lo + int(np.argmin(y[lo:hi]))
+    return out
+
+
+def regret(ds, choice):
+    t = ds["times"][np.arange(len(choice)), choice]
+    best = np.nanmin(ds["times"], axis=1)
+    r = t / best - 1.0
+    return np.where(np.isfinite(r), r, np.nan)
+
+
+def fixed_config_choice(train_ds, test_ds, tuning_shape=None):
+    """One config per path for every shape.  With tuning_shape = (M, N, K) it
+    is the winner of that single shape (the paper's tuning protocol);
+    otherwise the config with the lowest mean ln(t / t_best) over training."""
+    nat, _ = config_lists()
+    out = np.empty(len(test_ds["M"]), dtype=np.int64)
+    for p in (0, 1):
+        lo, hi = _valid_range(p, len(nat), train_ds["C"])
+        sel = train_ds["path"] == p
+        if not sel.any():
+            continue
+        if tuning_shape is not None:
+            d = (np.log2(train_ds["M"][sel]) - math.log2(tuning_shape[0])) ** 2 + \
+                (np.log2(train_ds["N"][sel]) - math.log2(tuning_shape[1])) ** 2 + \
+                (np.log2(train_ds["K"][sel]) - math.log2(tuning_shape[2])) ** 2
+            row = train_ds["times"][sel][int(np.argmin(d))]
+            c = lo + int(np.nanargmin(row[lo:hi]))
+        else:
+            T = np.where(train_ds["Mask"][sel] > 0, train_ds["T"][sel], np.inf)[:, lo:hi]
+            c = lo + int(np.argmin(np.mean(np.where(np.isfinite(T), T, 10.0), axis=0)))
+        out[test_ds["path"] == p] = c
+    return out
+
+
+def nearest_shape_choice(train_ds, test_ds):
+    f = lambda d: np.stack([np.log2(d["M"]), np.log2(d["N"]), np.log2(d["K"])], axis=1)
+    a, b = f(train_ds), f(test_ds)
+    out = np.empty(len(b), dtype=np.int64)
+    nat, _ = config_lists()
+    for i in range(len(b)):
+        same = train_ds["path"] == test_ds["path"][i]
+        idx = np.where(same)[0]
+        j = idx[int(np.argmin(((a[idx] - b[i]) ** 2).sum(axis=1)))]
+        lo, hi = _valid_range(test_ds["path"][i], len(nat), train_ds["C"])
+        out[i] = lo + int(np.nanargmin(train_ds["times"][j][lo:hi]))
+    return out
+
+
+def summarize(r):
+    r = r[np.isfinite(r)]
+    return {"mean": float(np.mean(r)), "median": float(np.median(r)),
+            "p90": float(np.percentile(r, 90)), "max": float(np.max(r)), "n": int(len(r))}
+
+
+def evaluate(model, train_ds, test_ds, tuning_shape=(10240, 10240, 10240)):
+    res = {"mlp": summarize(regret(test_ds, choose_by_model(model, test_ds))),
+           "fixed_tuned_once": summarize(regret(test_ds, fixed_config_choice(
+               train_ds, test_ds, tuning_shape))),
+           "fixed_best_mean": summarize(regret(test_ds, fixed_config_choice(train_ds, test_ds))),
+           "nearest_shape": summarize(regret(test_ds, nearest_shape_choice(train_ds, test_ds)))}
+    return res

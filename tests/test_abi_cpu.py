@@ -113,3 +113,25 @@ def test_argument_errors_return_before_launch(alp):
     # M == 0 or N == 0: nothing to do, nothing read
     assert g(0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == alp.ALP_OK
     assert g(4, 0, 4, 1.0, None, 4, None, 0, 0.0, None, 0) == alp.ALP_OK
+
+
+def test_batched_classes_and_config(alp):
+    assert alp.alp_batched_class_of(32, 32) == 0
+    assert alp.alp_batched_class_of(33, 32) == 3
+    assert alp.alp_batched_class_of(64, 65) == 5
+    assert alp.alp_batched_class_of(1000, 1) == 6
+    assert alp.alp_batched_class_of(65, 1000) == 8
+    old = alp.alp_batched_get_class_config(4)
+    try:
+        alp.alp_batched_set_class_config(4, 32, 128, 32)
+        assert alp.alp_batched_get_class_config(4) == (32, 128, 32)
+        with pytest.raises(alp.AlpError):
+            alp.alp_batched_set_class_config(4, 48, 64, 16)
+        with pytest.raises(alp.AlpError):
+            alp.alp_batched_set_class_config(9, 64, 64, 16)
+    finally:
+        alp.alp_batched_set_class_config(4, *old)
+    import numpy as np
+    hM = np.array([4, 5], dtype=np.int64)
+    assert alp.alp_gemm_batched_workspace(2, hM, hM, hM) > 0
+    assert alp.alp_gemm_batched_workspace(2, np.array([4, -1], dtype=np.int64), hM, hM) == 0

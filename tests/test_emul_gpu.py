@@ -119,6 +119,21 @@ def test_emul_worst_case_digits_exact(alp, orc):
     assert np.array_equal(got, ref)
 
 
+def test_emul_extreme_exponents(alp, orc):
+    """Rows and columns scaled far apart: results that underflow to
+    subnormals (one rounding) or overflow to infinity, bit-exact."""
+    M, N, K = 70, 90, 50
+    A, B, C = inputs.gemm_operands(3500, M, N, K)
+    A[:20] *= 2.0 ** -1000
+    B[:, :30] *= 2.0 ** -60
+    A[20:40] *= 2.0 ** 900
+    B[:, 30:60] *= 2.0 ** 200
+    got, st, err = run_emul(alp, A, B, C, 1.0, 0.0, 8)
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8)
+    assert np.array_equal(got, ref)
+    assert np.isinf(got).any() and (np.abs(got[:20, :30]) < 2.0 ** -1022).all()
+
+
 def test_emul_integer_inputs_exact(alp, orc):
     M = N = K = 512
     A, B, _ = inputs.gemm_operands(inputs.workload_seed("dgemm_512"), M, N, K, kind="int",

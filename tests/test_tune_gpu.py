@@ -1,0 +1,89 @@
+"""Autotuner (alp_tune through the C-ABI): exhaustive sweep, database, cache,
+timing proxy, prediction, and what the learned cost model gains over tuning
+without it."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1706_10086_gb300 import inputs, tuning
+
+pytestmark = pytest.mark.gpu
+
+
+def test_exhaustive_sweep_db_and_lookup(alp, tmp_path):
+    db = str(tmp_path / "db.jsonl")
+    os.environ["ALP_TUNE_DB"] = db
+    os.environ["ALP_TUNE_RUNS"] = "2"
+    try:
+        alp.alp_tune_clear_cache()
+        st, cfg, tf = alp.alp_tune(300, 200, 100, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_EXHAUSTIVE)
+        assert alp.alp_config_valid(cfg) and tf > 0
+        recs = tuning.load_db(db)
+        assert len(recs) == 1 and recs[0]["M"] == 300 and recs[0]["path"] == "native"
+        rows = recs[0]["configs"]
+        assert len(rows) == alp.alp_config_count(alp.ALP_PATH_NATIVE)
+        est = [r[6] for r in rows]
+        assert tuple(rows[recs[0]["winner"]][:6]) == cfg.astuple()
+        assert min(est) == est[recs[0]["winner"]]
+        st, cfg2, _ = alp.alp_tune(300, 200, 100, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_LOOKUP)
+        assert cfg2.astuple() == cfg.astuple()
+        st, _, _ = alp.alp_tune(301, 200, 100, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_LOOKUP,
+                                raise_on_error=False)
+        assert st == alp.ALP_ERR_NOT_TUNED
+        st, ecfg, _ = alp.alp_tune(256, 512, 300, alp.ALP_PATH_EMUL, alp.ALP_TUNE_EXHAUSTIVE)
+        assert alp.alp_config_valid(ecfg, alp.ALP_PATH_EMUL)
+        assert tuning.load_db(db)[-1]["path"] == "emul"
+        # resume: collect skips what is present
+        assert tuning.collect([(300, 200, 100)], ["native"], db) == 0
+    finally:
+        os.environ.pop("ALP_TUNE_DB", None)
+        alp.alp_tune_clear_cache()
+
+
+def test_timing_proxy_tracks_full_runs(alp):
+    """The one-wave, K <= 256 proxy against whole-problem timings."""
+    for (M, N, K) in [(2048, 2048, 1024), (4096, 1024, 2048), (1000, 3000, 700)]:
+        for cfg in [(128, 128, 16, 8, 8, 0), (64, 64, 16, 4, 4, 0)]:
+            est = alp.alp_tune_time_config(M, N, K, alp.ALP_PATH_NATIVE, cfg, True, 3)
+            full = alp.alp_tune_time_config(M, N, K, alp.ALP_PATH_NATIVE, cfg, False, 2)
+            assert abs(est / full - 1) < 0.15, (M, N, K, cfg, est, full)
+
+
+def test_predict_needs_model(alp):
+    alp.alp_tune_unload_model()
+    st, _, _ = alp.alp_tune(512, 512, 512, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_PREDICT,
+                            raise_on_error=False)
+    assert st == alp.ALP_ERR_NOT_TUNED
+
+
+def test_learned_model_beats_tuning_without_it(alp, tmp_path):
+    """Small-scale version of the predictor workload: sweep 90 training and 30
+    held-out shapes (native path), train the MLP on the GPU, and compare the
+    regret of its choices with one config tuned once and with the nearest
+    training shape's winner."""
+    db = str(tmp_path / "db.jsonl")
+    seed = inputs.workload_seed("mlp_predictor")
+    train_sh = inputs.shapes(seed, 90, 64, 2048)
+    test_sh = inputs.shapes(seed + 100, 30, 64, 2048)
+    tuning.collect(train_sh, ["native"], db, runs=2)
+    recs = tuning.load_db(db)
+    train_ds = tuning.dataset(recs)
+    tuning.collect(test_sh, ["native"], db, runs=2)
+    test_keys = {tuple(int(v) for v in s) for s in test_sh}
+    test_ds = tuning.dataset([r for r in tuning.load_db(db)
+                              if (r["M"], r["N"], r["K"]) in test_keys])
+    model, hist = tuning.train(train_ds, epochs=1500, lr=3e-3)
+    assert hist[-1] < hist[0]
+    res = tuning.evaluate(model, train_ds, test_ds, tuning_shape=(2048, 2048, 2048))
+    print(json.dumps(res))
+    assert res["mlp"]["mean"] < res["fixed_tuned_once"]["mean"]
+    # the model drives PREDICT and cfg == NULL calls
+    params, mean, std = model
+    alp.alp_tune_load_model(params, train_ds["C"], mean, std)
+    try:
+        st, cfg, _ = alp.alp_tune(700, 300, 900, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_PREDICT)
+        assert alp.alp_config_valid(cfg)
+    finally:
+        alp.alp_tune_unload_model()
