@@ -240,15 +240,18 @@ bool model_predict(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* o
         g_model.d_shape = nullptr;
         // one-time upload of the model to this device
         if (cudaMalloc(&g_model.d_params, param_count(C) * 4) != cudaSuccess ||
-            cudaMalloc(&g_model.d_scratch, (kF * 2 + C + 2 * kH) * 4) != cudaSuccess ||
+            cudaMalloc(&g_model.d_scratch, (kF + C + 2 * kH + 2 * kF) * 4) != cudaSuccess ||
             cudaMalloc(&g_model.d_shape, 4 * 8) != cudaSuccess)
             return false;
-        cudaMemcpy(g_model.d_params, g_model.params.data(), param_count(C) * 4,
-                   cudaMemcpyHostToDevice);
         float ms[2 * kF];
         std::memcpy(ms, g_model.mean, sizeof g_model.mean);
         std::memcpy(ms + kF, g_model.stdv, sizeof g_model.stdv);
-        cudaMemcpy(g_model.d_scratch + kF + C + 2 * kH, ms, sizeof ms, cudaMemcpyHostToDevice);
+        // scratch layout: X (7) | Y (C) | cache (128) | mean, std (14)
+        if (cudaMemcpy(g_model.d_params, g_model.params.data(), param_count(C) * 4,
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g_model.d_scratch + kF + C + 2 * kH, ms, sizeof ms,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
         g_model.dev = dev;
     }
     float* X = g_model.d_scratch;

@@ -238,8 +238,12 @@ alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t
 }
 
 // Blocks of this config that fit on one SM (0: cannot launch on this GPU).
+// Failed queries are consumed so that no CUDA error is left pending.
 int native_occupancy(const alp_config& cfg, bool use_tma) {
     const int stages = native_stages(cfg.bm, cfg.bn, cfg.bk, cfg.stages);
+    const int64_t need = use_tma ? native_stage_bytes(cfg.bm, cfg.bn, cfg.bk) * stages + 16 * stages + 16
+                                 : native_stage_bytes(cfg.bm, cfg.bn, cfg.bk) * 2;
+    if (need > kSmemLimit) return 0;
     int n = 0;
 #define ALP_OCC_CASE(a, b)                                                                        \
     if (cfg.tm == a && cfg.tn == b) {                                                             \
@@ -262,6 +266,7 @@ int native_occupancy(const alp_config& cfg, bool use_tma) {
     ALP_OCC_CASE(4, 2) ALP_OCC_CASE(4, 4) ALP_OCC_CASE(4, 8)
     ALP_OCC_CASE(8, 2) ALP_OCC_CASE(8, 4) ALP_OCC_CASE(8, 8)
 #undef ALP_OCC_CASE
+    cudaGetLastError();
     return n;
 }
 
