@@ -81,15 +81,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // block of any launch has already recorded ALP_ERR_TIMEOUT, so that a broken
 // launch ends after one limit rather than one limit per wave), records
 // ALP_ERR_TIMEOUT and returns false; the caller then leaves its loop.
+// Waits that make sure a block's own copies or MMAs have finished before it
+// frees shared memory or TMEM pass follow_global = false: they always wait for
+// the barrier itself (or their own limit).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns, volatile int* abort,
-                                                  int* err) {
+                                                  int* err, bool follow_global = true) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort && *abort) return false;
-        if (err && *reinterpret_cast<volatile int*>(err) == ALP_ERR_TIMEOUT) {
+        if (follow_global && err && *reinterpret_cast<volatile int*>(err) == ALP_ERR_TIMEOUT) {
             if (abort) *abort = 1;
             return false;
         }

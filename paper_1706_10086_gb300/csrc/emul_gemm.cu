@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // every copy issued must land before the block may exit
             for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
-                mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err);
+                mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err,
+                                  false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // all MMAs must have completed before TMEM and shared memory go away
             umma_commit(done);
-            mbar_wait_bounded(done, 0, tmo, nullptr, prm.err);
+            mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
         }
     } else {
         // ---------------- epilogue: TMEM -> exact int32 group sums ----------------

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(max_threads(TM, TN), 1)
                 if (kt == skipped) continue;
                 const int s = (int)(kt % S);
                 const uint32_t round = (uint32_t)(kt / S);
-                mbar_wait_bounded(&full[s], round & 1, p.timeout_ns, nullptr, p.err);
+                mbar_wait_bounded(&full[s], round & 1, p.timeout_ns, nullptr, p.err, false);
             }
         }
         return;
