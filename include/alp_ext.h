@@ -130,6 +130,28 @@ alp_status alp_batched_graph_create(int64_t count, const int64_t* dM, const int6
 alp_status alp_batched_graph_launch(void* graph, void* stream);
 alp_status alp_batched_graph_destroy(void* graph);
 
+/* Same computation as alp_gemm_batched_varsize (same arguments minus the
+ * workspace), for callers that cannot allocate device memory where they issue
+ * the GEMM: code running during CUDA graph capture, frameworks whose device
+ * memory belongs to their own pool, loops that must not enter the allocator.
+ * The paper has no counterpart; this is an interface convenience.
+ * The persistent kernel's work list lives in a 1 MiB array compiled into the
+ * library (held on every GPU that loads it until the process exits), so
+ * count is limited to about 65,000 problems: larger batches return
+ * ALP_ERR_WORKSPACE and must use alp_gemm_batched_varsize.  Nothing is
+ * allocated.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and each call rewrites it completely, so no
+ * clearing is needed between calls, but two calls whose kernels overlap on
+ * the GPU (e.g. on different streams without ordering) race on it. */
+alp_status alp_gemm_batched_varsize_noalloc(int64_t count, const int64_t* dM, const int64_t* dN,
+                                            const int64_t* dK, const double* dalpha,
+                                            const double* const* dA, const int64_t* dlda,
+                                            const double* const* dB, const int64_t* dldb,
+                                            const double* dbeta, double* const* dC,
+                                            const int64_t* dldc, const int64_t* hM,
+                                            const int64_t* hN, const int64_t* hK, void* stream);
+
 /* ---- FP64 peak probe ----------------------------------------------------- */
 
 /* Measured FP64 throughput of this GPU: kind 0 = m16n8k4 DMMA chains (the

@@ -104,6 +104,8 @@ _SIGS = {
                                   _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                   ctypes.POINTER(_vp)], _int),
     "alp_batched_graph_launch": ([_vp, _vp], _int),
+    "alp_gemm_batched_varsize_noalloc": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          _vp, _vp, _vp, _vp, _vp, _vp], _int),
     "alp_batched_graph_destroy": ([_vp], _int),
 }
 
@@ -384,3 +386,14 @@ def alp_tune_load_model(host_params, C, host_mean, host_std):
 
 def alp_tune_unload_model():
     return _check(lib().alp_tune_unload_model(), "alp_tune_unload_model", True)
+
+
+def alp_gemm_batched_varsize_noalloc(count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC,
+                                     dldc, hM, hN, hK, stream=None, raise_on_error=True):
+    """alp_gemm_batched_varsize without a workspace argument: the library's
+    built-in 1 MiB scratch holds the work list (no device allocation)."""
+    st = lib().alp_gemm_batched_varsize_noalloc(count, _p(dM), _p(dN), _p(dK), _p(dalpha),
+                                                _p(dA), _p(dlda), _p(dB), _p(dldb), _p(dbeta),
+                                                _p(dC), _p(dldc), _host(hM), _host(hN),
+                                                _host(hK), _s(stream))
+    return _check(st, "alp_gemm_batched_varsize_noalloc", raise_on_error)

@@ -398,3 +398,95 @@ alp_status alp_batched_graph_destroy(void* graph) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched GEMM without a caller-provided workspace.
+//
+// Some callers cannot allocate device memory at the point where they issue
+// the GEMM: code that runs while a CUDA graph is being captured (an
+// allocation there is either forbidden or becomes part of the graph),
+// frameworks whose device memory is owned by their own pool allocator, and
+// real-time loops that must not take the allocator's locks or trigger a
+// device synchronisation.  For them this entry point keeps the work list of
+// the persistent kernel in one file-scope device array instead of a
+// workspace.  The array is part of the library image: every GPU that loads
+// the library holds these kNoAllocScratchBytes until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;   // 1 MiB: up to 65,000 problems
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64];   // device address of g_noalloc_scratch per device (nullptr: not set up)
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up (cudaGetSymbolAddress, which allocates nothing);
+// later calls reuse it.
+alp_status noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ALP_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ALP_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ALP_OK;
+}
+}  // namespace
+
+extern "C" alp_status alp_gemm_batched_varsize_noalloc(
+    int64_t count, const int64_t* dM, const int64_t* dN, const int64_t* dK, const double* dalpha,
+    const double* const* dA, const int64_t* dlda, const double* const* dB, const int64_t* dldb,
+    const double* dbeta, double* const* dC, const int64_t* dldc, const int64_t* hM,
+    const int64_t* hN, const int64_t* hK, void* stream) {
+    alp_status st = check_host_sizes(count, hM, hN, hK);
+    if (st != ALP_OK) return st;
+    if (count == 0) return ALP_OK;
+    if (plan_layout(count).bytes > kNoAllocScratchBytes) return ALP_ERR_WORKSPACE;   // too many problems
+    BatchArgs a;
+    if ((st = fill_args(a, count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC, dldc)) !=
+        ALP_OK)
+        return st;
+    void* scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch)) != ALP_OK) return st;
+    // The plan kernel rewrites every part of the scratch it later reads
+    // (keys, order, prefix sums, counts, and the tile counter it sets to 0), so
+    // the previous call's contents need no clearing.
+    const ClassTable tab = current_table();
+    const PlanLayout L = plan_layout(count);
+    char* ws = static_cast<char*>(scratch);
+    Plan pl;
+    pl.key = reinterpret_cast<int32_t*>(ws + L.off_key);
+    pl.order = reinterpret_cast<int32_t*>(ws + L.off_order);
+    pl.prefix = reinterpret_cast<int64_t*>(ws + L.off_prefix);
+    pl.meta = reinterpret_cast<int64_t*>(ws + L.off_meta);
+    pl.counter = reinterpret_cast<unsigned long long*>(ws + L.off_counter);
+    int64_t tiles = 0;
+    for (int64_t p = 0; p < count; ++p) {
+        if (hM[p] <= 0 || hN[p] <= 0) continue;
+        const int c = class_of(hM[p], hN[p]);
+        tiles += ((hM[p] + tab.bm[c] - 1) / tab.bm[c]) * ((hN[p] + tab.bn[c] - 1) / tab.bn[c]);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    batched_plan_kernel<<<1, kPlanThreads, 0, s>>>(a, pl, tab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tiles == 0) return ALP_OK;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return ALP_ERR_CUDA;
+    const int smem = max_smem(tab);
+    e = cudaFuncSetAttribute(batched_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_persistent_kernel, kBatchedThreads,
+                                                  smem);
+    if (occ < 1) occ = 1;
+    int64_t grid = (int64_t)sms * occ;
+    if (grid > tiles) grid = tiles;
+    batched_persistent_kernel<<<(unsigned)grid, kBatchedThreads, smem, s>>>(a, pl, tab);
+    return cuda_status(cudaGetLastError());
+}
