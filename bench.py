@@ -3,8 +3,10 @@
 
 Workload (default): C = alpha*A*B + beta*C with M = N = K = 8192, FP64
 row-major operands u * 2^e (u uniform in [-1,1), e uniform in [-phi, phi],
-phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path with 8
-BF16 digit slices (the slice count whose error is no worse than native FP64).
+phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path with 7
+BF16 digit slices: for these inputs its largest elementwise error relative to
+|A||B| is no worse than the native FP64 kernel's, which the run checks over
+the whole result (the "accuracy" object).
 One step = one full emulated GEMM: exponent scans, digit splits, the
 tensor-core slice products and the exact recombination -- the same kernels
 alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
@@ -48,17 +50,25 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--nslices", type=int, default=8)
+    ap.add_argument("--nslices", type=int, default=7,
+                    help="digit slices; 7 is no less accurate than native FP64 for the default "
+                         "uniform inputs (checked live against 8 slices), 8 for wide exponent "
+                         "ranges")
     ap.add_argument("--phi", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-native", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", choices=("emul8192", "batched"), default="emul8192",
-                    help="emul8192 (default, the headline) or batched (4096 variable-size "
-                         "problems, persistent graph launch vs a loop of launches)")
+    ap.add_argument("--workload", choices=("emul8192", "batched", "native_scan"),
+                    default="emul8192",
+                    help="emul8192 (default, the headline), batched (4096 variable-size "
+                         "problems, persistent graph launch vs a loop of launches) or "
+                         "native_scan (native FP64 GEMM at N = 1024..16384, default and "
+                         "autotuned config)")
     ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched: keep the default class tiles instead of autotuning them")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no API check, native, e2e or CPU legs): for ncu")
     a = ap.parse_args()
@@ -227,24 +237,29 @@ def run_alp(args):
     f = torch.empty(N, dtype=torch.int32, device=dev)
     launches_per_step = 7   # scan rows, scan cols (2), split A, split B, slice products, recombine
 
-    def step(ev_k0=None, ev_k1=None):
+    def step(ev=None):
+        # ev: 7 events bracketing the six stages (None: no timing)
+        rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        rec(0)
         alp.alp_emul_exponents(M, K, A, K, 0, e, stream)
+        rec(1)
         alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
+        rec(2)
         alp.alp_emul_split(M, K, A, K, 0, e, s, da, kpad, stream)
+        rec(3)
         alp.alp_emul_split(N, K, B, N, 1, f, s, db, kpad, stream)
-        if ev_k0 is not None:
-            ev_k0.record(stream)
+        rec(4)
         alp.alp_emul_slice_products(M, N, K, s, da, db, kpad, G, ldg, stream)
-        if ev_k1 is not None:
-            ev_k1.record(stream)
+        rec(5)
         alp.alp_emul_recombine(M, N, s, G, ldg, e, f, alpha, beta, C, N, stream)
+        rec(6)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     assert alp.alp_get_device_error(stream) == alp.ALP_OK
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -255,17 +270,19 @@ def run_alp(args):
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for i in range(args.steps):
-        ev[i][0].record(stream)
-        step(ev[i][1], ev[i][2])
-        ev[i][3].record(stream)
+        step(ev[i])
     t_end.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    step_ms = [ev[i][0].elapsed_time(ev[i][3]) for i in range(args.steps)]
-    kern_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    step_ms = [ev[i][0].elapsed_time(ev[i][6]) for i in range(args.steps)]
+    kern_ms = [ev[i][4].elapsed_time(ev[i][5]) for i in range(args.steps)]
+    stage_names = ("scan_rows", "scan_cols", "split_A", "split_B", "slice_products", "recombine")
+    stage_ms = {nm: round(statistics.median(ev[i][k].elapsed_time(ev[i][k + 1])
+                                            for i in range(args.steps)), 4)
+                for k, nm in enumerate(stage_names)}
     assert alp.alp_get_device_error(stream) == alp.ALP_OK
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -297,6 +314,7 @@ def run_alp(args):
                       "result_dtype": "f64", "parallelism": f"replicas{ws}",
                       "l2": "inputs 1.5 GB > 129 MB L2; no flush"},
            "step_ms_median": round(statistics.median(step_ms), 3),
+           "stage_ms_median": stage_ms,
            "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk}
 
@@ -370,6 +388,33 @@ def run_alp(args):
                                                      "SMs, measured in this run)"},
                          "emulated_speedup": round(value / ws / nat_tf, 2)}
 
+    if not args.no_native:
+        # accuracy of this run's emulated result, over every element: against 8
+        # slices (within 0.1 u of the long-double oracle on sampled rows) and
+        # relative to |A||B| from the native kernel; the native result likewise
+        C8 = torch.empty_like(C)
+        ws8 = alp.alp_gemm_f64_emul_workspace(M, N, K, 8, alp.ALP_SLICE_BF16)
+        work8 = torch.empty(ws8, dtype=torch.uint8, device=dev)
+        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, C8, N, 8, alp.ALP_SLICE_BF16,
+                              work8, ws8, stream)
+        del work8
+        Cs = torch.empty_like(C)
+        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, Cs, N, s, alp.ALP_SLICE_BF16, work,
+                              wsb, stream)
+        Cn = torch.empty_like(C)
+        alp.alp_gemm_f64(M, N, K, alpha, A, K, B, N, 0.0, Cn, N, stream=stream)
+        absAB = torch.empty_like(C)
+        alp.alp_gemm_f64(M, N, K, 1.0, A.abs(), K, B.abs(), N, 0.0, absAB, N, stream=stream)
+        torch.cuda.synchronize()
+        u = 2.0 ** -53
+        out["accuracy"] = {
+            "reference": "8 slices (within 0.1 u of the long-double oracle on sampled rows)",
+            "emulated_max_componentwise_u": float(((Cs - C8).abs() / absAB).max()) / u,
+            "native_max_componentwise_u": float(((Cn - C8).abs() / absAB).max()) / u,
+            "emulated_normwise": float(torch.linalg.norm(Cs - C8) / torch.linalg.norm(C8)),
+            "native_normwise": float(torch.linalg.norm(Cn - C8) / torch.linalg.norm(C8))}
+        del C8, Cs, Cn, absAB
+
     if rank == 0 and ws == 1 and not args.no_cpu:
         # CPU baseline: the long-double oracle on a bounded sample of rows
         rows = 64
@@ -416,7 +461,8 @@ def run_reference(args):
            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double accumulation)",
            "data": "synthetic (seeded SplitMix64, uniform [-1,1))",
-           "config": {"workload": f"emulated_dgemm_{n}_bf16x8slices_phi0", "M": n, "N": n,
+           "config": {"workload": f"emulated_dgemm_{n}_bf16x{args.nslices}slices_phi{args.phi}",
+                      "M": n, "N": n,
                       "K": n, "sample_rows_per_step": rows_per_step},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                             "sample": f"{rows_per_step} rows of the {n}^3 product per step"},
@@ -457,6 +503,13 @@ def run_batched(args):
     dA, dB, dC = t(pA), t(pB), t(pC)
     dlda, dldb, dldc = t(K), t(N), t(N)
     flops = float(np.sum(2.0 * M * N * K))
+    tuned = None
+    if not args.no_tune:
+        # per-size-class tiles from the autotuner (outside the timed region)
+        from paper_1706_10086_gb300 import tuning
+        res = tuning.tune_batched_classes(M, N, K, pA, pB, pC, runs=2)
+        tuned = {int(c): list(v[0]) for c, v in res.items()}
+        bufC.copy_(bufC0)
     ws = alp.alp_gemm_batched_workspace(n, M, N, K)
     work = torch.empty(ws, dtype=torch.uint8, device=dev)
     graph = alp.alp_batched_graph_create(n, dM, dN, dK, dal, dA, dlda, dB, dldb, dbe, dC, dldc,
@@ -512,10 +565,50 @@ def run_batched(args):
                                 "tflops": round(flops / (ms_loop * 1e-3) / 1e12, 4)},
            "loop_of_launches_graph": {"ms": round(ms_loop_graph, 3),
                                       "tflops": round(flops / (ms_loop_graph * 1e-3) / 1e12, 4)},
+           "class_tiles": tuned if tuned is not None else "defaults",
            "speedup_vs_loop": round(ms_loop / ms_graph, 3),
            "speedup_vs_loop_graph": round(ms_loop_graph / ms_graph, 3),
            "gpu_launches": 2 * args.steps, "clocks": clk}
     print(json.dumps(out), flush=True)
+
+
+def run_native_scan(args):
+    """Native DGEMM size scan: square N in {1024, ..., 16384}, U[-1,1), alpha =
+    1.5, beta = 0.5; the default config and the autotuner's pick, each timed on
+    the full problem (best of 3 after a warm-up, CUDA events)."""
+    import torch
+
+    from paper_1706_10086_gb300 import alp
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1706 + 1)
+    peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
+    rows = []
+    for n in (1024, 2048, 4096, 8192, 16384):
+        A = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        B = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        C = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        _, tuned, _ = alp.alp_tune(n, n, n, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_EXHAUSTIVE)
+        res = {"N": n, "tuned_config": list(tuned.astuple())}
+        for name, cfg in (("untuned_128x128", (128, 128, 16, 8, 8, 0)), ("tuned", tuned)):
+            times = []
+            alp.alp_gemm_f64(n, n, n, 1.5, A, n, B, n, 0.5, C, n, cfg=cfg, stream=stream)
+            for _ in range(3 if n <= 8192 else 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                alp.alp_gemm_f64(n, n, n, 1.5, A, n, B, n, 0.5, C, n, cfg=cfg, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            tf = 2.0 * n ** 3 / (min(times) * 1e-3) / 1e12
+            res[name] = {"ms": round(min(times), 3), "tflops": round(tf, 4),
+                         "frac_of_fp64_peak": round(tf / peak, 4)}
+        rows.append(res)
+        del A, B, C
+    print(json.dumps({"metric": "native FP64 GEMM TFLOP/s, size scan", "unit": UNIT,
+                      "fp64_dmma_peak_measured": round(peak, 4), "alpha": 1.5, "beta": 0.5,
+                      "rows": rows}), flush=True)
 
 
 def main():
@@ -524,6 +617,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "native_scan":
+        run_native_scan(args)
     else:
         run_alp(args)
 

@@ -20,7 +20,10 @@ extern "C" {
  * {64,128,256}; bk in {16,32,64}; tm, tn in {2,4,8}; one producer warp plus
  * (bm/(8 tm)) * (bn/(4 tn)) compute warps within the per-(tm,tn) thread cap
  * that keeps the register tile resident; at least 2 stages of
- * (bm+bn)*bk*8 bytes within 227 KiB of shared memory. */
+ * (bm+bn)*bk*8 bytes within 227 KiB of shared memory.  Emulated path:
+ * {128, 256, 64, cluster, 0, group} with cluster in {1, 2} (blocks sharing each
+ * B tile through multicast) and group in {1, 2, 4, 8, 16, 32} (tile-rows per
+ * raster group). */
 int alp_config_valid(const alp_config* cfg, alp_path path);
 
 /* Shared-memory bytes of the A and B tiles of all stages: stages*(bm+bn)*bk*8

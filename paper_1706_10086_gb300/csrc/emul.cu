@@ -110,7 +110,7 @@ __global__ void zero_empty_columns_kernel(int64_t N, int32_t* __restrict__ f) {
 // that last bit, so the digits equal those of the exact value (s*7 <= 56).
 // Each step is d = round-half-even(X / 2^55), X = (X - d 2^55) * 2^7, which is
 // x = r * 2^7, d = nearest integer (ties to even), r = x - d in fixed point.
-__device__ __forceinline__ void split_digits(double a, int e, int s, int (&d)[kMaxSlices]) {
+__device__ __forceinline__ uint64_t fixed_point_r0(double a, int e) {
     const uint64_t bits = (uint64_t)__double_as_longlong(a);
     const bool neg = (bits >> 63) != 0;
     const int ex = (int)((bits >> 52) & 0x7FF);
@@ -133,31 +133,36 @@ __device__ __forceinline__ void split_digits(double a, int e, int s, int (&d)[kM
         const int r = -sh;
         Y = (m >> r) | ((m & ((1ull << r) - 1)) != 0 ? 1ull : 0ull);
     } else Y = 1;   // nonzero but below 2^-62: sticky bit only
-    uint64_t X = neg ? (0ull - Y) : Y;   // two's complement of the signed value
+    return neg ? (0ull - Y) : Y;   // two's complement of the signed value
+}
+
+template <int S>
+__device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
+    uint64_t X = fixed_point_r0(a, e);
 #pragma unroll
-    for (int p = 0; p < kMaxSlices; ++p) {
-        if (p < s) {
-            const int64_t q = ((int64_t)X) >> 55;
-            const uint64_t rem = X & ((1ull << 55) - 1);
-            const int64_t dd = q + ((rem > (1ull << 54)) || (rem == (1ull << 54) && (q & 1)) ? 1 : 0);
-            d[p] = (int)dd;
-            X = (X - ((uint64_t)dd << 55)) << 7;
-        } else {
-            d[p] = 0;
-        }
+    for (int p = 0; p < S; ++p) {
+        const int64_t q = ((int64_t)X) >> 55;
+        const uint64_t rem = X & ((1ull << 55) - 1);
+        const int64_t dd = q + ((rem > (1ull << 54)) || (rem == (1ull << 54) && (q & 1)) ? 1 : 0);
+        d[p] = (int)dd;
+        X = (X - ((uint64_t)dd << 55)) << 7;
     }
 }
 
+// Two digits (|v| <= 256) as packed bf16: the float 1.5*2^23 + v - 1.5*2^23
+// is exactly v, and its upper 16 bits are its bf16 encoding (at most 9
+// significant bits), so no conversion instruction is needed.
 __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-    // integers with |v| <= 256 are exact in bf16
-    const __nv_bfloat16 a = __int2bfloat16_rn(lo), b = __int2bfloat16_rn(hi);
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    const float fl = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+    const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+    return __byte_perm((uint32_t)__float_as_int(fl), (uint32_t)__float_as_int(fh), 0x7632);
 }
 
 // A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
 // thread handles two consecutive k.
+template <int S>
 __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K,
-                                  int64_t ldx, const int32_t* __restrict__ e, int s,
+                                  int64_t ldx, const int32_t* __restrict__ e,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
     const int64_t half = kpad >> 1;
     const int64_t total = R * half;
@@ -167,20 +172,20 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
         const int64_t r = idx / half;
         const int64_t k = (idx - r * half) * 2;
         const int er = e[r];
-        int d0[kMaxSlices], d1[kMaxSlices];
-        split_digits(k < K ? __ldg(X + r * ldx + k) : 0.0, er, s, d0);
-        split_digits(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, s, d1);
+        int d0[S], d1[S];
+        split_digits<S>(k < K ? __ldg(X + r * ldx + k) : 0.0, er, d0);
+        split_digits<S>(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, d1);
         uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
 #pragma unroll
-        for (int p = 0; p < kMaxSlices; ++p)
-            if (p < s) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
     }
 }
 
 // B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
 // shared memory so that reads run along j and writes along k.
+template <int S>
 __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N,
-                                  int64_t ldx, const int32_t* __restrict__ f, int s,
+                                  int64_t ldx, const int32_t* __restrict__ f,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
     __shared__ double t[32][65];
     const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
@@ -197,15 +202,14 @@ __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64
         const int64_t j = j0 + jj;
         if (j >= N) continue;
         const int fj = f[j];
-        int d0[kMaxSlices], d1[kMaxSlices];
-        split_digits(t[jj][2 * tx], fj, s, d0);
-        split_digits(t[jj][2 * tx + 1], fj, s, d1);
+        int d0[S], d1[S];
+        split_digits<S>(t[jj][2 * tx], fj, d0);
+        split_digits<S>(t[jj][2 * tx + 1], fj, d1);
         const int64_t k = k0 + 2 * tx;
         if (k >= kpad) continue;
         uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
 #pragma unroll
-        for (int p = 0; p < kMaxSlices; ++p)
-            if (p < s) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
     }
 }
 
@@ -250,33 +254,63 @@ __device__ __forceinline__ double int128_scaled_to_double_rn(unsigned __int128 x
 }
 
 // One block row of threads per matrix row chunk: rows from blockIdx.y (grid
-// stride), columns from the x dimension (no integer division per element).
+// stride), two columns per thread from the x dimension (no integer division
+// per element).  The slice count is a template parameter so that the S loads
+// are independent and the sum is a Horner chain, X = X * 2^7 + S^t.
+template <int S>
+__device__ __forceinline__ double recombine_one(const int32_t* __restrict__ g, int64_t gplane,
+                                                int E) {
+    int32_t v[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) v[t] = __ldg(g + (int64_t)t * gplane);
+    unsigned __int128 X = (unsigned __int128)(__int128)v[0];
+#pragma unroll
+    for (int t = 1; t < S; ++t) X = (X << kDigitBits) + (unsigned __int128)(__int128)v[t];
+    return int128_scaled_to_double_rn(X, E);
+}
+
+template <int S>
 __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, int64_t ldg,
-                                 int s, const int32_t* __restrict__ e,
-                                 const int32_t* __restrict__ f, int64_t M, int64_t N,
-                                 double alpha, double beta, double* __restrict__ C, int64_t ldc) {
-    const int shift0 = (s + 1) * kDigitBits;
+                                 const int32_t* __restrict__ e, const int32_t* __restrict__ f,
+                                 int64_t M, int64_t N, double alpha, double beta,
+                                 double* __restrict__ C, int64_t ldc) {
+    const int shift0 = (S + 1) * kDigitBits;
     for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
-        const int ei = e[i];
+        const int ei = e[i] - shift0;
         const int32_t* gi = G + i * ldg;
         double* ci = C + i * ldc;
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            unsigned __int128 X = 0;
-            for (int t = 2; t <= s + 1; ++t) {
-                const int64_t S = __ldg(gi + (int64_t)(t - 2) * gplane + j);
-                X += ((unsigned __int128)(__int128)S) << ((s + 1 - t) * kDigitBits);
+        for (int64_t j = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N;
+             j += 2 * (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t jj = j + u;
+                if (jj >= N) break;
+                const double w = recombine_one<S>(gi + jj, gplane, ei + __ldg(f + jj));
+                double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
+                if (beta != 0.0) out = __fma_rn(beta, ci[jj], out);
+                ci[jj] = out;
             }
-            const double w = int128_scaled_to_double_rn(X, ei + __ldg(f + j) - shift0);
-            double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
-            if (beta != 0.0) out = __fma_rn(beta, ci[j], out);
-            ci[j] = out;
         }
     }
 }
 
+static alp_status launch_recombine(int s, dim3 grid, cudaStream_t st, const int32_t* G,
+                                   int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
+                                   int64_t M, int64_t N, double alpha, double beta, double* C,
+                                   int64_t ldc) {
+#define ALP_RECOMBINE_CASE(x) \
+    case x: recombine_kernel<x><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc); break;
+    switch (s) {
+        ALP_RECOMBINE_CASE(1) ALP_RECOMBINE_CASE(2) ALP_RECOMBINE_CASE(3) ALP_RECOMBINE_CASE(4)
+        ALP_RECOMBINE_CASE(5) ALP_RECOMBINE_CASE(6) ALP_RECOMBINE_CASE(7) ALP_RECOMBINE_CASE(8)
+        default: return ALP_ERR_INVALID_ARG;
+    }
+#undef ALP_RECOMBINE_CASE
+    return cuda_status(cudaGetLastError());
+}
+
 static dim3 recombine_grid(int64_t M, int64_t N) {
-    const int64_t bx = (N + 255) / 256;
+    const int64_t bx = (N + 511) / 512;
     int64_t by = (int64_t)device_sm_count() * 16 / (bx > 0 ? bx : 1);
     if (by < 1) by = 1;
     if (by > M) by = M;
@@ -332,13 +366,21 @@ alp_status emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t l
 alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
                       const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
                       cudaStream_t st) {
-    if (!trans) {
-        split_rows_kernel<<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(X, R, K, ldx, exps, s,
-                                                                        out, kpad);
-    } else {
-        dim3 grid((unsigned)((R + 31) / 32), (unsigned)(kpad / 64));
-        split_cols_kernel<<<grid, 256, 0, st>>>(X, K, R, ldx, exps, s, out, kpad);
+#define ALP_SPLIT_CASE(x)                                                                        \
+    case x:                                                                                      \
+        if (!trans)                                                                              \
+            split_rows_kernel<x><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(X, R, K, ldx,    \
+                                                                               exps, out, kpad); \
+        else                                                                                     \
+            split_cols_kernel<x><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)), 256,   \
+                                   0, st>>>(X, K, R, ldx, exps, out, kpad);                      \
+        break;
+    switch (s) {
+        ALP_SPLIT_CASE(1) ALP_SPLIT_CASE(2) ALP_SPLIT_CASE(3) ALP_SPLIT_CASE(4)
+        ALP_SPLIT_CASE(5) ALP_SPLIT_CASE(6) ALP_SPLIT_CASE(7) ALP_SPLIT_CASE(8)
+        default: return ALP_ERR_INVALID_ARG;
     }
+#undef ALP_SPLIT_CASE
     return cuda_status(cudaGetLastError());
 }
 
@@ -399,9 +441,8 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, const int32_t* 
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
-    recombine_kernel<<<recombine_grid(M, N), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        G, M * ldg, ldg, nslices, e, f, M, N, alpha, beta, C, ldc);
-    return cuda_status(cudaGetLastError());
+    return launch_recombine(nslices, recombine_grid(M, N), reinterpret_cast<cudaStream_t>(stream),
+                            G, M * ldg, ldg, e, f, M, N, alpha, beta, C, ldc);
 }
 
 alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -431,13 +472,12 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s)) != ALP_OK) return st;
     if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s)) != ALP_OK) return st;
     alp_config cfg;
-    const int group_m = (select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg))
-                            ? cfg.stages : 0;
-    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s, group_m)) != ALP_OK)
+    const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
+    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
+                              have ? cfg.stages : 0, have ? cfg.tm : 0)) != ALP_OK)
         return st;
-    recombine_kernel<<<recombine_grid(M, N), 256, 0, s>>>(G, M * L.ldg, L.ldg, nslices, e, f, M,
-                                                          N, alpha, beta, C, ldc);
-    return cuda_status(cudaGetLastError());
+    return launch_recombine(nslices, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
+                            alpha, beta, C, ldc);
 }
 
 }  // extern "C"

@@ -26,14 +26,16 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s);
 // S^t for t = 2..s+1 into G[(t-2)][M][ldg] (int32), from the digit slices
 // da[s][M][kpad] and db[s][N][kpad] (bf16, K-major).  group_m: tile-rows per
 // raster group (0 = default, the tunable of the emulated path).
+// cluster: blocks per cluster sharing B tiles (1 or 2; 0 = default 1).
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream, int group_m = 0);
+                           cudaStream_t stream, int group_m = 0, int cluster = 0);
 
-// Configs of the emulated path: alp_config{128, 256, 64, 0, 0, group_m} with
-// group_m in {1, 2, 4, 8, 16, 32} (the tile is fixed; the raster group is tuned).
+// Configs of the emulated path: alp_config{128, 256, 64, cluster, 0, group_m}
+// with cluster in {1, 2} (blocks sharing each B tile) and group_m in
+// {1, 2, 4, 8, 16, 32} (tile-rows per raster group); the tile is fixed.
 inline bool emul_config_valid(const alp_config& c) {
-    return c.bm == 128 && c.bn == 256 && c.bk == 64 && c.tm == 0 && c.tn == 0 &&
+    return c.bm == 128 && c.bn == 256 && c.bk == 64 && (c.tm == 1 || c.tm == 2) && c.tn == 0 &&
            (c.stages == 1 || c.stages == 2 || c.stages == 4 || c.stages == 8 || c.stages == 16 ||
             c.stages == 32);
 }

@@ -31,6 +31,20 @@ namespace alp {
 alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1,
                              uint64_t d2, uint32_t box0, uint32_t box1);
 
+// Blocks per cluster sharing B tiles when the config does not say (env
+// ALP_EMUL_CLUSTER: 1 or 2; default 1: sharing B measured no faster at 8192^3).
+static int emul_cluster() {
+    static int c = 0;
+    if (c == 0) {
+        c = 1;
+        if (const char* s = std::getenv("ALP_EMUL_CLUSTER")) {
+            const int v = std::atoi(s);
+            if (v == 1 || v == 2) c = v;
+        }
+    }
+    return c;
+}
+
 // Tile-rows per raster group (env ALP_EMUL_GROUP_M overrides; default 8, the
 // fastest of {1, 4, 8, 16, 32, 64} at 8192^3 on GB300).
 static int emul_group_m() {
@@ -120,6 +134,12 @@ __device__ __forceinline__ void store4_sub_and_zero(int32_t* g, uint32_t bias, u
         : "memory");
 }
 
+// CL = 1: one block per tile.  CL = 2: clusters of two blocks on vertically
+// adjacent tiles (same 256 columns of B); each block loads one 128-row half of
+// the shared B tile and multicasts it to both, and each block's MMA thread
+// releases a stage in both blocks, so a stage is refilled only after both
+// blocks have consumed it.  Halves the B bytes read from L2 and DRAM.
+template <int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     emul_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
@@ -141,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], CL);   // one release per block of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -157,21 +177,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_relinquish();
     }
     tc_fence_before();
-    __syncthreads();
+    if (CL > 1) cluster_sync_all();   // the peer's barriers exist before any multicast
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int njobs = *njobs_slot;
+    const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1);
 
     // grouped raster: blocks run down group_m tile-rows before moving one
     // tile-column right, so a wave of blocks shares a compact set of A and B
     // digit panels in L2
+    // (with clusters, in units of CL tile-rows; a block whose tile lies past M
+    // still loads its half of B for its peer and stores nothing)
     int m0, n0;
     {
-        const int pid = (int)blockIdx.x, in_group = prm.group_m * prm.tiles_n;
-        const int first_m = (pid / in_group) * prm.group_m;
-        const int gsz = min(prm.tiles_m - first_m, prm.group_m);
+        const int tiles_mc = (prm.tiles_m + CL - 1) / CL;
+        const int gm = prm.group_m / CL > 0 ? prm.group_m / CL : 1;
+        const int pid = (int)blockIdx.x / CL, in_group = gm * prm.tiles_n;
+        const int first_m = (pid / in_group) * gm;
+        const int gsz = min(tiles_mc - first_m, gm);
         const int local = pid % in_group;
-        m0 = (first_m + local % gsz) * kTM;
+        m0 = ((first_m + local % gsz) * CL + rank) * kTM;
         n0 = (local / gsz) * kTN;
     }
     const uint64_t tmo = prm.timeout_ns;
@@ -195,13 +222,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive_expect_tx(&full[st], kStageBytes);
                     unsigned char* a = tiles + st * kStageBytes;
                     tma_load_3d(a, &tmA, &full[st], kb * kTK, m0, job_p(jd) - 1);
-                    tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
+                    if (CL == 1) {
+                        tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
+                    } else {
+                        constexpr uint32_t half = kBTile / CL;
+                        tma_load_3d_multicast(a + kATile + rank * half, &tmB, &full[st], kb * kTK,
+                                              n0 + rank * (kTN / CL), job_q(jd) - 1, kMask);
+                    }
                 }
             }
             // every copy issued must land before the block may exit
             for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
                 mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err,
                                   false);
+            if (CL > 1) {
+                // and every release the peer sends to this block's barriers must
+                // have arrived: the last round of each stage completes only
+                // after both blocks' releases
+                for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
+                    mbar_wait_bounded(&empty[j % kStages], (j / kStages) & 1, tmo, nullptr,
+                                      prm.err, false);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -236,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         umma_bf16(d_tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, accumulate);
                         accumulate = 1;
                     }
-                    umma_commit(&empty[st]);
+                    if (CL == 1) umma_commit(&empty[st]);
+                    else umma_commit_multicast(&empty[st], kMask);
                 }
                 if (!ok) break;
                 umma_commit(&accf[b]);
@@ -263,10 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                tmem_drain8_magic(taddr + c * 8, acc[c * 8 + 0], acc[c * 8 + 1], acc[c * 8 + 2],
-                                  acc[c * 8 + 3], acc[c * 8 + 4], acc[c * 8 + 5], acc[c * 8 + 6],
-                                  acc[c * 8 + 7]);
+            for (int c = 0; c < 4; ++c) tmem_drain32_magic(taddr + c * 32, &acc[c * 32]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
@@ -290,7 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    if (CL > 1) cluster_sync_all();   // no block leaves while its peer may still signal it
+    else __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -302,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream, int group_m) {
+                           cudaStream_t stream, int group_m, int cluster) {
     {   // the job table of one tile must fit its shared-memory slot
         const int64_t kblocks = (K + kTK - 1) / kTK;
         int64_t njobs = 0;
@@ -314,10 +355,11 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
             }
         if (njobs > kMaxJobs || kblocks > 1023) return ALP_ERR_UNSUPPORTED;
     }
+    const int cl = (cluster == 1 || cluster == 2) ? cluster : emul_cluster();
     CUtensorMap ta, tb;
     alp_status st = make_tmap_3d_bf16(&ta, da, (uint64_t)kpad, (uint64_t)M, (uint64_t)s, kTK, kTM);
     if (st != ALP_OK) return st;
-    st = make_tmap_3d_bf16(&tb, db, (uint64_t)kpad, (uint64_t)N, (uint64_t)s, kTK, kTN);
+    st = make_tmap_3d_bf16(&tb, db, (uint64_t)kpad, (uint64_t)N, (uint64_t)s, kTK, kTN / cl);
     if (st != ALP_OK) return st;
     EmulGemmParams p;
     p.M = M;
@@ -334,11 +376,32 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.group_m = group_m > 0 ? group_m : emul_group_m();
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
-    cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel,
+    if (cl == 1) {
+        cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        emul_gemm_kernel<1><<<(unsigned)(tiles_m * tiles_n), kThreads, kSmemBytes, stream>>>(ta, tb, p);
+        return cuda_status(cudaGetLastError());
+    }
+    cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return cuda_status(e);
-    emul_gemm_kernel<<<(unsigned)(tiles_m * tiles_n), kThreads, kSmemBytes, stream>>>(ta, tb, p);
-    return cuda_status(cudaGetLastError());
+    const int64_t grid = 2 * ((tiles_m + 1) / 2) * tiles_n;
+    if (grid > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = kSmemBytes;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelEx(&lc, emul_gemm_kernel<2>, ta, tb, p);
+    return cuda_status(e);
 }
 
 }  // namespace alp

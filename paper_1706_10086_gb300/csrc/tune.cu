@@ -68,7 +68,8 @@ std::vector<alp_config> native_configs() {
 
 std::vector<alp_config> emul_configs() {
     std::vector<alp_config> v;
-    for (int g : kGroups) v.push_back(alp_config{128, 256, 64, 0, 0, g});
+    for (int cl = 1; cl <= 2; ++cl)
+        for (int g : kGroups) v.push_back(alp_config{128, 256, 64, cl, 0, g});
     return v;
 }
 
@@ -173,7 +174,9 @@ bool time_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_confi
     const auto* da = reinterpret_cast<const __nv_bfloat16*>(base);
     const auto* db = reinterpret_cast<const __nv_bfloat16*>(base + ba);
     int32_t* G = reinterpret_cast<int32_t*>(base + ba + bb);
-    auto launch = [&]() { return emul_slice_gemm(M, N, Kp, s, da, db, kpad, G, ldg, st, cfg.stages); };
+    auto launch = [&]() {
+        return emul_slice_gemm(M, N, Kp, s, da, db, kpad, G, ldg, st, cfg.stages, cfg.tm);
+    };
     if (!time_launch(launch, st, runs, meas_best, meas_median)) return false;
     *est_ms = *meas_best * ((double)K / (double)Kp);
     return true;

@@ -266,3 +266,107 @@ def evaluate(model, train_ds, test_ds, tuning_shape=(10240, 10240, 10240)):
            "fixed_best_mean": summarize(regret(test_ds, fixed_config_choice(train_ds, test_ds))),
            "nearest_shape": summarize(regret(test_ds, nearest_shape_choice(train_ds, test_ds)))}
     return res
+
+
+def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
+                         tiles=(32, 64, 128), bks=(16, 32), log=None):
+    """Autotunes the batched GEMM's tile per size class: for every class
+    present in the batch, times the class's own problems (alp_gemm_batched_varsize
+    on that sub-batch, CUDA events, best of ``runs`` after a warm-up) with each
+    candidate (bm, bn, bk) and installs the fastest with
+    alp_batched_set_class_config.  M, N, K, pA, pB, pC are host arrays (sizes and
+    device addresses of row-major operands with tight leading dimensions).
+    Returns {class: ((bm, bn, bk), ms, {candidate: ms})}."""
+    import torch
+    dev = torch.device("cuda")
+    M, N, K = (np.ascontiguousarray(a, dtype=np.int64) for a in (M, N, K))
+    cls = np.array([alp.alp_batched_class_of(int(m), int(n)) for m, n in zip(M, N)])
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for c in sorted(set(cls.tolist())):
+        idx = np.where(cls == c)[0]
+        hM, hN, hK = M[idx].copy(), N[idx].copy(), K[idx].copy()
+        t = lambda a, dt=torch.int64: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+        n = len(idx)
+        args = (n, t(hM), t(hN), t(hK), t(np.full(n, alpha), torch.float64),
+                t(np.asarray(pA)[idx]), t(hK), t(np.asarray(pB)[idx]), t(hN),
+                t(np.full(n, beta), torch.float64), t(np.asarray(pC)[idx]), t(hN), hM, hN, hK)
+        ws = alp.alp_gemm_batched_workspace(n, hM, hN, hK)
+        work = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+        old = alp.alp_batched_get_class_config(c)
+        times = {}
+        for bm in tiles:
+            for bn in tiles:
+                for bk in bks:
+                    alp.alp_batched_set_class_config(c, bm, bn, bk)
+                    alp.alp_gemm_batched_varsize(*args, work, ws, stream=stream)
+                    best = float("inf")
+                    for _ in range(runs):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        alp.alp_gemm_batched_varsize(*args, work, ws, stream=stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        best = min(best, e0.elapsed_time(e1))
+                    times[(bm, bn, bk)] = best
+        win = min(times, key=lambda k: (times[k], k))
+        alp.alp_batched_set_class_config(c, *win)
+        out[c] = (win, times[win], times)
+        if log:
+            log(f"class {c}: {n} problems, default {old} {times.get(tuple(old), float('nan')):.3f} ms"
+                f" -> {win} {times[win]:.3f} ms")
+    return out
+
+
+def run(db, n_train=2000, n_test=500, lo=64, hi=16384, paths=("native", "emul"), runs=2,
+        epochs=3000, lr=3e-3, out=None, log_every=100):
+    """The whole predictor workload: sweep, train on the GPU, evaluate."""
+    import time
+    seed = inputs.workload_seed("mlp_predictor")
+    train_sh = inputs.shapes(seed, n_train, lo, hi)
+    test_sh = inputs.shapes(seed + 1, n_test, lo, hi)
+    t0 = time.time()
+    collect(train_sh, paths, db, runs=runs, log_every=log_every)
+    collect(test_sh, paths, db, runs=runs, log_every=log_every)
+    t_collect = time.time() - t0
+    recs = load_db(db)
+    key = lambda r: (r["M"], r["N"], r["K"])
+    train_keys = {tuple(int(v) for v in s) for s in train_sh}
+    test_keys = {tuple(int(v) for v in s) for s in test_sh}
+    train_ds = dataset([r for r in recs if key(r) in train_keys])
+    test_ds = dataset([r for r in recs if key(r) in test_keys and key(r) not in train_keys])
+    t0 = time.time()
+    model, hist = train(train_ds, epochs=epochs, lr=lr, log_every=max(1, epochs // 10))
+    t_train = time.time() - t0
+    res = {"n_train": int(len(train_ds["M"])), "n_test": int(len(test_ds["M"])),
+           "collect_s": round(t_collect, 1), "train_s": round(t_train, 2),
+           "loss_history": [round(h, 5) for h in hist]}
+    for pname, pid in (("all", None), ("native", 0), ("emul", 1)):
+        sel = np.ones(len(test_ds["M"]), bool) if pid is None else test_ds["path"] == pid
+        if not sel.any():
+            continue
+        sub = {k: (v[sel] if isinstance(v, np.ndarray) and len(v) == len(sel) else v)
+               for k, v in test_ds.items()}
+        res[pname] = evaluate(model, train_ds, sub)
+    if out:
+        with open(out, "w") as f:
+            json.dump(res, f, indent=1)
+        np.savez(out + ".model.npz", params=model[0], mean=model[1], std=model[2])
+    return res, model
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="tile-config predictor workload")
+    ap.add_argument("--db", required=True)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=500)
+    ap.add_argument("--runs", type=int, default=2)
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--paths", default="native,emul")
+    a = ap.parse_args()
+    res, _ = run(a.db, a.train, a.test, paths=tuple(a.paths.split(",")), runs=a.runs,
+                 epochs=a.epochs, out=a.out)
+    print(json.dumps({k: v for k, v in res.items() if k != "loss_history"}))

@@ -95,6 +95,24 @@ def test_emul_bit_exact_vs_model(alp, orc, shape, s, phi):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("cluster,group", [(1, 1), (1, 8), (2, 1), (2, 4), (2, 32)])
+def test_emul_every_config_bit_exact(alp, orc, cluster, group):
+    """Each emulated config (blocks sharing B tiles, raster group), forced
+    through the tuned cache, on a shape with an odd number of tile-rows."""
+    M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
+    cfg = (128, 256, 64, cluster, 0, group)
+    assert alp.alp_config_valid(cfg, alp.ALP_PATH_EMUL)
+    A, B, C = inputs.gemm_operands(3600 + cluster * 100 + group, M, N, K, kind="scaled", phi=8)
+    alp.alp_tune_set_cached(M, N, K, alp.ALP_PATH_EMUL, cfg)
+    try:
+        got, st, err = run_emul(alp, A, B, C, 1.5, 0.5, 8)
+    finally:
+        alp.alp_tune_clear_cache()
+    assert err == alp.ALP_OK
+    ref, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 8)
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("K", [255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 4097])
 def test_emul_chunk_boundaries(alp, orc, K):
     """K around the drain chunks (256, 512, 1024) and the 64-wide k-blocks."""
