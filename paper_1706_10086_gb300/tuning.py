@@ -215,9 +215,10 @@ def regret(ds, choice):
     return np.where(np.isfinite(r), r, np.nan)
 
 
-def fixed_config_choice(train_ds, test_ds, tuning_shape=None):
-    """One config per path for every shape.  With tuning_shape = (M, N, K) it
-    is the winner of that single shape (the paper's tuning protocol);
+def fixed_config_choice(train_ds, test_ds, tuning_shape=None, tuning_ds=None):
+    """One config per path for every shape.  With tuning_ds (the sweep of the
+    tuning shape, e.g. N = 10240 as in the paper's Sect. 3) it is that sweep's
+    winner; with only tuning_shape, the winner of the nearest training shape;
     otherwise the config with the lowest mean ln(t / t_best) over training."""
     nat, _ = config_lists()
     out = np.empty(len(test_ds["M"]), dtype=np.int64)
@@ -226,7 +227,10 @@ def fixed_config_choice(train_ds, test_ds, tuning_shape=None):
         sel = train_ds["path"] == p
         if not sel.any():
             continue
-        if tuning_shape is not None:
+        if tuning_ds is not None and (tuning_ds["path"] == p).any():
+            row = tuning_ds["times"][np.where(tuning_ds["path"] == p)[0][0]]
+            c = lo + int(np.nanargmin(row[lo:hi]))
+        elif tuning_shape is not None:
             d = (np.log2(train_ds["M"][sel]) - math.log2(tuning_shape[0])) ** 2 + \
                 (np.log2(train_ds["N"][sel]) - math.log2(tuning_shape[1])) ** 2 + \
                 (np.log2(train_ds["K"][sel]) - math.log2(tuning_shape[2])) ** 2
@@ -259,10 +263,10 @@ def summarize(r):
             "p90": float(np.percentile(r, 90)), "max": float(np.max(r)), "n": int(len(r))}
 
 
-def evaluate(model, train_ds, test_ds, tuning_shape=(10240, 10240, 10240)):
+def evaluate(model, train_ds, test_ds, tuning_shape=(10240, 10240, 10240), tuning_ds=None):
     res = {"mlp": summarize(regret(test_ds, choose_by_model(model, test_ds))),
            "fixed_tuned_once": summarize(regret(test_ds, fixed_config_choice(
-               train_ds, test_ds, tuning_shape))),
+               train_ds, test_ds, tuning_shape, tuning_ds))),
            "fixed_best_mean": summarize(regret(test_ds, fixed_config_choice(train_ds, test_ds))),
            "nearest_shape": summarize(regret(test_ds, nearest_shape_choice(train_ds, test_ds)))}
     return res
@@ -329,8 +333,12 @@ def run(db, n_train=2000, n_test=500, lo=64, hi=16384, paths=("native", "emul"),
     t0 = time.time()
     collect(train_sh, paths, db, runs=runs, log_every=log_every)
     collect(test_sh, paths, db, runs=runs, log_every=log_every)
+    # the paper's tuning sizes (Sect. 3): N = 10240, control N = 7168
+    tuning_shapes = [(10240, 10240, 10240), (7168, 7168, 7168)]
+    collect(tuning_shapes, paths, db, runs=runs)
     t_collect = time.time() - t0
     recs = load_db(db)
+    tuning_ds = dataset([r for r in recs if (r["M"], r["N"], r["K"]) == tuning_shapes[0]])
     key = lambda r: (r["M"], r["N"], r["K"])
     train_keys = {tuple(int(v) for v in s) for s in train_sh}
     test_keys = {tuple(int(v) for v in s) for s in test_sh}
@@ -348,7 +356,13 @@ def run(db, n_train=2000, n_test=500, lo=64, hi=16384, paths=("native", "emul"),
             continue
         sub = {k: (v[sel] if isinstance(v, np.ndarray) and len(v) == len(sel) else v)
                for k, v in test_ds.items()}
-        res[pname] = evaluate(model, train_ds, sub)
+        res[pname] = evaluate(model, train_ds, sub, tuning_ds=tuning_ds)
+    control = dataset([r for r in recs if (r["M"], r["N"], r["K"]) == tuning_shapes[1]])
+    nat, _ = config_lists()
+    res["tuning_shape_winners"] = {
+        f"{tuning_shapes[i][0]}^3 {'native' if p == 0 else 'emul'}":
+            list((nat + config_lists()[1])[int(np.nanargmin(d["times"][j]))])
+        for i, d in enumerate((tuning_ds, control)) for j, p in enumerate(d["path"])}
     if out:
         with open(out, "w") as f:
             json.dump(res, f, indent=1)
