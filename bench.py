@@ -54,6 +54,8 @@ def parse_args():
                     help="digit slices; 7 is no less accurate than native FP64 for the default "
                          "uniform inputs (checked live against 8 slices), 8 for wide exponent "
                          "ranges")
+    ap.add_argument("--digit-bits", type=int, choices=(7, 8), default=7,
+                    help="bits per digit slice: 7 (up to 8 slices) or 8 (up to 7 slices)")
     ap.add_argument("--phi", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
@@ -209,6 +211,10 @@ def cpu_oracle_sample(A_rows, B, alpha, target_s):
     return flops / dt / 1e12, rows, dt, n_threads
 
 
+def workload_name(n, s, b, phi):
+    return f"emulated_dgemm_{n}_bf16x{s}slices{'' if b == 7 else f'_{b}bit'}_phi{phi}"
+
+
 def make_inputs(torch, n, phi, seed, device):
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -234,7 +240,8 @@ def run_alp(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
-    n, s, phi = args.n, args.nslices, args.phi
+    n, s, phi, b = args.n, args.nslices, args.phi, args.digit_bits
+    kind = alp.ALP_SLICE_BF16 if b == 7 else alp.ALP_SLICE_BF16_B8
     M = N = K = n
     seed = 1706 + 2
     A, B = make_inputs(torch, n, phi, seed, dev)
@@ -259,13 +266,13 @@ def run_alp(args):
         rec(1)
         alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
         rec(2)
-        alp.alp_emul_split(M, K, A, K, 0, e, s, da, kpad, stream)
+        alp.alp_emul_split(M, K, A, K, 0, e, s, b, da, kpad, stream)
         rec(3)
-        alp.alp_emul_split(N, K, B, N, 1, f, s, db, kpad, stream)
+        alp.alp_emul_split(N, K, B, N, 1, f, s, b, db, kpad, stream)
         rec(4)
-        alp.alp_emul_slice_products(M, N, K, s, da, db, kpad, G, ldg, stream)
+        alp.alp_emul_slice_products(M, N, K, s, b, da, db, kpad, G, ldg, stream)
         rec(5)
-        alp.alp_emul_recombine(M, N, s, G, ldg, e, f, alpha, beta, C, N, stream)
+        alp.alp_emul_recombine(M, N, s, b, G, ldg, e, f, alpha, beta, C, N, stream)
         rec(6)
 
     for _ in range(max(3, args.warmup)):
@@ -320,8 +327,9 @@ def run_alp(args):
            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
            "data": "synthetic (seeded torch generator on the GPU; u*2^e, u~U[-1,1), e~U{-phi..phi})",
-           "config": {"workload": f"emulated_dgemm_{n}_bf16x{s}slices_phi{phi}", "M": M, "N": N,
-                      "K": K, "nslices": s, "phi": phi, "alpha": alpha, "beta": beta,
+           "config": {"workload": workload_name(n, s, b, phi), "M": M, "N": N,
+                      "K": K, "nslices": s, "digit_bits": b, "phi": phi, "alpha": alpha,
+                      "beta": beta,
                       "result_dtype": "f64", "parallelism": f"replicas{ws}",
                       "l2": "inputs 1.5 GB > 129 MB L2; no flush"},
            "step_ms_median": round(statistics.median(step_ms), 3),
@@ -333,15 +341,14 @@ def run_alp(args):
         print(json.dumps(out), flush=True)
         return
     # public single-call API on the same device buffers (same kernels, one call)
-    wsb = alp.alp_gemm_f64_emul_workspace(M, N, K, s, alp.ALP_SLICE_BF16)
+    wsb = alp.alp_gemm_f64_emul_workspace(M, N, K, s, kind)
     work = torch.empty(wsb, dtype=torch.uint8, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, alp.ALP_SLICE_BF16, work,
-                          wsb, stream)
+    alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, kind, work, wsb, stream)
     e0.record(stream)
     for _ in range(3):
-        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, alp.ALP_SLICE_BF16,
-                              work, wsb, stream)
+        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, beta, C, N, s, kind, work, wsb,
+                              stream)
     e1.record(stream)
     torch.cuda.synchronize()
     out["api_call_ms"] = round(e0.elapsed_time(e1) / 3, 3)
@@ -384,8 +391,8 @@ def run_alp(args):
                 stream.wait_event(h2d[i])
                 if i >= 2:
                     stream.wait_event(d2h[i - 2])
-                alp.alp_gemm_f64_emul(M, N, K, alpha, dA, K, dB, N, beta, dC, N, s,
-                                      alp.ALP_SLICE_BF16, work, wsb, stream)
+                alp.alp_gemm_f64_emul(M, N, K, alpha, dA, K, dB, N, beta, dC, N, s, kind, work,
+                                      wsb, stream)
                 comp[i].record(stream)
                 copy.wait_event(comp[i])
                 with torch.cuda.stream(copy):
@@ -436,8 +443,8 @@ def run_alp(args):
                               work8, ws8, stream)
         del work8
         Cs = torch.empty_like(C)
-        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, Cs, N, s, alp.ALP_SLICE_BF16, work,
-                              wsb, stream)
+        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, Cs, N, s, kind, work, wsb,
+                              stream)
         Cn = torch.empty_like(C)
         alp.alp_gemm_f64(M, N, K, alpha, A, K, B, N, 0.0, Cn, N, stream=stream)
         absAB = torch.empty_like(C)
@@ -498,7 +505,7 @@ def run_reference(args):
            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double accumulation)",
            "data": "synthetic (seeded SplitMix64, uniform [-1,1))",
-           "config": {"workload": f"emulated_dgemm_{n}_bf16x{args.nslices}slices_phi{args.phi}",
+           "config": {"workload": workload_name(n, args.nslices, args.digit_bits, args.phi),
                       "M": n, "N": n,
                       "K": n, "sample_rows_per_step": rows_per_step},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",

@@ -155,6 +155,19 @@ alp_status alp_gemm_batched_varsize_noalloc(int64_t count, const int64_t* dM, co
                                             const int64_t* dldc, const int64_t* hM,
                                             const int64_t* hN, const int64_t* hK, void* stream);
 
+/* ---- emulated path: launch shape -------------------------------------------- */
+
+/* Host-only query (no GPU needed): how alp_emul_slice_products cuts a launch
+ * of `tiles` 128 x 256 tiles with `nslices` slices on `sms` SMs when blocks do
+ * not share B tiles.  Blocks [0, *n_full) take whole tiles; each remaining
+ * tile (the last, partial wave) is taken by *pieces blocks, piece i computing
+ * the group sums S^t for t = t_lo[i]..t_hi[i] (arrays of 8).  The cut is the
+ * contiguous one whose largest piece (in digit pairs) is smallest, with at most
+ * min(sms / r, nslices, 8) pieces for r tiles in the last wave.  Splitting the
+ * groups changes no result: each group sum is exact and written once. */
+alp_status alp_emul_tail_split(int tiles, int nslices, int sms, int* n_full, int* pieces,
+                               int* t_lo, int* t_hi);
+
 /* ---- FP64 peak probe ----------------------------------------------------- */
 
 /* Measured FP64 throughput of this GPU: kind 0 = m16n8k4 DMMA chains (the

@@ -27,6 +27,7 @@ ALP_ERR_NOT_TUNED = 6
 # alp_slice_kind
 ALP_SLICE_INT8 = 0
 ALP_SLICE_BF16 = 1
+ALP_SLICE_BF16_B8 = 2
 # alp_path
 ALP_PATH_NATIVE = 0
 ALP_PATH_EMUL = 1
@@ -65,9 +66,11 @@ _SIGS = {
                            _int, _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f64_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
     "alp_emul_exponents": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
-    "alp_emul_split": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _vp, _i64, _vp], _int),
-    "alp_emul_slice_products": ([_i64, _i64, _i64, _int, _vp, _vp, _i64, _vp, _i64, _vp], _int),
-    "alp_emul_recombine": ([_i64, _i64, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64, _vp],
+    "alp_emul_split": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _i64, _vp], _int),
+    "alp_emul_slice_products": ([_i64, _i64, _i64, _int, _int, _vp, _vp, _i64, _vp, _i64, _vp],
+                                _int),
+    "alp_emul_recombine": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64,
+                            _vp],
                            _int),
     "alp_gemm_batched_varsize": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp], _int),
@@ -83,6 +86,8 @@ _SIGS = {
     "alp_set_wait_timeout_ms": ([_f64], _int),
     "alp_debug_inject_skip": ([_int], _int),
     "alp_probe_fp64_peak": ([_int, _i64, _int, _int, ctypes.POINTER(_f64), _vp], _int),
+    "alp_emul_tail_split": ([_int, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                             ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
     "alp_tune_time_config": ([_i64, _i64, _i64, _int, ctypes.POINTER(alp_config), _int, _int,
                               ctypes.POINTER(_f64)], _int),
     "alp_tune_set_cached": ([_i64, _i64, _i64, _int, ctypes.POINTER(alp_config)], _int),
@@ -190,24 +195,24 @@ def alp_emul_exponents(rows, cols, X, ldx, trans, exps, stream=None, raise_on_er
     return _check(st, "alp_emul_exponents", raise_on_error)
 
 
-def alp_emul_split(R, K, X, ldx, trans, exps, nslices, out, kpad, stream=None,
+def alp_emul_split(R, K, X, ldx, trans, exps, nslices, digit_bits, out, kpad, stream=None,
                    raise_on_error=True):
-    st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices), _p(out),
-                              kpad, _s(stream))
+    st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices),
+                              int(digit_bits), _p(out), kpad, _s(stream))
     return _check(st, "alp_emul_split", raise_on_error)
 
 
-def alp_emul_slice_products(M, N, K, nslices, da, db, kpad, G, ldg, stream=None,
+def alp_emul_slice_products(M, N, K, nslices, digit_bits, da, db, kpad, G, ldg, stream=None,
                             raise_on_error=True):
-    st = lib().alp_emul_slice_products(M, N, K, int(nslices), _p(da), _p(db), kpad, _p(G), ldg,
-                                       _s(stream))
+    st = lib().alp_emul_slice_products(M, N, K, int(nslices), int(digit_bits), _p(da), _p(db),
+                                       kpad, _p(G), ldg, _s(stream))
     return _check(st, "alp_emul_slice_products", raise_on_error)
 
 
-def alp_emul_recombine(M, N, nslices, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
-                       raise_on_error=True):
-    st = lib().alp_emul_recombine(M, N, int(nslices), _p(G), ldg, _p(e), _p(f), float(alpha),
-                                  float(beta), _p(C), ldc, _s(stream))
+def alp_emul_recombine(M, N, nslices, digit_bits, G, ldg, e, f, alpha, beta, C, ldc,
+                       stream=None, raise_on_error=True):
+    st = lib().alp_emul_recombine(M, N, int(nslices), int(digit_bits), _p(G), ldg, _p(e), _p(f),
+                                  float(alpha), float(beta), _p(C), ldc, _s(stream))
     return _check(st, "alp_emul_recombine", raise_on_error)
 
 
@@ -284,6 +289,15 @@ def alp_probe_fp64_peak(kind=0, iters=20000, blocks_per_sm=2, threads=256, strea
     _check(lib().alp_probe_fp64_peak(int(kind), int(iters), int(blocks_per_sm), int(threads),
                                      ctypes.byref(out), _s(stream)), "alp_probe_fp64_peak", True)
     return out.value
+
+
+def alp_emul_tail_split(tiles, nslices, sms):
+    """(n_full, [(t_lo, t_hi) per piece]) of the slice-product launch."""
+    n_full, pieces = ctypes.c_int(0), ctypes.c_int(0)
+    lo, hi = (_int * 8)(), (_int * 8)()
+    _check(lib().alp_emul_tail_split(int(tiles), int(nslices), int(sms), ctypes.byref(n_full),
+                                     ctypes.byref(pieces), lo, hi), "alp_emul_tail_split", True)
+    return n_full.value, [(lo[i], hi[i]) for i in range(pieces.value)]
 
 
 def alp_batched_class_of(M, N) -> int:

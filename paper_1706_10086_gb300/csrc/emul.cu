@@ -3,9 +3,9 @@
 //
 //   1. exponent scan: e_i = frexp exponent of max_k |A_ik|, f_j of max_k |B_kj|
 //      (integer max over the IEEE bit patterns; Inf/NaN -> ALP_ERR_UNSUPPORTED);
-//   2. split: each A_ik * 2^-e_i is cut into s digits of b = 7 bits with round
-//      half to even (|d_1| <= 128, |d_p| <= 64), stored exactly as bf16,
-//      K-major for both operands (B is transposed on the way);
+//   2. split: each A_ik * 2^-e_i is cut into s digits of b = 7 or 8 bits with
+//      round half to even (|d_1| <= 2^b, |d_p| <= 2^(b-1)), stored exactly as
+//      bf16, K-major for both operands (B is transposed on the way);
 //   3. slice products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..s+1, on tcgen05
 //      (emul_gemm.cu) as exact int32 per group;
 //   4. recombination: X = sum_t S^t 2^((s+1-t) b) exactly (128-bit integer),
@@ -107,9 +107,10 @@ __global__ void zero_empty_columns_kernel(int64_t N, int32_t* __restrict__ f) {
 // Digits of a * 2^-e.  r0 = a * 2^-e is held as a 64-bit fixed-point number
 // with 62 fraction bits, rounded to odd (truncate, then set the last bit if
 // anything was cut off): every later rounding happens at least 2 bits above
-// that last bit, so the digits equal those of the exact value (s*7 <= 56).
-// Each step is d = round-half-even(X / 2^55), X = (X - d 2^55) * 2^7, which is
-// x = r * 2^7, d = nearest integer (ties to even), r = x - d in fixed point.
+// that last bit, so the digits equal those of the exact value ((s-1) b + 2 <=
+// 62 - b).  Each step is d = round-half-even(X / 2^(62-b)), X = (X - d 2^(62-b))
+// * 2^b, which is x = r * 2^b, d = nearest integer (ties to even), r = x - d in
+// fixed point.
 __device__ __forceinline__ uint64_t fixed_point_r0(double a, int e) {
     const uint64_t bits = (uint64_t)__double_as_longlong(a);
     const bool neg = (bits >> 63) != 0;
@@ -136,16 +137,18 @@ __device__ __forceinline__ uint64_t fixed_point_r0(double a, int e) {
     return neg ? (0ull - Y) : Y;   // two's complement of the signed value
 }
 
-template <int S>
+template <int S, int B>
 __device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
+    constexpr int SH = 62 - B;   // the digit's unit in the fixed point
     uint64_t X = fixed_point_r0(a, e);
 #pragma unroll
     for (int p = 0; p < S; ++p) {
-        const int64_t q = ((int64_t)X) >> 55;
-        const uint64_t rem = X & ((1ull << 55) - 1);
-        const int64_t dd = q + ((rem > (1ull << 54)) || (rem == (1ull << 54) && (q & 1)) ? 1 : 0);
+        const int64_t q = ((int64_t)X) >> SH;
+        const uint64_t rem = X & ((1ull << SH) - 1);
+        const uint64_t half = 1ull << (SH - 1);
+        const int64_t dd = q + ((rem > half) || (rem == half && (q & 1)) ? 1 : 0);
         d[p] = (int)dd;
-        X = (X - ((uint64_t)dd << 55)) << 7;
+        X = (X - ((uint64_t)dd << SH)) << B;
     }
 }
 
@@ -160,7 +163,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
 
 // A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
 // thread handles two consecutive k.
-template <int S>
+template <int S, int B>
 __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K,
                                   int64_t ldx, const int32_t* __restrict__ e,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
@@ -173,8 +176,8 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
         const int64_t k = (idx - r * half) * 2;
         const int er = e[r];
         int d0[S], d1[S];
-        split_digits<S>(k < K ? __ldg(X + r * ldx + k) : 0.0, er, d0);
-        split_digits<S>(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, d1);
+        split_digits<S, B>(k < K ? __ldg(X + r * ldx + k) : 0.0, er, d0);
+        split_digits<S, B>(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, d1);
         uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
 #pragma unroll
         for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
@@ -183,7 +186,7 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
 
 // B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
 // shared memory so that reads run along j and writes along k.
-template <int S>
+template <int S, int B>
 __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N,
                                   int64_t ldx, const int32_t* __restrict__ f,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
@@ -203,8 +206,8 @@ __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64
         if (j >= N) continue;
         const int fj = f[j];
         int d0[S], d1[S];
-        split_digits<S>(t[jj][2 * tx], fj, d0);
-        split_digits<S>(t[jj][2 * tx + 1], fj, d1);
+        split_digits<S, B>(t[jj][2 * tx], fj, d0);
+        split_digits<S, B>(t[jj][2 * tx + 1], fj, d1);
         const int64_t k = k0 + 2 * tx;
         if (k >= kpad) continue;
         uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
@@ -257,7 +260,7 @@ __device__ __forceinline__ double int128_scaled_to_double_rn(unsigned __int128 x
 // stride), two columns per thread from the x dimension (no integer division
 // per element).  The slice count is a template parameter so that the S loads
 // are independent and the sum is a Horner chain, X = X * 2^7 + S^t.
-template <int S>
+template <int S, int B>
 __device__ __forceinline__ double recombine_one(const int32_t* __restrict__ g, int64_t gplane,
                                                 int E) {
     int32_t v[S];
@@ -265,16 +268,16 @@ __device__ __forceinline__ double recombine_one(const int32_t* __restrict__ g, i
     for (int t = 0; t < S; ++t) v[t] = __ldg(g + (int64_t)t * gplane);
     unsigned __int128 X = (unsigned __int128)(__int128)v[0];
 #pragma unroll
-    for (int t = 1; t < S; ++t) X = (X << kDigitBits) + (unsigned __int128)(__int128)v[t];
+    for (int t = 1; t < S; ++t) X = (X << B) + (unsigned __int128)(__int128)v[t];
     return int128_scaled_to_double_rn(X, E);
 }
 
-template <int S>
+template <int S, int B>
 __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, int64_t ldg,
                                  const int32_t* __restrict__ e, const int32_t* __restrict__ f,
                                  int64_t M, int64_t N, double alpha, double beta,
                                  double* __restrict__ C, int64_t ldc) {
-    const int shift0 = (S + 1) * kDigitBits;
+    const int shift0 = (S + 1) * B;
     for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
         const int ei = e[i] - shift0;
         const int32_t* gi = G + i * ldg;
@@ -285,7 +288,7 @@ __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, 
             for (int u = 0; u < 2; ++u) {
                 const int64_t jj = j + u;
                 if (jj >= N) break;
-                const double w = recombine_one<S>(gi + jj, gplane, ei + __ldg(f + jj));
+                const double w = recombine_one<S, B>(gi + jj, gplane, ei + __ldg(f + jj));
                 double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
                 if (beta != 0.0) out = __fma_rn(beta, ci[jj], out);
                 ci[jj] = out;
@@ -294,12 +297,13 @@ __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, 
     }
 }
 
-static alp_status launch_recombine(int s, dim3 grid, cudaStream_t st, const int32_t* G,
-                                   int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
-                                   int64_t M, int64_t N, double alpha, double beta, double* C,
-                                   int64_t ldc) {
+template <int B>
+static alp_status launch_recombine_b(int s, dim3 grid, cudaStream_t st, const int32_t* G,
+                                     int64_t gplane, int64_t ldg, const int32_t* e,
+                                     const int32_t* f, int64_t M, int64_t N, double alpha,
+                                     double beta, double* C, int64_t ldc) {
 #define ALP_RECOMBINE_CASE(x) \
-    case x: recombine_kernel<x><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc); break;
+    case x: recombine_kernel<x, B><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc); break;
     switch (s) {
         ALP_RECOMBINE_CASE(1) ALP_RECOMBINE_CASE(2) ALP_RECOMBINE_CASE(3) ALP_RECOMBINE_CASE(4)
         ALP_RECOMBINE_CASE(5) ALP_RECOMBINE_CASE(6) ALP_RECOMBINE_CASE(7) ALP_RECOMBINE_CASE(8)
@@ -307,6 +311,17 @@ static alp_status launch_recombine(int s, dim3 grid, cudaStream_t st, const int3
     }
 #undef ALP_RECOMBINE_CASE
     return cuda_status(cudaGetLastError());
+}
+
+static alp_status launch_recombine(int s, int b, dim3 grid, cudaStream_t st, const int32_t* G,
+                                   int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
+                                   int64_t M, int64_t N, double alpha, double beta, double* C,
+                                   int64_t ldc) {
+    if (b == 7)
+        return launch_recombine_b<7>(s, grid, st, G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc);
+    if (b == 8)
+        return launch_recombine_b<8>(s, grid, st, G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc);
+    return ALP_ERR_INVALID_ARG;
 }
 
 static dim3 recombine_grid(int64_t M, int64_t N) {
@@ -363,17 +378,18 @@ alp_status emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t l
     return cuda_status(cudaGetLastError());
 }
 
-alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
-                      const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
-                      cudaStream_t st) {
+template <int B>
+static alp_status emul_split_b(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+                               const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
+                               cudaStream_t st) {
 #define ALP_SPLIT_CASE(x)                                                                        \
     case x:                                                                                      \
         if (!trans)                                                                              \
-            split_rows_kernel<x><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(X, R, K, ldx,    \
-                                                                               exps, out, kpad); \
+            split_rows_kernel<x, B><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(              \
+                X, R, K, ldx, exps, out, kpad);                                                  \
         else                                                                                     \
-            split_cols_kernel<x><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)), 256,   \
-                                   0, st>>>(X, K, R, ldx, exps, out, kpad);                      \
+            split_cols_kernel<x, B><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)),     \
+                                      256, 0, st>>>(X, K, R, ldx, exps, out, kpad);              \
         break;
     switch (s) {
         ALP_SPLIT_CASE(1) ALP_SPLIT_CASE(2) ALP_SPLIT_CASE(3) ALP_SPLIT_CASE(4)
@@ -384,18 +400,44 @@ alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int tr
     return cuda_status(cudaGetLastError());
 }
 
+alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+                      const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
+                      cudaStream_t st, int b) {
+    if (b == 7) return emul_split_b<7>(R, K, X, ldx, trans, exps, s, out, kpad, st);
+    if (b == 8) return emul_split_b<8>(R, K, X, ldx, trans, exps, s, out, kpad, st);
+    return ALP_ERR_INVALID_ARG;
+}
+
 }  // namespace alp
 
 using namespace alp;
 
 extern "C" {
 
+static int digit_bits_of(alp_slice_kind kind) {
+    return kind == ALP_SLICE_BF16 ? 7 : kind == ALP_SLICE_BF16_B8 ? 8 : 0;
+}
+
 size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind) {
-    if (M < 0 || N < 0 || K < 0 || nslices < kMinSlices || nslices > kMaxSlices ||
-        kind != ALP_SLICE_BF16)
+    const int b = digit_bits_of(kind);
+    if (M < 0 || N < 0 || K < 0 || b == 0 || nslices < kMinSlices || nslices > emul_max_slices(b))
         return 0;
     return emul_layout(M, N, K, nslices).bytes;
+}
+
+alp_status alp_emul_tail_split(int tiles, int nslices, int sms, int* n_full, int* pieces,
+                               int* t_lo, int* t_hi) {
+    if (tiles < 0 || nslices < 1 || nslices > 8 || sms < 1 || !n_full || !pieces || !t_lo || !t_hi)
+        return ALP_ERR_INVALID_ARG;
+    const TailSplit ts = tail_split(tiles, nslices, sms);
+    *n_full = ts.n_full;
+    *pieces = ts.pieces;
+    for (int i = 0; i < 8; ++i) {
+        t_lo[i] = ts.t_lo[i];
+        t_hi[i] = ts.t_hi[i];
+    }
+    return ALP_OK;
 }
 
 alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx,
@@ -408,41 +450,45 @@ alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64
 }
 
 alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
-                          const int32_t* exps, int nslices, void* out_bf16, int64_t kpad,
-                          void* stream) {
-    if (R < 0 || K < 0 || nslices < 1 || nslices > kMaxSlices || kpad < K || kpad % 64 ||
-        !exps || !out_bf16 || (R > 0 && K > 0 && !X))
+                          const int32_t* exps, int nslices, int digit_bits, void* out_bf16,
+                          int64_t kpad, void* stream) {
+    if (R < 0 || K < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
+        nslices > emul_max_slices(digit_bits) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
+        (R > 0 && K > 0 && !X))
         return ALP_ERR_INVALID_ARG;
     if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
     if (trans && ldx < R) return ALP_ERR_INVALID_ARG;
     if (R == 0 || kpad == 0) return ALP_OK;
     return emul_split(R, K, X, ldx, trans, exps, nslices,
                       reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
-                      reinterpret_cast<cudaStream_t>(stream));
+                      reinterpret_cast<cudaStream_t>(stream), digit_bits);
 }
 
-alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
+alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices, int digit_bits,
                                    const void* da_bf16, const void* db_bf16, int64_t kpad,
                                    int32_t* G, int64_t ldg, void* stream) {
-    if (M < 0 || N < 0 || K < 0 || nslices < 1 || nslices > kMaxSlices || kpad < K ||
-        kpad % kEmulBK || ldg < N || ldg % 256 || K > kEmulMaxK)
+    if (M < 0 || N < 0 || K < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
+        nslices > emul_max_slices(digit_bits) || kpad < K || kpad % kEmulBK || ldg < N ||
+        ldg % 256 || K > emul_max_k(digit_bits))
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0 || K == 0) return ALP_OK;
     if (!da_bf16 || !db_bf16 || !G) return ALP_ERR_INVALID_ARG;
     return emul_slice_gemm(M, N, K, nslices, reinterpret_cast<const __nv_bfloat16*>(da_bf16),
                            reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, G, ldg,
-                           reinterpret_cast<cudaStream_t>(stream));
+                           reinterpret_cast<cudaStream_t>(stream), 0, 0, digit_bits);
 }
 
-alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, const int32_t* G, int64_t ldg,
-                              const int32_t* e, const int32_t* f, double alpha, double beta,
-                              double* C, int64_t ldc, void* stream) {
-    if (M < 0 || N < 0 || nslices < 1 || nslices > kMaxSlices || ldg < N || ldc < N)
+alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, int digit_bits, const int32_t* G,
+                              int64_t ldg, const int32_t* e, const int32_t* f, double alpha,
+                              double beta, double* C, int64_t ldc, void* stream) {
+    if (M < 0 || N < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
+        nslices > emul_max_slices(digit_bits) || ldg < N || ldc < N)
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
-    return launch_recombine(nslices, recombine_grid(M, N), reinterpret_cast<cudaStream_t>(stream),
-                            G, M * ldg, ldg, e, f, M, N, alpha, beta, C, ldc);
+    return launch_recombine(nslices, digit_bits, recombine_grid(M, N),
+                            reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M, N,
+                            alpha, beta, C, ldc);
 }
 
 alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -451,13 +497,14 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
                              size_t workspace_bytes, void* stream) {
     alp_status st = validate_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     if (st != ALP_OK) return st;
-    if (nslices < kMinSlices || nslices > kMaxSlices) return ALP_ERR_INVALID_ARG;
     if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
-    if (kind != ALP_SLICE_BF16) return ALP_ERR_INVALID_ARG;
+    const int b = digit_bits_of(kind);
+    if (b == 0) return ALP_ERR_INVALID_ARG;
+    if (nslices < kMinSlices || nslices > emul_max_slices(b)) return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (alpha == 0.0 || K == 0) return native_scale(M, N, beta, C, ldc, s);
-    if (K > kEmulMaxK || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
     const EmulLayout L = emul_layout(M, N, K, nslices);
     if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
         return ALP_ERR_WORKSPACE;
@@ -469,14 +516,14 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
     if ((st = emul_exponents(M, K, A, lda, 0, e, s)) != ALP_OK) return st;
     if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
-    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s)) != ALP_OK) return st;
-    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s)) != ALP_OK) return st;
+    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
+    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
     alp_config cfg;
     const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
     if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
-                              have ? cfg.stages : 0, have ? cfg.tm : 0)) != ALP_OK)
+                              have ? cfg.stages : 0, have ? cfg.tm : 0, b)) != ALP_OK)
         return st;
-    return launch_recombine(nslices, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
+    return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
                             alpha, beta, C, ldc);
 }
 

@@ -7,13 +7,20 @@
 
 namespace alp {
 
-constexpr int kDigitBits = 7;      // b: bits per digit; digits |d| <= 128 are exact in bf16
+// Digits of b bits, b = 7 (ALP_SLICE_BF16) or 8 (ALP_SLICE_BF16_B8): |d_1| <= 2^b,
+// |d_p| <= 2^(b-1), all exact in bf16 (integers up to 256).
+constexpr int kDigitBits = 7;
 constexpr int kMinSlices = 3;
-constexpr int kMaxSlices = 8;      // s * b <= 56 keeps the split's fixed point exact
+constexpr int kMaxSlices = 8;      // array bound; per digit width see emul_max_slices
 constexpr int kEmulBK = 64;        // K elements per pipeline stage (128 bytes of bf16)
-// Largest K per call: the int32 group sums |S^t| <= K * 2^12 * (t + 1) (t <= 9)
-// stay below 2^31 for K <= 32768.
+// Most slices per digit width: the split's 62-bit fixed point stays exact
+// while (s - 1) * b + 2 <= 62 - b.
+inline int emul_max_slices(int b) { return b == 8 ? 7 : 8; }
+// Largest K per call: the int32 group sums |S^t| <= K * 2^(2b-2) * (t + 1),
+// t <= s + 1, stay below 2^31 (b = 7: K <= 32768; b = 8: K <= 14336).
+inline int64_t emul_max_k(int b) { return b == 8 ? 14336 : 32768; }
 constexpr int64_t kEmulMaxK = 32768;
+inline bool emul_digit_bits_ok(int b) { return b == 7 || b == 8; }
 
 struct EmulLayout {
     int64_t kpad;    // K rounded up to kEmulBK (digit rows, zero filled)
@@ -29,7 +36,17 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s);
 // cluster: blocks per cluster sharing B tiles (1 or 2; 0 = default 1).
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream, int group_m = 0, int cluster = 0);
+                           cudaStream_t stream, int group_m = 0, int cluster = 0,
+                           int digit_bits = kDigitBits);
+
+// Tail split of the slice-product launch (see emul_gemm.cu): whole tiles for
+// blocks [0, n_full), then each remaining tile cut into `pieces` blocks by
+// group ranges t_lo[i]..t_hi[i].
+struct TailSplit {
+    int n_full, pieces;
+    int t_lo[8], t_hi[8];
+};
+TailSplit tail_split(int tiles, int s, int sms);
 
 // Configs of the emulated path: alp_config{128, 256, 64, cluster, 0, group_m}
 // with cluster in {1, 2} (blocks sharing each B tile) and group_m in

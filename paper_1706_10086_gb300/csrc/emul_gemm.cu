@@ -1,6 +1,8 @@
 // Slice products of the emulated FP64 GEMM on tcgen05 tensor cores.
 //
-// One thread block per 128 x 256 tile of C.  For every digit pair (p, q) with
+// One thread block per 128 x 256 tile of C, except in the last, partial wave
+// of blocks, whose tiles are each cut into up to 8 blocks by ranges of groups
+// t (tail_split below) so that wave ends sooner.  For every digit pair (p, q) with
 // p + q = t <= s + 1 (groups t ascending, p ascending) the block multiplies the
 // bf16 digit slices D_A^p (128 x K) and D_B^q (256 x K, K-major) in K chunks:
 //
@@ -59,6 +61,17 @@ static int emul_group_m() {
     return g;
 }
 
+// Whether the last partial wave is split (env ALP_EMUL_TAIL_SPLIT=0 turns it
+// off; default on).
+static bool emul_tail_split_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char* s = std::getenv("ALP_EMUL_TAIL_SPLIT");
+        on = (s && std::atoi(s) == 0) ? 0 : 1;
+    }
+    return on == 1;
+}
+
 namespace {
 
 constexpr int kTM = 128, kTN = 256, kTK = kEmulBK;
@@ -70,37 +83,47 @@ constexpr uint32_t kBTile = kTN * kTK * 2;
 constexpr uint32_t kStageBytes = kATile + kBTile;
 constexpr uint32_t kTmemCols = 2 * kTN;
 constexpr uint32_t kMagicBits = 0x4B400000u;   // bit pattern of 1.5 * 2^23 (see tmem_drain8_magic)
-constexpr int kMaxJobs = 2048;   // >= jobs of one tile at s = 8, K = 32768 (1696)
+constexpr int kMaxJobs = 2560;   // >= jobs of one tile: s = 8, b = 7, K = 32768: 1696;
+                                 // s = 7, b = 8, K = 14336: 2408
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/ + 4 * kMaxJobs;
 
 struct EmulGemmParams {
     int64_t M, N, K;
-    int s;
+    int s, digit_bits;
     int32_t* G;
     int64_t ldg, gplane;
     int tiles_m, tiles_n, group_m;
+    // tail split: blocks [0, n_full) take whole tiles; tiles n_full.. (the last,
+    // partial wave) are cut into `pieces` blocks each, piece i taking the
+    // groups t_lo..t_hi packed in byte i of t_ranges (t_lo | t_hi << 4).
+    // Groups write disjoint planes of G.
+    int n_full, pieces;
+    uint64_t t_ranges;
     uint64_t timeout_ns;
     int* err;
 };
 
-// K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^22.
-__device__ __forceinline__ int chunk_of(int p, int q) {
-    return (p == 1 && q == 1) ? 256 : (p == 1 || q == 1) ? 512 : 1024;
+// K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^22,
+// from the product bounds 2^(2b) (p = q = 1), 2^(2b-1) (one first digit),
+// 2^(2b-2) (none): 256 / 512 / 1024 for b = 7, 64 / 128 / 256 for b = 8.
+__host__ __device__ __forceinline__ int chunk_of(int p, int q, int b) {
+    const int e = (p == 1 && q == 1) ? 2 * b : (p == 1 || q == 1) ? 2 * b - 1 : 2 * b - 2;
+    return 1 << (22 - e);
 }
 
-// The fixed job order of one tile: groups t = 2..s+1, pairs p ascending
-// (q = t - p), K chunks ascending.  One 32-bit word per job: first k-block
+// The fixed job order of one tile (or of one piece of it, groups t_lo..t_hi):
+// groups t ascending, pairs p ascending (q = t - p), K chunks ascending.  One 32-bit word per job: first k-block
 // (bits 0..9), end k-block (10..19), p-1 (20..22), q-1 (23..25), last chunk
 // of its group (26).  Thread 0 writes the table into shared memory; every role
 // walks it.  Returns the number of jobs.
-__device__ int build_jobs(int s, int K, uint32_t* jobs) {
+__device__ int build_jobs(int s, int K, int b, int t_lo, int t_hi, uint32_t* jobs) {
     int n = 0;
     const int kblocks = (K + kTK - 1) / kTK;
-    for (int t = 2; t <= s + 1; ++t) {
+    for (int t = t_lo; t <= t_hi; ++t) {
         const int plo = (t - s > 1) ? t - s : 1, phi = (s < t - 1) ? s : t - 1;
         for (int p = plo; p <= phi; ++p) {
             const int q = t - p;
-            const int cb = chunk_of(p, q) / kTK;
+            const int cb = chunk_of(p, q, b) / kTK;
             for (int kb = 0; kb < kblocks; kb += cb) {
                 const int ke = (kb + cb < kblocks) ? kb + cb : kblocks;
                 const uint32_t last = (ke == kblocks && p == phi) ? 1u : 0u;
@@ -169,7 +192,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(done, 1);
         *abort_flag = 0;
-        *njobs_slot = build_jobs(prm.s, (int)prm.K, jobs);
+        int t_lo = 2, t_hi = prm.s + 1;
+        if ((int)blockIdx.x >= prm.n_full) {
+            const int pc = ((int)blockIdx.x - prm.n_full) % prm.pieces;
+            const uint32_t r = (uint32_t)(prm.t_ranges >> (8 * pc)) & 0xffu;
+            t_lo = (int)(r & 15u);
+            t_hi = (int)(r >> 4);
+        }
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, t_lo, t_hi, jobs);
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -194,7 +224,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     {
         const int tiles_mc = (prm.tiles_m + CL - 1) / CL;
         const int gm = prm.group_m / CL > 0 ? prm.group_m / CL : 1;
-        const int pid = (int)blockIdx.x / CL, in_group = gm * prm.tiles_n;
+        const int tile = (int)blockIdx.x < prm.n_full
+                             ? (int)blockIdx.x
+                             : prm.n_full + ((int)blockIdx.x - prm.n_full) / prm.pieces;
+        const int pid = tile / CL, in_group = gm * prm.tiles_n;
         const int first_m = (pid / in_group) * gm;
         const int gsz = min(tiles_mc - first_m, gm);
         const int local = pid % in_group;
@@ -339,18 +372,84 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Streaming multiprocessors of the current device (one block of this kernel
+// fits per SM).
+int num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
+
 }  // namespace
+
+// Tail split of a launch of `tiles` tiles on `sms` SMs (one block each): the
+// last, partial wave of r tiles becomes r * pieces blocks, pieces = the
+// largest count <= min(sms / r, s, 8) whose best cut of groups t = 2..s+1
+// (group t holds t-1 digit pairs) into contiguous ranges keeps the largest
+// piece smallest.  No split when the last wave is full or pieces < 2.
+TailSplit tail_split(int tiles, int s, int sms) {
+    TailSplit ts;
+    ts.n_full = tiles;
+    ts.pieces = 1;
+    for (int i = 0; i < 8; ++i) ts.t_lo[i] = ts.t_hi[i] = 0;
+    ts.t_lo[0] = 2;
+    ts.t_hi[0] = s + 1;
+    if (tiles <= 0 || sms <= 0 || s < 2) return ts;
+    const int r = tiles % sms == 0 ? sms : tiles % sms;
+    int k = sms / r;
+    if (k > s) k = s;
+    if (k > 8) k = 8;
+    if (k < 2 || r == sms) return ts;
+    // smallest threshold whose greedy contiguous cut needs <= k pieces
+    const int total = s * (s + 1) / 2;
+    for (int cap = s; cap <= total; ++cap) {
+        int lo[8], hi[8], n = 0, acc = 0;
+        bool fits = true;
+        for (int t = 2; t <= s + 1 && fits; ++t) {
+            const int w = t - 1;
+            if (n == 0 || acc + w > cap) {
+                if (n == k) fits = false;
+                else {
+                    lo[n] = t;
+                    hi[n] = t;
+                    ++n;
+                    acc = w;
+                }
+            } else {
+                hi[n - 1] = t;
+                acc += w;
+            }
+        }
+        if (!fits) continue;
+        ts.n_full = tiles - r;
+        ts.pieces = n;
+        for (int i = 0; i < n; ++i) {
+            ts.t_lo[i] = lo[i];
+            ts.t_hi[i] = hi[i];
+        }
+        if (n < 2) ts.n_full = tiles;
+        return ts;
+    }
+    return ts;
+}
 
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream, int group_m, int cluster) {
+                           cudaStream_t stream, int group_m, int cluster, int digit_bits) {
+    if (!emul_digit_bits_ok(digit_bits) || s > emul_max_slices(digit_bits) ||
+        K > emul_max_k(digit_bits))
+        return ALP_ERR_UNSUPPORTED;
     {   // the job table of one tile must fit its shared-memory slot
         const int64_t kblocks = (K + kTK - 1) / kTK;
         int64_t njobs = 0;
         for (int t = 2; t <= s + 1; ++t)
             for (int pp = (t - s > 1 ? t - s : 1); pp <= (s < t - 1 ? s : t - 1); ++pp) {
                 const int qq = t - pp;
-                const int64_t cb = ((pp == 1 && qq == 1) ? 256 : (pp == 1 || qq == 1) ? 512 : 1024) / kTK;
+                const int64_t cb = chunk_of(pp, qq, digit_bits) / kTK;
                 njobs += (kblocks + cb - 1) / cb;
             }
         if (njobs > kMaxJobs || kblocks > 1023) return ALP_ERR_UNSUPPORTED;
@@ -366,6 +465,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.N = N;
     p.K = K;
     p.s = s;
+    p.digit_bits = digit_bits;
     p.G = G;
     p.ldg = ldg;
     p.gplane = M * ldg;
@@ -376,11 +476,26 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.group_m = group_m > 0 ? group_m : emul_group_m();
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
+    const int tiles = (int)(tiles_m * tiles_n);
+    p.n_full = 0x7fffffff;   // every block a whole tile unless split below
+    p.pieces = 1;
+    p.t_ranges = 2u | (uint32_t)(s + 1) << 4;
+    if (cl == 1 && emul_tail_split_on()) {
+        const TailSplit ts = tail_split(tiles, s, num_sms());
+        p.n_full = ts.n_full;
+        p.pieces = ts.pieces;
+        p.t_ranges = 0;
+        for (int i = 0; i < ts.pieces; ++i)
+            p.t_ranges |= (uint64_t)(ts.t_lo[i] | ts.t_hi[i] << 4) << (8 * i);
+    }
     if (cl == 1) {
+        const int64_t grid = p.n_full >= tiles
+                                 ? (int64_t)tiles
+                                 : (int64_t)p.n_full + (int64_t)(tiles - p.n_full) * p.pieces;
         cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return cuda_status(e);
-        emul_gemm_kernel<1><<<(unsigned)(tiles_m * tiles_n), kThreads, kSmemBytes, stream>>>(ta, tb, p);
+        emul_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(ta, tb, p);
         return cuda_status(cudaGetLastError());
     }
     cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<2>,

@@ -198,10 +198,10 @@ def test_row_exponents_follow_frexp(orc):
 
 
 @pytest.mark.parametrize("phi", [0, 8, 32])
-def test_split_reconstructs_exactly(orc, phi):
+@pytest.mark.parametrize("s,b", [(8, 7), (7, 8)])
+def test_split_reconstructs_exactly(orc, phi, s, b):
     """sum_p d_p 2^(-p b) + r_s 2^(-s b) = A 2^-e exactly; digit bounds; each
     digit is the round-half-even of the exact scaled remainder."""
-    s, b = 8, orc.BF16_DIGIT_BITS
     A = inputs.scaled(60 + phi, 0, (6, 10), phi)
     A[0, 0] = 0.5 * 2.0 ** 3        # exact ties appear for short dyadics
     A[0, 1] = -0.75 * 2.0 ** 3
@@ -232,18 +232,18 @@ def emul_budget(alpha, beta, C, e, f, K, s, b, out):
     return t + 3 * U * np.abs(out) + (U * np.abs(beta * C) if beta != 0 else 0.0) + 1e-300
 
 
-@pytest.mark.parametrize("s", [3, 5, 8])
+@pytest.mark.parametrize("s,b", [(3, 7), (5, 7), (8, 7), (3, 8), (6, 8), (7, 8)])
 @pytest.mark.parametrize("phi", [0, 8])
-def test_emul_gemm_within_derived_bound(orc, s, phi):
+def test_emul_gemm_within_derived_bound(orc, s, b, phi):
     M, N, K = 5, 4, 23
     A, B, C = inputs.gemm_operands(70 + s + phi, M, N, K, kind="scaled", phi=phi)
     alpha, beta = 1.5, 0.5
-    D, rc = orc.emul_gemm(alpha, A, B, beta, C, s)
+    D, rc = orc.emul_gemm(alpha, A, B, beta, C, s, b=b)
     assert rc == 0
     E = exact_gemm(alpha, A, B, beta, C)
     e, _ = orc.row_exponents(A)
     f, _ = orc.col_exponents(B)
-    bud = emul_budget(alpha, beta, C, e, f, K, s, orc.BF16_DIGIT_BITS, D)
+    bud = emul_budget(alpha, beta, C, e, f, K, s, b, D)
     for i in range(M):
         for j in range(N):
             assert abs(Fraction(D[i, j]) - E[i][j]) <= Fraction(bud[i, j]), (i, j, s, phi)
@@ -288,13 +288,14 @@ def fraction_emul(alpha, A, B, beta, C, s, b):
     return out
 
 
-@pytest.mark.parametrize("s,phi", [(3, 0), (6, 8), (8, 0), (8, 32)])
-def test_emul_gemm_bit_exact_against_rationals(orc, s, phi):
+@pytest.mark.parametrize("s,b,phi", [(3, 7, 0), (6, 7, 8), (8, 7, 0), (8, 7, 32), (3, 8, 0),
+                                     (6, 8, 8), (7, 8, 32)])
+def test_emul_gemm_bit_exact_against_rationals(orc, s, b, phi):
     M, N, K = 4, 3, 9
     A, B, C = inputs.gemm_operands(90 + s + phi, M, N, K, kind="scaled", phi=phi)
-    D, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s)
+    D, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s, b=b)
     assert rc == 0
-    ref = fraction_emul(1.5, A, B, 0.5, C, s, orc.BF16_DIGIT_BITS)
+    ref = fraction_emul(1.5, A, B, 0.5, C, s, b)
     assert np.array_equal(D, ref)
 
 
