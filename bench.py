@@ -41,6 +41,9 @@ UNIT = "TFLOP/s"
 KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_gb300/csrc/tc.cuh",
                   "paper_1706_10086_gb300/csrc/emul.cuh")
 TRAFFIC_PROFILE = "profiles/emul_gemm_kernel_8192.md"
+# slice kinds of alp_gemm_f64_emul: name -> (enum value, digit pairs for s slices)
+KINDS = {"bf16": (1, lambda s: s * (s + 1) // 2), "bf16_b8": (2, lambda s: s * (s + 1) // 2),
+         "bf16_b8_trim": (3, lambda s: s * (s - 1) // 2 + 2)}
 
 
 def parse_args():
@@ -54,8 +57,10 @@ def parse_args():
                     help="digit slices; 7 is no less accurate than native FP64 for the default "
                          "uniform inputs (checked live against 8 slices), 8 for wide exponent "
                          "ranges")
-    ap.add_argument("--digit-bits", type=int, choices=(7, 8), default=7,
-                    help="bits per digit slice: 7 (up to 8 slices) or 8 (up to 7 slices)")
+    ap.add_argument("--kind", choices=tuple(KINDS), default="bf16",
+                    help="digit scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
+                         "up to 7), bf16_b8_trim (8-bit, last group keeps only its two "
+                         "leading-digit pairs)")
     ap.add_argument("--phi", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
@@ -211,8 +216,8 @@ def cpu_oracle_sample(A_rows, B, alpha, target_s):
     return flops / dt / 1e12, rows, dt, n_threads
 
 
-def workload_name(n, s, b, phi):
-    return f"emulated_dgemm_{n}_bf16x{s}slices{'' if b == 7 else f'_{b}bit'}_phi{phi}"
+def workload_name(n, s, kind, phi):
+    return f"emulated_dgemm_{n}_{kind}x{s}slices_phi{phi}"
 
 
 def make_inputs(torch, n, phi, seed, device):
@@ -240,8 +245,8 @@ def run_alp(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
-    n, s, phi, b = args.n, args.nslices, args.phi, args.digit_bits
-    kind = alp.ALP_SLICE_BF16 if b == 7 else alp.ALP_SLICE_BF16_B8
+    n, s, phi = args.n, args.nslices, args.phi
+    kind, pairs_of = KINDS[args.kind]
     M = N = K = n
     seed = 1706 + 2
     A, B = make_inputs(torch, n, phi, seed, dev)
@@ -266,13 +271,13 @@ def run_alp(args):
         rec(1)
         alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
         rec(2)
-        alp.alp_emul_split(M, K, A, K, 0, e, s, b, da, kpad, stream)
+        alp.alp_emul_split(M, K, A, K, 0, e, s, kind, da, kpad, stream)
         rec(3)
-        alp.alp_emul_split(N, K, B, N, 1, f, s, b, db, kpad, stream)
+        alp.alp_emul_split(N, K, B, N, 1, f, s, kind, db, kpad, stream)
         rec(4)
-        alp.alp_emul_slice_products(M, N, K, s, b, da, db, kpad, G, ldg, stream)
+        alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
         rec(5)
-        alp.alp_emul_recombine(M, N, s, b, G, ldg, e, f, alpha, beta, C, N, stream)
+        alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)
         rec(6)
 
     for _ in range(max(3, args.warmup)):
@@ -309,7 +314,7 @@ def run_alp(args):
     total_ms, total_flops = aggregate_over_ranks(total_ms, args.steps * flops_step,
                                                  dist if ws > 1 else None, dev)
     value = total_flops / (total_ms * 1e-3) / 1e12
-    pairs = s * (s + 1) // 2
+    pairs = pairs_of(s)
     kern_avg = statistics.mean(kern_ms)
     peaks, peak_kind = load_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
@@ -327,9 +332,9 @@ def run_alp(args):
            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
            "data": "synthetic (seeded torch generator on the GPU; u*2^e, u~U[-1,1), e~U{-phi..phi})",
-           "config": {"workload": workload_name(n, s, b, phi), "M": M, "N": N,
-                      "K": K, "nslices": s, "digit_bits": b, "phi": phi, "alpha": alpha,
-                      "beta": beta,
+           "config": {"workload": workload_name(n, s, args.kind, phi), "M": M, "N": N,
+                      "K": K, "nslices": s, "slice_kind": args.kind, "digit_pairs": pairs,
+                      "phi": phi, "alpha": alpha, "beta": beta,
                       "result_dtype": "f64", "parallelism": f"replicas{ws}",
                       "l2": "inputs 1.5 GB > 129 MB L2; no flush"},
            "step_ms_median": round(statistics.median(step_ms), 3),
@@ -505,7 +510,7 @@ def run_reference(args):
            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double accumulation)",
            "data": "synthetic (seeded SplitMix64, uniform [-1,1))",
-           "config": {"workload": workload_name(n, args.nslices, args.digit_bits, args.phi),
+           "config": {"workload": workload_name(n, args.nslices, args.kind, args.phi),
                       "M": n, "N": n,
                       "K": n, "sample_rows_per_step": rows_per_step},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",

@@ -56,7 +56,9 @@ typedef enum alp_status {
 typedef enum alp_slice_kind {
     ALP_SLICE_INT8 = 0,        /* not available on sm_103a: tcgen05 has no kind::i8 there */
     ALP_SLICE_BF16 = 1,        /* digits of 7 bits held exactly in bf16; 3..8 slices, K <= 32768 */
-    ALP_SLICE_BF16_B8 = 2      /* digits of 8 bits held exactly in bf16; 3..7 slices, K <= 14336 */
+    ALP_SLICE_BF16_B8 = 2,     /* digits of 8 bits held exactly in bf16; 3..7 slices, K <= 14336 */
+    ALP_SLICE_BF16_B8_TRIM = 3 /* as ALP_SLICE_BF16_B8, but the last group t = nslices+1 keeps
+                                  only the pairs with a leading digit, (1, s) and (s, 1) */
 } alp_slice_kind;
 
 typedef enum alp_path { ALP_PATH_NATIVE = 0, ALP_PATH_EMUL = 1 } alp_path;
@@ -106,13 +108,15 @@ alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha,
  * max_k |A_ik|; every A_ik * 2^-e_i is cut into `nslices` digits of b bits
  * (b = 7 for ALP_SLICE_BF16, 8 for ALP_SLICE_BF16_B8; round to nearest even,
  * held exactly in bf16); likewise the columns of B with exponents f_j.  The
- * slice products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..nslices+1, run on
+ * slice products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..nslices+1 (for
+ * ALP_SLICE_BF16_B8_TRIM, S^(nslices+1) sums only the pairs (1, nslices) and
+ * (nslices, 1): s(s-1)/2 + 2 products instead of s(s+1)/2), run on
  * tcgen05 tensor cores with exact integer-valued fp32 partial sums (drained
  * every 2^(22-2b)..2^(24-2b) k into int32), and are recombined exactly and
  * rounded once to FP64:
  *   X = sum_t S^t 2^(b(nslices+1-t)),  C = alpha * (X rounded to nearest,
  *   times 2^(e_i + f_j - b(nslices+1)))  (+ fma(beta, C, .) when beta != 0).
- * nslices in 3..8 (b = 7) or 3..7 (b = 8).  ALP_SLICE_INT8 returns
+ * nslices in 3..8 (b = 7) or 3..7 (b = 8, either kind).  ALP_SLICE_INT8 returns
  * ALP_ERR_UNSUPPORTED on sm_103a, whose tcgen05 has no kind::i8.
  * K <= 32768 (b = 7) or 14336 (b = 8) (int32 group sums; larger K returns
  * ALP_ERR_UNSUPPORTED).
@@ -140,27 +144,30 @@ size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
  * row-major R x K matrix given its per-row exponents, written as bf16 to
  * out[p][r][k] (p = 0..nslices-1, row stride kpad elements, kpad >= K, zero
  * filled beyond K); for a K x N row-major B pass trans = 1, R = N and the
- * result is the transposed digit matrix out[p][n][k].  digit_bits is b, 7 or 8.
+ * result is the transposed digit matrix out[p][n][k].  kind fixes b (7 for
+ * ALP_SLICE_BF16, 8 for the other two); every stage of one product takes the
+ * same kind.
  */
 alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx,
                               int trans, int32_t* exps, void* stream);
 alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
-                          const int32_t* exps, int nslices, int digit_bits, void* out_bf16,
+                          const int32_t* exps, int nslices, alp_slice_kind kind, void* out_bf16,
                           int64_t kpad, void* stream);
 /* alp_emul_slice_products: the tensor-core stage, S^t = sum_{p+q=t}
  * D_A^p (D_B^q)^T for t = 2..nslices+1 as exact int32 into
  * G[t-2][m][n] (row stride ldg, ldg a multiple of 256 and >= N; plane stride
  * M*ldg), from digit slices da[p][m][k] (M x kpad) and db[p][n][k] (N x kpad)
- * as written by alp_emul_split with the same digit_bits; kpad a multiple of
+ * as written by alp_emul_split with the same kind (ALP_SLICE_BF16_B8_TRIM:
+ * the last group sums only its two leading-digit pairs); kpad a multiple of
  * 64, K <= 32768 (b = 7) or 14336 (b = 8).
  * alp_emul_recombine: C = alpha * round(sum_t S^t 2^(b(nslices+1-t))) *
  * 2^(e_i + f_j - b(nslices+1)) (+ fma(beta, C, .)) from those sums. */
-alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices, int digit_bits,
-                                   const void* da_bf16, const void* db_bf16, int64_t kpad,
-                                   int32_t* G, int64_t ldg, void* stream);
-alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, int digit_bits, const int32_t* G,
-                              int64_t ldg, const int32_t* e, const int32_t* f, double alpha,
-                              double beta, double* C, int64_t ldc, void* stream);
+alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind, const void* da_bf16, const void* db_bf16,
+                                   int64_t kpad, int32_t* G, int64_t ldg, void* stream);
+alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
+                              const int32_t* G, int64_t ldg, const int32_t* e, const int32_t* f,
+                              double alpha, double beta, double* C, int64_t ldc, void* stream);
 
 /*
  * Batched variable-size native GEMM: `count` independent problems

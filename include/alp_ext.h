@@ -162,11 +162,13 @@ alp_status alp_gemm_batched_varsize_noalloc(int64_t count, const int64_t* dM, co
  * not share B tiles.  Blocks [0, *n_full) take whole tiles; each remaining
  * tile (the last, partial wave) is taken by *pieces blocks, piece i computing
  * the group sums S^t for t = t_lo[i]..t_hi[i] (arrays of 8).  The cut is the
- * contiguous one whose largest piece (in digit pairs) is smallest, with at most
+ * contiguous one whose largest piece (in digit pairs of the kind's scheme:
+ * group t holds t-1 pairs, or 2 when it is the trimmed last group) is
+ * smallest, with at most
  * min(sms / r, nslices, 8) pieces for r tiles in the last wave.  Splitting the
  * groups changes no result: each group sum is exact and written once. */
-alp_status alp_emul_tail_split(int tiles, int nslices, int sms, int* n_full, int* pieces,
-                               int* t_lo, int* t_hi);
+alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,
+                               int* pieces, int* t_lo, int* t_hi);
 
 /* ---- FP64 peak probe ----------------------------------------------------- */
 

@@ -55,7 +55,7 @@ def lib():
             L.orc_col_exponents.argtypes = [i64, i64, vp, i64, vp]
             L.orc_split.argtypes = [i64, i64, vp, i64, vp, i32, i32, vp, vp]
             L.orc_emul_gemm.argtypes = [i64, i64, i64, f64, vp, i64, vp, i64, f64, vp, i64,
-                                        vp, i64, i32, i32, vp, i64, i32]
+                                        vp, i64, i32, i32, i32, vp, i64, i32]
             L.orc_int128_to_double.argtypes = [i64, ctypes.c_uint64]
             L.orc_int128_to_double.restype = ctypes.c_double
             for fn in ("orc_gemm_f64", "orc_absgemm", "orc_row_exponents", "orc_col_exponents",
@@ -145,8 +145,9 @@ def split(X, e, s, b=BF16_DIGIT_BITS):
     return d, rem
 
 
-def emul_gemm(alpha, A, B, beta, C, s, b=BF16_DIGIT_BITS, rows=None, nthreads=None):
-    """The emulated FP64 GEMM, bit-exact model of the GPU path.
+def emul_gemm(alpha, A, B, beta, C, s, b=BF16_DIGIT_BITS, rows=None, nthreads=None, trim=False):
+    """The emulated FP64 GEMM, bit-exact model of the GPU path.  ``trim``: the
+    last group t = s+1 keeps only the pairs (1, s) and (s, 1).
 
     Returns (D, status): status 0 on success, 2 when A or B holds Inf/NaN."""
     A, B = _f64(A), _f64(B)
@@ -159,7 +160,8 @@ def emul_gemm(alpha, A, B, beta, C, s, b=BF16_DIGIT_BITS, rows=None, nthreads=No
     nr = M if ridx is None else len(ridx)
     D = np.empty((nr, N))
     rc = lib().orc_emul_gemm(M, N, K, float(alpha), _ptr(A), K, _ptr(B), N, float(beta),
-                             _ptr(C), N, _ptr(D), N, int(s), int(b), _ptr(ridx), nr,
+                             _ptr(C), N, _ptr(D), N, int(s), int(b), int(bool(trim)),
+                             _ptr(ridx), nr,
                              _threads(nthreads))
     assert rc in (0, 2), rc
     return D, rc

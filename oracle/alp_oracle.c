@@ -138,6 +138,8 @@ int orc_absgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
 /*  digits   for p = 1..s:  x = r_{p-1} * 2^b,  d_p = nearest integer to x   */
 /*           (ties to even),  r_p = x - d_p.  All steps are exact in FP64.   */
 /*  products S^t = sum_{p+q=t} D_A^p (D_B^q)^T, t = 2..s+1, exact integers.  */
+/*           Trimmed variant (trim = 1): the last group t = s+1 keeps only   */
+/*           the pairs with a leading digit, (1, s) and (s, 1).              */
 /*  combine  X = sum_t S^t 2^((s+1-t) b)  exactly (an integer below 2^100),  */
 /*           v = X rounded once to the nearest double (ties to even),        */
 /*           w = v * 2^(e_i + f_j - (s+1) b)  (one rounding if subnormal),   */
@@ -219,7 +221,7 @@ typedef struct {
     double* D;
     int64_t ldd;
     const int64_t* rows;
-    int s, b;
+    int s, b, trim;
     const int16_t *dA, *dB;   /* [s][nrows][K] (row r of the output), [s][N][K] */
     int64_t nra;
     const int32_t *e, *f;
@@ -241,6 +243,7 @@ static void emul_row(void* p, int64_t r) {
             for (int pa = 1; pa <= s; ++pa) {
                 int qb = t - pa;
                 if (qb < 1 || qb > s) continue;
+                if (g->trim && t == s + 1 && pa != 1 && qb != 1) continue;
                 const int16_t* a = g->dA + ((int64_t)(pa - 1) * g->nra + r) * g->K;
                 const int16_t* bb = g->dB + ((int64_t)(qb - 1) * g->N + j) * g->K;
                 for (int64_t k = 0; k < g->K; ++k) S += (int64_t)a[k] * (int64_t)bb[k];
@@ -274,15 +277,17 @@ static void split_row(void* p, int64_t r) {
     }
 }
 
-/* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range).
- * Returns 0, or 2 when A or B holds an Inf or NaN (the emulated path does not
- * support them), 1 on bad sizes. */
+/* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range);
+ * trim = 1 selects the trimmed last group.  Returns 0, or 2 when A or B holds
+ * an Inf or NaN (the emulated path does not support them), 1 on bad sizes. */
 int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb,
                   double beta, const double* C, int64_t ldc,
-                  double* D, int64_t ldd, int s, int b,
+                  double* D, int64_t ldd, int s, int b, int trim,
                   const int64_t* rows, int64_t nrows, int nthreads) {
-    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 15 || s * b > 90) return 1;
+    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 15 || s * b > 90 ||
+        (trim != 0 && trim != 1))
+        return 1;
     const int64_t nra = rows ? nrows : M;
     int32_t* e = (int32_t*)calloc((size_t)(M > 0 ? M : 1), sizeof(int32_t));
     int32_t* f = (int32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
@@ -299,7 +304,7 @@ int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
     for_rows(nra, nthreads, split_row, &sa);
     split_ctx sb = {Bt, K, K, f, NULL, s, b, dB, N};
     for_rows(N, nthreads, split_row, &sb);
-    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, dA, dB, nra, e, f};
+    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, trim, dA, dB, nra, e, f};
     for_rows(nra, nthreads, emul_row, &g);
     free(Bt); free(dA); free(dB); free(e); free(f);
     return 0;

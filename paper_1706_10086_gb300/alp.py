@@ -28,6 +28,7 @@ ALP_ERR_NOT_TUNED = 6
 ALP_SLICE_INT8 = 0
 ALP_SLICE_BF16 = 1
 ALP_SLICE_BF16_B8 = 2
+ALP_SLICE_BF16_B8_TRIM = 3
 # alp_path
 ALP_PATH_NATIVE = 0
 ALP_PATH_EMUL = 1
@@ -86,7 +87,7 @@ _SIGS = {
     "alp_set_wait_timeout_ms": ([_f64], _int),
     "alp_debug_inject_skip": ([_int], _int),
     "alp_probe_fp64_peak": ([_int, _i64, _int, _int, ctypes.POINTER(_f64), _vp], _int),
-    "alp_emul_tail_split": ([_int, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
+    "alp_emul_tail_split": ([_int, _int, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_int),
                              ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
     "alp_tune_time_config": ([_i64, _i64, _i64, _int, ctypes.POINTER(alp_config), _int, _int,
                               ctypes.POINTER(_f64)], _int),
@@ -195,23 +196,23 @@ def alp_emul_exponents(rows, cols, X, ldx, trans, exps, stream=None, raise_on_er
     return _check(st, "alp_emul_exponents", raise_on_error)
 
 
-def alp_emul_split(R, K, X, ldx, trans, exps, nslices, digit_bits, out, kpad, stream=None,
+def alp_emul_split(R, K, X, ldx, trans, exps, nslices, kind, out, kpad, stream=None,
                    raise_on_error=True):
-    st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices),
-                              int(digit_bits), _p(out), kpad, _s(stream))
+    st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices), int(kind),
+                              _p(out), kpad, _s(stream))
     return _check(st, "alp_emul_split", raise_on_error)
 
 
-def alp_emul_slice_products(M, N, K, nslices, digit_bits, da, db, kpad, G, ldg, stream=None,
+def alp_emul_slice_products(M, N, K, nslices, kind, da, db, kpad, G, ldg, stream=None,
                             raise_on_error=True):
-    st = lib().alp_emul_slice_products(M, N, K, int(nslices), int(digit_bits), _p(da), _p(db),
-                                       kpad, _p(G), ldg, _s(stream))
+    st = lib().alp_emul_slice_products(M, N, K, int(nslices), int(kind), _p(da), _p(db), kpad,
+                                       _p(G), ldg, _s(stream))
     return _check(st, "alp_emul_slice_products", raise_on_error)
 
 
-def alp_emul_recombine(M, N, nslices, digit_bits, G, ldg, e, f, alpha, beta, C, ldc,
-                       stream=None, raise_on_error=True):
-    st = lib().alp_emul_recombine(M, N, int(nslices), int(digit_bits), _p(G), ldg, _p(e), _p(f),
+def alp_emul_recombine(M, N, nslices, kind, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
+                       raise_on_error=True):
+    st = lib().alp_emul_recombine(M, N, int(nslices), int(kind), _p(G), ldg, _p(e), _p(f),
                                   float(alpha), float(beta), _p(C), ldc, _s(stream))
     return _check(st, "alp_emul_recombine", raise_on_error)
 
@@ -291,11 +292,12 @@ def alp_probe_fp64_peak(kind=0, iters=20000, blocks_per_sm=2, threads=256, strea
     return out.value
 
 
-def alp_emul_tail_split(tiles, nslices, sms):
+def alp_emul_tail_split(tiles, nslices, kind, sms):
     """(n_full, [(t_lo, t_hi) per piece]) of the slice-product launch."""
     n_full, pieces = ctypes.c_int(0), ctypes.c_int(0)
     lo, hi = (_int * 8)(), (_int * 8)()
-    _check(lib().alp_emul_tail_split(int(tiles), int(nslices), int(sms), ctypes.byref(n_full),
+    _check(lib().alp_emul_tail_split(int(tiles), int(nslices), int(kind), int(sms),
+                                     ctypes.byref(n_full),
                                      ctypes.byref(pieces), lo, hi), "alp_emul_tail_split", True)
     return n_full.value, [(lo[i], hi[i]) for i in range(pieces.value)]
 

@@ -414,23 +414,22 @@ using namespace alp;
 
 extern "C" {
 
-static int digit_bits_of(alp_slice_kind kind) {
-    return kind == ALP_SLICE_BF16 ? 7 : kind == ALP_SLICE_BF16_B8 ? 8 : 0;
-}
-
 size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind) {
-    const int b = digit_bits_of(kind);
-    if (M < 0 || N < 0 || K < 0 || b == 0 || nslices < kMinSlices || nslices > emul_max_slices(b))
+    EmulScheme sc;
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < kMinSlices ||
+        nslices > emul_max_slices(sc.b))
         return 0;
     return emul_layout(M, N, K, nslices).bytes;
 }
 
-alp_status alp_emul_tail_split(int tiles, int nslices, int sms, int* n_full, int* pieces,
-                               int* t_lo, int* t_hi) {
-    if (tiles < 0 || nslices < 1 || nslices > 8 || sms < 1 || !n_full || !pieces || !t_lo || !t_hi)
+alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,
+                               int* pieces, int* t_lo, int* t_hi) {
+    EmulScheme sc;
+    if (tiles < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 || nslices > emul_max_slices(sc.b) ||
+        sms < 1 || !n_full || !pieces || !t_lo || !t_hi)
         return ALP_ERR_INVALID_ARG;
-    const TailSplit ts = tail_split(tiles, nslices, sms);
+    const TailSplit ts = tail_split(tiles, nslices, sms, sc.trim);
     *n_full = ts.n_full;
     *pieces = ts.pieces;
     for (int i = 0; i < 8; ++i) {
@@ -450,10 +449,11 @@ alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64
 }
 
 alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
-                          const int32_t* exps, int nslices, int digit_bits, void* out_bf16,
+                          const int32_t* exps, int nslices, alp_slice_kind kind, void* out_bf16,
                           int64_t kpad, void* stream) {
-    if (R < 0 || K < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
-        nslices > emul_max_slices(digit_bits) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
+    EmulScheme sc;
+    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > emul_max_slices(sc.b) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
         (R > 0 && K > 0 && !X))
         return ALP_ERR_INVALID_ARG;
     if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
@@ -461,32 +461,34 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
     if (R == 0 || kpad == 0) return ALP_OK;
     return emul_split(R, K, X, ldx, trans, exps, nslices,
                       reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
-                      reinterpret_cast<cudaStream_t>(stream), digit_bits);
+                      reinterpret_cast<cudaStream_t>(stream), sc.b);
 }
 
-alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices, int digit_bits,
-                                   const void* da_bf16, const void* db_bf16, int64_t kpad,
-                                   int32_t* G, int64_t ldg, void* stream) {
-    if (M < 0 || N < 0 || K < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
-        nslices > emul_max_slices(digit_bits) || kpad < K || kpad % kEmulBK || ldg < N ||
-        ldg % 256 || K > emul_max_k(digit_bits))
+alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind, const void* da_bf16, const void* db_bf16,
+                                   int64_t kpad, int32_t* G, int64_t ldg, void* stream) {
+    EmulScheme sc;
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > emul_max_slices(sc.b) || kpad < K || kpad % kEmulBK || ldg < N ||
+        ldg % 256 || K > emul_max_k(sc.b))
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0 || K == 0) return ALP_OK;
     if (!da_bf16 || !db_bf16 || !G) return ALP_ERR_INVALID_ARG;
     return emul_slice_gemm(M, N, K, nslices, reinterpret_cast<const __nv_bfloat16*>(da_bf16),
                            reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, G, ldg,
-                           reinterpret_cast<cudaStream_t>(stream), 0, 0, digit_bits);
+                           reinterpret_cast<cudaStream_t>(stream), 0, 0, sc.b, sc.trim);
 }
 
-alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, int digit_bits, const int32_t* G,
-                              int64_t ldg, const int32_t* e, const int32_t* f, double alpha,
-                              double beta, double* C, int64_t ldc, void* stream) {
-    if (M < 0 || N < 0 || !emul_digit_bits_ok(digit_bits) || nslices < 1 ||
-        nslices > emul_max_slices(digit_bits) || ldg < N || ldc < N)
+alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
+                              const int32_t* G, int64_t ldg, const int32_t* e, const int32_t* f,
+                              double alpha, double beta, double* C, int64_t ldc, void* stream) {
+    EmulScheme sc;
+    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > emul_max_slices(sc.b) || ldg < N || ldc < N)
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
-    return launch_recombine(nslices, digit_bits, recombine_grid(M, N),
+    return launch_recombine(nslices, sc.b, recombine_grid(M, N),
                             reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M, N,
                             alpha, beta, C, ldc);
 }
@@ -498,8 +500,9 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     alp_status st = validate_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     if (st != ALP_OK) return st;
     if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
-    const int b = digit_bits_of(kind);
-    if (b == 0) return ALP_ERR_INVALID_ARG;
+    EmulScheme sc;
+    if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
+    const int b = sc.b;
     if (nslices < kMinSlices || nslices > emul_max_slices(b)) return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -521,7 +524,7 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     alp_config cfg;
     const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
     if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
-                              have ? cfg.stages : 0, have ? cfg.tm : 0, b)) != ALP_OK)
+                              have ? cfg.stages : 0, have ? cfg.tm : 0, b, sc.trim)) != ALP_OK)
         return st;
     return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
                             alpha, beta, C, ldc);

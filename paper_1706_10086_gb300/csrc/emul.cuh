@@ -22,6 +22,25 @@ inline int64_t emul_max_k(int b) { return b == 8 ? 14336 : 32768; }
 constexpr int64_t kEmulMaxK = 32768;
 inline bool emul_digit_bits_ok(int b) { return b == 7 || b == 8; }
 
+// The digit scheme of a slice kind: b bits per digit, and whether the last
+// group t = s+1 is trimmed to its pairs with a leading digit, (1, s) and (s, 1).
+struct EmulScheme {
+    int b;
+    bool trim;
+};
+inline bool emul_scheme_of(int kind, EmulScheme* sc) {
+    switch (kind) {
+        case ALP_SLICE_BF16: *sc = {7, false}; return true;
+        case ALP_SLICE_BF16_B8: *sc = {8, false}; return true;
+        case ALP_SLICE_BF16_B8_TRIM: *sc = {8, true}; return true;
+        default: return false;
+    }
+}
+// Whether digit pair (p, q) of group t = p + q is multiplied.
+__host__ __device__ inline bool emul_pair_kept(int p, int q, int s, bool trim) {
+    return p + q <= s + 1 && (!trim || p + q <= s || p == 1 || q == 1);
+}
+
 struct EmulLayout {
     int64_t kpad;    // K rounded up to kEmulBK (digit rows, zero filled)
     int64_t ldg;     // row stride of the int32 group sums (N rounded up to 256)
@@ -37,7 +56,7 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s);
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
                            cudaStream_t stream, int group_m = 0, int cluster = 0,
-                           int digit_bits = kDigitBits);
+                           int digit_bits = kDigitBits, bool trim = false);
 
 // Tail split of the slice-product launch (see emul_gemm.cu): whole tiles for
 // blocks [0, n_full), then each remaining tile cut into `pieces` blocks by
@@ -46,7 +65,7 @@ struct TailSplit {
     int n_full, pieces;
     int t_lo[8], t_hi[8];
 };
-TailSplit tail_split(int tiles, int s, int sms);
+TailSplit tail_split(int tiles, int s, int sms, bool trim = false);
 
 // Configs of the emulated path: alp_config{128, 256, 64, cluster, 0, group_m}
 // with cluster in {1, 2} (blocks sharing each B tile) and group_m in

@@ -15,14 +15,15 @@
 //   warps 2-9   drain a finished chunk from TMEM (tcgen05.ld) while the other
 //               accumulator fills, and add it exactly into int32 registers.
 //
-// Exactness: digits satisfy |d_1| <= 2^7, |d_p| <= 2^6 (p >= 2), so a chunk of
-// 256 (pair 1,1), 512 (one first digit) or 1024 (no first digit) products has
-// |partial sum| <= 2^22: every partial sum is an integer that f32 holds
-// exactly.  The drain adds 1.5 * 2^23 to the f32 value, whose bit pattern then
-// is 0x4B400000 + x for |x| <= 2^22; the int32 sum of those patterns minus
-// (chunks * 0x4B400000) is the exact group sum S^t (mod 2^32 arithmetic, and
-// |S^t| < 2^31 for K <= 32768).  At the end of each group the block writes S^t
-// to G[t-2] (int32).
+// Exactness: digits satisfy |d_1| <= 2^b, |d_p| <= 2^(b-1) (p >= 2), so a
+// chunk of 2^(24-2b) (pair 1,1), 2^(25-2b) (one first digit) or 2^(26-2b) (no
+// first digit) products -- 1024 / 2048 / 4096 for b = 7, 256 / 512 / 1024 for
+// b = 8 -- has |partial sum| <= 2^24: every value the f32 accumulator takes
+// is an integer f32 holds exactly, so no MMA rounds.  The drain converts each
+// chunk's integer exactly into a 32-bit running sum (tmem_drain32_exact); the
+// sum minus chunks * kChunkBias is the exact group sum S^t (mod 2^32
+// arithmetic, and |S^t| < 2^31 for the K limits).  At the end of each group
+// the block writes S^t to G[t-2] (int32).
 #include <cstdlib>
 
 #include "emul.cuh"
@@ -82,14 +83,13 @@ constexpr uint32_t kATile = kTM * kTK * 2;
 constexpr uint32_t kBTile = kTN * kTK * 2;
 constexpr uint32_t kStageBytes = kATile + kBTile;
 constexpr uint32_t kTmemCols = 2 * kTN;
-constexpr uint32_t kMagicBits = 0x4B400000u;   // bit pattern of 1.5 * 2^23 (see tmem_drain8_magic)
-constexpr int kMaxJobs = 2560;   // >= jobs of one tile: s = 8, b = 7, K = 32768: 1696;
-                                 // s = 7, b = 8, K = 14336: 2408
+constexpr int kMaxJobs = 1024;   // >= jobs of one tile: s = 8, b = 7, K = 32768: 424;
+                                 // s = 7, b = 8, K = 14336: 602
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/ + 4 * kMaxJobs;
 
 struct EmulGemmParams {
     int64_t M, N, K;
-    int s, digit_bits;
+    int s, digit_bits, trim;
     int32_t* G;
     int64_t ldg, gplane;
     int tiles_m, tiles_n, group_m;
@@ -103,12 +103,12 @@ struct EmulGemmParams {
     int* err;
 };
 
-// K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^22,
+// K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^24,
 // from the product bounds 2^(2b) (p = q = 1), 2^(2b-1) (one first digit),
-// 2^(2b-2) (none): 256 / 512 / 1024 for b = 7, 64 / 128 / 256 for b = 8.
+// 2^(2b-2) (none): 1024 / 2048 / 4096 for b = 7, 256 / 512 / 1024 for b = 8.
 __host__ __device__ __forceinline__ int chunk_of(int p, int q, int b) {
     const int e = (p == 1 && q == 1) ? 2 * b : (p == 1 || q == 1) ? 2 * b - 1 : 2 * b - 2;
-    return 1 << (22 - e);
+    return 1 << (24 - e);
 }
 
 // The fixed job order of one tile (or of one piece of it, groups t_lo..t_hi):
@@ -116,13 +116,16 @@ __host__ __device__ __forceinline__ int chunk_of(int p, int q, int b) {
 // (bits 0..9), end k-block (10..19), p-1 (20..22), q-1 (23..25), last chunk
 // of its group (26).  Thread 0 writes the table into shared memory; every role
 // walks it.  Returns the number of jobs.
-__device__ int build_jobs(int s, int K, int b, int t_lo, int t_hi, uint32_t* jobs) {
+__device__ int build_jobs(int s, int K, int b, bool trim, int t_lo, int t_hi, uint32_t* jobs) {
     int n = 0;
     const int kblocks = (K + kTK - 1) / kTK;
     for (int t = t_lo; t <= t_hi; ++t) {
-        const int plo = (t - s > 1) ? t - s : 1, phi = (s < t - 1) ? s : t - 1;
+        const int plo = (t - s > 1) ? t - s : 1;
+        int phi = (s < t - 1) ? s : t - 1;
+        while (phi > plo && !emul_pair_kept(phi, t - phi, s, trim)) --phi;   // last kept pair
         for (int p = plo; p <= phi; ++p) {
             const int q = t - p;
+            if (!emul_pair_kept(p, q, s, trim)) continue;
             const int cb = chunk_of(p, q, b) / kTK;
             for (int kb = 0; kb < kblocks; kb += cb) {
                 const int ke = (kb + cb < kblocks) ? kb + cb : kblocks;
@@ -199,7 +202,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             t_lo = (int)(r & 15u);
             t_hi = (int)(r >> 4);
         }
-        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, t_lo, t_hi, jobs);
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, t_lo, t_hi,
+                                 jobs);
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) tmem_drain32_magic(taddr + c * 32, &acc[c * 32]);
+            for (int c = 0; c < 4; ++c) tmem_drain32_exact(taddr + c * 32, &acc[c * 32]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t jd = jobs[job];
             if (job_last(jd)) {
                 t_group = job_p(jd) + job_q(jd);
-                const uint32_t bias = nchunks * kMagicBits;
+                const uint32_t bias = nchunks * kChunkBias;
                 // G rows are padded to whole 256-column tiles, so the strip is in
                 // bounds; rows past M are not stored.  Each asm block stores
                 // (acc - bias) and zeroes acc in place.
@@ -391,7 +395,7 @@ int num_sms() {
 // largest count <= min(sms / r, s, 8) whose best cut of groups t = 2..s+1
 // (group t holds t-1 digit pairs) into contiguous ranges keeps the largest
 // piece smallest.  No split when the last wave is full or pieces < 2.
-TailSplit tail_split(int tiles, int s, int sms) {
+TailSplit tail_split(int tiles, int s, int sms, bool trim) {
     TailSplit ts;
     ts.n_full = tiles;
     ts.pieces = 1;
@@ -404,13 +408,19 @@ TailSplit tail_split(int tiles, int s, int sms) {
     if (k > s) k = s;
     if (k > 8) k = 8;
     if (k < 2 || r == sms) return ts;
-    // smallest threshold whose greedy contiguous cut needs <= k pieces
-    const int total = s * (s + 1) / 2;
-    for (int cap = s; cap <= total; ++cap) {
+    // smallest threshold whose greedy contiguous cut needs <= k pieces; group t
+    // holds t-1 pairs (2 when it is the trimmed last group)
+    auto weight = [&](int t) { return (trim && t == s + 1 && s > 2) ? 2 : t - 1; };
+    int total = 0, widest = 0;
+    for (int t = 2; t <= s + 1; ++t) {
+        total += weight(t);
+        widest = weight(t) > widest ? weight(t) : widest;
+    }
+    for (int cap = widest; cap <= total; ++cap) {
         int lo[8], hi[8], n = 0, acc = 0;
         bool fits = true;
         for (int t = 2; t <= s + 1 && fits; ++t) {
-            const int w = t - 1;
+            const int w = weight(t);
             if (n == 0 || acc + w > cap) {
                 if (n == k) fits = false;
                 else {
@@ -439,7 +449,8 @@ TailSplit tail_split(int tiles, int s, int sms) {
 
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
-                           cudaStream_t stream, int group_m, int cluster, int digit_bits) {
+                           cudaStream_t stream, int group_m, int cluster, int digit_bits,
+                           bool trim) {
     if (!emul_digit_bits_ok(digit_bits) || s > emul_max_slices(digit_bits) ||
         K > emul_max_k(digit_bits))
         return ALP_ERR_UNSUPPORTED;
@@ -449,6 +460,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
         for (int t = 2; t <= s + 1; ++t)
             for (int pp = (t - s > 1 ? t - s : 1); pp <= (s < t - 1 ? s : t - 1); ++pp) {
                 const int qq = t - pp;
+                if (!emul_pair_kept(pp, qq, s, trim)) continue;
                 const int64_t cb = chunk_of(pp, qq, digit_bits) / kTK;
                 njobs += (kblocks + cb - 1) / cb;
             }
@@ -466,6 +478,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.K = K;
     p.s = s;
     p.digit_bits = digit_bits;
+    p.trim = trim ? 1 : 0;
     p.G = G;
     p.ldg = ldg;
     p.gplane = M * ldg;
@@ -481,7 +494,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.pieces = 1;
     p.t_ranges = 2u | (uint32_t)(s + 1) << 4;
     if (cl == 1 && emul_tail_split_on()) {
-        const TailSplit ts = tail_split(tiles, s, num_sms());
+        const TailSplit ts = tail_split(tiles, s, num_sms(), trim);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
         p.t_ranges = 0;

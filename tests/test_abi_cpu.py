@@ -137,11 +137,14 @@ def test_batched_classes_and_config(alp):
     assert alp.alp_gemm_batched_workspace(2, np.array([4, -1], dtype=np.int64), hM, hM) == 0
 
 
-def _best_cut(s, k):
+def _best_cut(s, k, trim=False):
     """Smallest largest piece (in digit pairs) over every cut of groups
-    t = 2..s+1 (group t holds t-1 pairs) into at most k contiguous ranges."""
+    t = 2..s+1 (group t holds t-1 pairs; the trimmed last group 2) into at
+    most k contiguous ranges."""
     import itertools
     w = list(range(1, s + 1))
+    if trim:
+        w[-1] = min(w[-1], 2)
     best = sum(w)
     for n in range(1, k + 1):
         for cuts in itertools.combinations(range(1, s), n - 1):
@@ -154,15 +157,19 @@ def test_emul_tail_split(alp):
     """The last partial wave of the slice-product launch is cut into pieces
     that cover the groups once, in order, with the smallest possible largest
     piece (brute force over every cut)."""
-    assert alp.alp_emul_tail_split(2048, 7, 152) == (1976, [(2, 6), (7, 8)])
-    assert alp.alp_emul_tail_split(32, 7, 152) == (0, [(2, 4), (5, 6), (7, 7), (8, 8)])
-    assert alp.alp_emul_tail_split(13 * 152, 7, 152) == (13 * 152, [(2, 8)])   # full last wave
-    assert alp.alp_emul_tail_split(100, 7, 152) == (100, [(2, 8)])   # 152 // 100 = 1 piece
-    assert alp.alp_emul_tail_split(0, 7, 152) == (0, [(2, 8)])
-    for s in range(2, 9):
+    B7, B8T = alp.ALP_SLICE_BF16, alp.ALP_SLICE_BF16_B8_TRIM
+    assert alp.alp_emul_tail_split(2048, 7, B7, 152) == (1976, [(2, 6), (7, 8)])
+    assert alp.alp_emul_tail_split(32, 7, B7, 152) == (0, [(2, 4), (5, 6), (7, 7), (8, 8)])
+    assert alp.alp_emul_tail_split(13 * 152, 7, B7, 152) == (13 * 152, [(2, 8)])   # full wave
+    assert alp.alp_emul_tail_split(100, 7, B7, 152) == (100, [(2, 8)])   # 152 // 100 = 1 piece
+    assert alp.alp_emul_tail_split(0, 7, B7, 152) == (0, [(2, 8)])
+    # trimmed, 7 slices: groups t = 2..8 hold 1, 2, 3, 4, 5, 6 and 2 pairs; the
+    # best cut into 4 pieces has 8 pairs in its largest piece
+    assert alp.alp_emul_tail_split(32, 7, B8T, 152) == (0, [(2, 4), (5, 5), (6, 6), (7, 8)])
+    for s, kind in [(s, B7) for s in range(2, 9)] + [(s, B8T) for s in range(3, 8)]:
         for tiles in (1, 5, 19, 38, 50, 75, 151, 152, 153, 300, 2048):
             for sms in (1, 8, 152, 160):
-                n_full, pieces = alp.alp_emul_tail_split(tiles, s, sms)
+                n_full, pieces = alp.alp_emul_tail_split(tiles, s, kind, sms)
                 r = tiles % sms or sms
                 k = min(sms // r, s, 8)
                 if k < 2 or r == sms:
@@ -173,7 +180,11 @@ def test_emul_tail_split(alp):
                 assert all(a <= b for a, b in pieces)
                 assert all(pieces[i][1] + 1 == pieces[i + 1][0] for i in range(len(pieces) - 1))
                 assert 2 <= len(pieces) <= k
-                largest = max(sum(t - 1 for t in range(a, b + 1)) for a, b in pieces)
-                assert largest == _best_cut(s, k), (s, tiles, sms, pieces)
+                trim = kind == B8T
+                w = lambda t: 2 if trim and t == s + 1 else t - 1
+                largest = max(sum(w(t) for t in range(a, b + 1)) for a, b in pieces)
+                assert largest == _best_cut(s, k, trim), (s, kind, tiles, sms, pieces)
     with pytest.raises(alp.AlpError):
-        alp.alp_emul_tail_split(10, 9, 152)
+        alp.alp_emul_tail_split(10, 9, B7, 152)
+    with pytest.raises(alp.AlpError):
+        alp.alp_emul_tail_split(10, 8, B8T, 152)

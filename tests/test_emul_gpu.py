@@ -13,21 +13,27 @@ from .gpu_util import dev
 pytestmark = pytest.mark.gpu
 
 
-def slice_kind(alp, b):
-    return alp.ALP_SLICE_BF16 if b == 7 else alp.ALP_SLICE_BF16_B8
+# slice kinds: name -> (alp_slice_kind value, digit bits b, trimmed last group)
+KINDS = {"b7": (1, 7, False), "b8": (2, 8, False), "b8t": (3, 8, True)}
 
 
-def run_emul(alp, A, B, C, alpha, beta, s, lda=None, ldc=None, raise_on_error=True, b=7):
+def model(orc, alpha, A, B, beta, C, s, kind="b7", rows=None):
+    _, b, trim = KINDS[kind]
+    return orc.emul_gemm(alpha, A, B, beta, C, s, b=b, trim=trim, rows=rows)
+
+
+def run_emul(alp, A, B, C, alpha, beta, s, lda=None, ldc=None, raise_on_error=True, kind="b7"):
     import torch
     M, K = A.shape
     N = B.shape[1]
     dA, lda = dev(A, lda)
     dB, ldb = dev(B)
     dC, ldc = dev(C if C is not None else np.full((M, N), np.nan), ldc)
-    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, s, slice_kind(alp, b))
+    k = KINDS[kind][0]
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, s, k)
     work = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
-    st = alp.alp_gemm_f64_emul(M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, s,
-                               slice_kind(alp, b), work, ws, raise_on_error=raise_on_error)
+    st = alp.alp_gemm_f64_emul(M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, s, k, work, ws,
+                               raise_on_error=raise_on_error)
     torch.cuda.synchronize()
     err = alp.alp_get_device_error()
     return dC.cpu().numpy()[:M, :N], st, err
@@ -59,8 +65,8 @@ def test_exponents_match_oracle(alp, orc):
 
 
 @pytest.mark.parametrize("phi", [0, 8, 32])
-@pytest.mark.parametrize("s,b", [(8, 7), (7, 8), (3, 8)])
-def test_split_matches_oracle(alp, orc, phi, s, b):
+@pytest.mark.parametrize("s,kind", [(8, "b7"), (7, "b8"), (3, "b8"), (7, "b8t")])
+def test_split_matches_oracle(alp, orc, phi, s, kind):
     import torch
     R, K = 70, 150
     kpad = 192
@@ -69,19 +75,20 @@ def test_split_matches_oracle(alp, orc, phi, s, b):
     X[1] = 0.0
     X[2, :4] = [1.0 - 2.0 ** -53, -(1.0 - 2.0 ** -53), 0.5 + 2.0 ** -10, 1.0 / 512]
     e, _ = orc.row_exponents(X)
+    k, b, _ = KINDS[kind]
     ref, _ = orc.split(X, e, s, b)
     assert np.abs(ref[0]).max() <= 2 ** b and np.abs(ref[1:]).max() <= 2 ** (b - 1)
     dX = torch.from_numpy(X).cuda()
     de = torch.from_numpy(e).cuda()
     out = torch.full((s, R, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
-    alp.alp_emul_split(R, K, dX, K, 0, de, s, b, out, kpad)
+    alp.alp_emul_split(R, K, dX, K, 0, de, s, k, out, kpad)
     got = out.float().cpu().numpy()
     assert np.array_equal(got[:, :, :K], ref.astype(np.float32))
     assert np.all(got[:, :, K:] == 0.0)
     # transposed input: a K x R row-major matrix whose columns are split
     XT = np.ascontiguousarray(X.T)
     out2 = torch.full((s, R, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
-    alp.alp_emul_split(R, K, torch.from_numpy(XT).cuda(), R, 1, de, s, b, out2, kpad)
+    alp.alp_emul_split(R, K, torch.from_numpy(XT).cuda(), R, 1, de, s, k, out2, kpad)
     got2 = out2.float().cpu().numpy()
     assert np.array_equal(got2[:, :, :K], ref.astype(np.float32))
     assert np.all(got2[:, :, K:] == 0.0)
@@ -103,14 +110,16 @@ def test_emul_bit_exact_vs_model(alp, orc, shape, s, phi):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", ["b8", "b8t"])
 @pytest.mark.parametrize("s,phi", [(3, 0), (6, 0), (7, 0), (7, 32), (5, 8)])
-def test_emul_8bit_digits_bit_exact_vs_model(alp, orc, shape, s, phi):
-    """8-bit digits (ALP_SLICE_BF16_B8): the same model with b = 8."""
+def test_emul_8bit_digits_bit_exact_vs_model(alp, orc, shape, kind, s, phi):
+    """8-bit digits (ALP_SLICE_BF16_B8) and the trimmed last group
+    (ALP_SLICE_BF16_B8_TRIM): the same model with b = 8."""
     M, N, K = shape
     A, B, C = inputs.gemm_operands(3700 + M + N + K + s + phi, M, N, K, kind="scaled", phi=phi)
-    got, st, err = run_emul(alp, A, B, C, 1.5, 0.5, s, b=8)
+    got, st, err = run_emul(alp, A, B, C, 1.5, 0.5, s, kind=kind)
     assert st == alp.ALP_OK and err == alp.ALP_OK
-    ref, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s, b=8)
+    ref, rc = model(orc, 1.5, A, B, 0.5, C, s, kind)
     assert rc == 0
     assert np.array_equal(got, ref)
 
@@ -125,63 +134,96 @@ def test_emul_every_config_bit_exact(alp, orc, cluster, group):
     A, B, C = inputs.gemm_operands(3600 + cluster * 100 + group, M, N, K, kind="scaled", phi=8)
     alp.alp_tune_set_cached(M, N, K, alp.ALP_PATH_EMUL, cfg)
     try:
-        got, st, err = run_emul(alp, A, B, C, 1.5, 0.5, 8)
-        got8, st8, err8 = run_emul(alp, A, B, C, 1.5, 0.5, 7, b=8)
+        runs = (("b7", 8), ("b8", 7), ("b8t", 7))
+        got = [run_emul(alp, A, B, C, 1.5, 0.5, s, kind=kind) for kind, s in runs]
     finally:
         alp.alp_tune_clear_cache()
-    assert err == alp.ALP_OK and err8 == alp.ALP_OK
-    ref, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 8)
-    assert np.array_equal(got, ref)
-    ref8, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 7, b=8)
-    assert np.array_equal(got8, ref8)
+    for (kind, s), (res, st, err) in zip(runs, got):
+        assert err == alp.ALP_OK
+        ref, _ = model(orc, 1.5, A, B, 0.5, C, s, kind)
+        assert np.array_equal(res, ref), kind
 
 
-@pytest.mark.parametrize("K", [255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 4097])
+# rows of a 130-row result on both sides of the 128-row tile edge
+EDGE_ROWS = np.array([0, 1, 63, 127, 128, 129])
+
+
+@pytest.mark.parametrize("K", [63, 64, 65, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097,
+                               8193])
 def test_emul_chunk_boundaries(alp, orc, K):
-    """K around the drain chunks (256, 512, 1024) and the 64-wide k-blocks."""
+    """K around the 7-bit drain chunks (1024, 2048, 4096) and the 64-wide
+    k-blocks; the result on rows across the tile edge, every column."""
     M, N = 130, 260
     A, B, _ = inputs.gemm_operands(3200 + K, M, N, K, kind="scaled", phi=4, with_c=False)
     got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 8)
-    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8)
-    assert np.array_equal(got, ref)
+    assert err == alp.ALP_OK
+    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 8, rows=EDGE_ROWS)
+    assert np.array_equal(got[EDGE_ROWS], ref)
 
 
-@pytest.mark.parametrize("K", [63, 64, 65, 127, 128, 129, 255, 256, 257, 1000])
-def test_emul_8bit_chunk_boundaries(alp, orc, K):
-    """8-bit digits drain every 64, 128 or 256 k: K around those chunks."""
+@pytest.mark.parametrize("K", [255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2000])
+@pytest.mark.parametrize("kind", ["b8", "b8t"])
+def test_emul_8bit_chunk_boundaries(alp, orc, K, kind):
+    """8-bit digits drain every 256, 512 or 1024 k: K around those chunks."""
     M, N = 130, 260
     A, B, _ = inputs.gemm_operands(3800 + K, M, N, K, kind="scaled", phi=4, with_c=False)
-    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 7, b=8)
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, 7, kind=kind)
     assert err == alp.ALP_OK
-    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 7, b=8)
-    assert np.array_equal(got, ref)
+    ref, _ = model(orc, 1.0, A, B, 0.0, None, 7, kind, rows=EDGE_ROWS)
+    assert np.array_equal(got[EDGE_ROWS], ref)
 
 
-@pytest.mark.parametrize("b,s", [(7, 8), (8, 7)])
-def test_emul_largest_k(alp, orc, b, s):
+@pytest.mark.parametrize("kind,s", [("b7", 8), ("b8", 7), ("b8t", 7)])
+def test_emul_partial_sums_at_the_chunk_bound(alp, orc, kind, s):
+    """Entries whose first three digits are 2^b, -2^(b-1), 2^(b-1) (a tie at
+    each of the first two steps): every product of pairs among the first three
+    digits is at its bound, and with equal signs along k each chunk's f32
+    partial sum reaches exactly +-2^24, the largest the chunking allows.  Rows
+    of A flip sign and carry a second pattern, so both signs of the bound occur."""
+    _, b, _ = KINDS[kind]
+    x = (2.0 ** b - 0.5 + 2.0 ** (-b - 1)) / 2.0 ** b
+    d, _ = orc.split(np.array([[x]]), np.array([0], dtype=np.int32), 4, b)
+    assert list(d[:, 0, 0]) == [2 ** b, -2 ** (b - 1), 2 ** (b - 1), 0]
+    M, N = 130, 260
+    K = 2 ** (26 - 2 * b)                       # one chunk of the pairs without a first digit
+    A = np.full((M, K), x)
+    A[1::2] *= -1
+    A[2::3, ::2] = 0.5                          # second pattern: digits (2^(b-1), 0, ...)
+    B = np.full((K, N), x)
+    B[:, 1::4] *= -1
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, kind=kind)
+    assert err == alp.ALP_OK
+    rows = np.array([0, 1, 2, 3, 4, 5, 63, 127, 128, 129])
+    ref, _ = model(orc, 1.0, A, B, 0.0, None, s, kind, rows=rows)
+    assert np.array_equal(got[rows], ref)
+
+
+@pytest.mark.parametrize("kind,s", [("b7", 8), ("b8", 7), ("b8t", 7)])
+def test_emul_largest_k(alp, orc, kind, s):
     """K at the int32 group-sum limit (32768 for 7-bit digits, 14336 for
     8-bit); row 0 has its leading digit at the bound 2^b with signs matching
     B's, so its first group sum S^2 is K * 2^(2b), the largest one; one past
     the limit is refused."""
     M, N = 130, 40
+    b = KINDS[kind][1]
     K = 32768 if b == 7 else 14336
     A = np.full((M, K), 1.0 - 2.0 ** -53)
     A[:, 1::2] *= -1
     A[1:] = inputs.scaled(3900 + b, 0, (M - 1, K), 0)
     B = np.full((K, N), 1.0 - 2.0 ** -53)
     B[1::2, :] *= -1
-    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, b=b)
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, kind=kind)
     assert st == alp.ALP_OK and err == alp.ALP_OK
     rows = np.array([0, 1, 77, M - 1])
-    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, s, b=b, rows=rows)
+    ref, _ = model(orc, 1.0, A, B, 0.0, None, s, kind, rows=rows)
     assert np.array_equal(got[rows], ref)
     _, st, _ = run_emul(alp, np.zeros((8, K + 1)), np.zeros((K + 1, 8)), None, 1.0, 0.0, s,
-                        b=b, raise_on_error=False)
+                        kind=kind, raise_on_error=False)
     assert st == alp.ALP_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("b", [7, 8])
-def test_emul_worst_case_digits_exact_b(alp, orc, b):
+@pytest.mark.parametrize("kind", ["b7", "b8", "b8t"])
+def test_emul_worst_case_digits_exact_b(alp, orc, kind):
     """Near-maximal alternating entries for either digit width: every digit at
     or next to its bound, partial sums as large as the chunking allows."""
     M, N, K = 128, 256, 1024
@@ -189,9 +231,9 @@ def test_emul_worst_case_digits_exact_b(alp, orc, b):
     A[:, 1::2] *= -1
     B = np.full((K, N), 1.0 - 2.0 ** -53)
     B[1::2, :] *= -1
-    s = 8 if b == 7 else 7
-    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, b=b)
-    ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, s, b=b)
+    s = 8 if kind == "b7" else 7
+    got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, kind=kind)
+    ref, _ = model(orc, 1.0, A, B, 0.0, None, s, kind)
     assert np.array_equal(got, ref)
 
 
@@ -264,10 +306,15 @@ def test_emul_inf_nan_and_unsupported(alp, orc):
                                  None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_WORKSPACE
     assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_BF16_B8,
                                  None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
-    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 7, 3, None, 0, stream=0,
-                                 raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 7, 4, None, 0, stream=0,
+                                 raise_on_error=False) == alp.ALP_ERR_INVALID_ARG   # no kind 4
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_BF16_B8_TRIM,
+                                 None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 8, alp.ALP_SLICE_BF16_B8) == 0
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, alp.ALP_SLICE_BF16_B8) > 0
+    assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 8, alp.ALP_SLICE_BF16_B8_TRIM) == 0
+    assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, alp.ALP_SLICE_BF16_B8_TRIM) > 0
+    assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, 4) == 0
 
 
 def componentwise_ratio(got, ref, absAB, alpha, beta, C):
@@ -302,8 +349,8 @@ def test_emul_full_size_sampled_rows(alp, orc):
     A, B, _ = inputs.gemm_operands(inputs.workload_seed("emul_8192"), M, N, K, kind="scaled",
                                    phi=8, with_c=False)
     rows = np.array([0, 4097, 8191])
-    for s, b in ((8, 7), (7, 7), (6, 8)):
-        got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, b=b)
+    for s, kind in ((8, "b7"), (7, "b7"), (6, "b8"), (7, "b8t")):
+        got, st, err = run_emul(alp, A, B, None, 1.0, 0.0, s, kind=kind)
         assert err == alp.ALP_OK
-        ref, _ = orc.emul_gemm(1.0, A, B, 0.0, None, s, b=b, rows=rows)
-        assert np.array_equal(got[rows], ref), (s, b)
+        ref, _ = model(orc, 1.0, A, B, 0.0, None, s, kind, rows=rows)
+        assert np.array_equal(got[rows], ref), (s, kind)

@@ -223,27 +223,32 @@ def test_split_reconstructs_exactly(orc, phi, s, b):
             assert recon * Fraction(2) ** int(e[i]) == Fraction(A[i, k])
 
 
-def emul_budget(alpha, beta, C, e, f, K, s, b, out):
+def emul_budget(alpha, beta, C, e, f, K, s, b, out, trim=False):
     """Error of the emulated GEMM against the exact product: cut-off digits and
     dropped pairs (<= 2^(e_i+f_j) K 2^(-s b) (1 + 0.26 s)) plus the roundings
-    of the conversion, the alpha product and the beta fma (<= 3 u |out| + u |beta C|)."""
+    of the conversion, the alpha product and the beta fma (<= 3 u |out| + u |beta C|).
+    The trimmed last group drops s-2 more pairs (p, q >= 2, p + q = s+1), each
+    at most K 2^(2b-2) 2^(-(s+1) b) 2^(e_i+f_j)."""
     scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
     t = scale * K * 2.0 ** (-s * b) * (1 + 0.26 * s) * abs(alpha)
+    if trim:
+        t = t + scale * K * max(s - 2, 0) * 2.0 ** (2 * b - 2 - (s + 1) * b) * abs(alpha)
     return t + 3 * U * np.abs(out) + (U * np.abs(beta * C) if beta != 0 else 0.0) + 1e-300
 
 
-@pytest.mark.parametrize("s,b", [(3, 7), (5, 7), (8, 7), (3, 8), (6, 8), (7, 8)])
+@pytest.mark.parametrize("s,b,trim", [(3, 7, 0), (5, 7, 0), (8, 7, 0), (3, 8, 0), (6, 8, 0),
+                                      (7, 8, 0), (3, 8, 1), (5, 8, 1), (7, 8, 1)])
 @pytest.mark.parametrize("phi", [0, 8])
-def test_emul_gemm_within_derived_bound(orc, s, b, phi):
+def test_emul_gemm_within_derived_bound(orc, s, b, trim, phi):
     M, N, K = 5, 4, 23
     A, B, C = inputs.gemm_operands(70 + s + phi, M, N, K, kind="scaled", phi=phi)
     alpha, beta = 1.5, 0.5
-    D, rc = orc.emul_gemm(alpha, A, B, beta, C, s, b=b)
+    D, rc = orc.emul_gemm(alpha, A, B, beta, C, s, b=b, trim=trim)
     assert rc == 0
     E = exact_gemm(alpha, A, B, beta, C)
     e, _ = orc.row_exponents(A)
     f, _ = orc.col_exponents(B)
-    bud = emul_budget(alpha, beta, C, e, f, K, s, b, D)
+    bud = emul_budget(alpha, beta, C, e, f, K, s, b, D, trim)
     for i in range(M):
         for j in range(N):
             assert abs(Fraction(D[i, j]) - E[i][j]) <= Fraction(bud[i, j]), (i, j, s, phi)
@@ -261,10 +266,11 @@ def fraction_digits(x: float, e: int, s: int, b: int):
     return out
 
 
-def fraction_emul(alpha, A, B, beta, C, s, b):
+def fraction_emul(alpha, A, B, beta, C, s, b, trim=False):
     """The emulated GEMM evaluated independently of the C oracle: digits and
     products in exact rationals, the kept sum rounded by Python's correctly
-    rounded int -> float, scalings with math.ldexp, the fma in rationals."""
+    rounded int -> float, scalings with math.ldexp, the fma in rationals.
+    trim: of the pairs with p + q = s + 1 only (1, s) and (s, 1) are kept."""
     M, K = A.shape
     N = B.shape[1]
     e = [math.frexp(float(np.max(np.abs(A[i]))))[1] if np.any(A[i]) else 0 for i in range(M)]
@@ -278,6 +284,8 @@ def fraction_emul(alpha, A, B, beta, C, s, b):
             X = 0
             for p in range(1, s + 1):
                 for q in range(1, s + 2 - p):
+                    if trim and p + q == s + 1 and min(p, q) > 1:
+                        continue
                     X += sum(dA[i][k][p - 1] * dB[j][k][q - 1] for k in range(K)) \
                         * 2 ** ((s + 1 - p - q) * b)
             w = math.ldexp(float(X), e[i] + f[j] - (s + 1) * b)
@@ -288,14 +296,15 @@ def fraction_emul(alpha, A, B, beta, C, s, b):
     return out
 
 
-@pytest.mark.parametrize("s,b,phi", [(3, 7, 0), (6, 7, 8), (8, 7, 0), (8, 7, 32), (3, 8, 0),
-                                     (6, 8, 8), (7, 8, 32)])
-def test_emul_gemm_bit_exact_against_rationals(orc, s, b, phi):
+@pytest.mark.parametrize("s,b,trim,phi", [(3, 7, 0, 0), (6, 7, 0, 8), (8, 7, 0, 0), (8, 7, 0, 32),
+                                          (3, 8, 0, 0), (6, 8, 0, 8), (7, 8, 0, 32), (4, 8, 1, 0),
+                                          (7, 8, 1, 8), (7, 8, 1, 32)])
+def test_emul_gemm_bit_exact_against_rationals(orc, s, b, trim, phi):
     M, N, K = 4, 3, 9
     A, B, C = inputs.gemm_operands(90 + s + phi, M, N, K, kind="scaled", phi=phi)
-    D, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s, b=b)
+    D, rc = orc.emul_gemm(1.5, A, B, 0.5, C, s, b=b, trim=trim)
     assert rc == 0
-    ref = fraction_emul(1.5, A, B, 0.5, C, s, b)
+    ref = fraction_emul(1.5, A, B, 0.5, C, s, b, trim)
     assert np.array_equal(D, ref)
 
 
@@ -320,6 +329,25 @@ def test_emul_gemm_integer_inputs_bit_exact(orc):
     for s in (3, 8):
         D, rc = orc.emul_gemm(1.0, A, B, 0.0, None, s)
         assert rc == 0 and np.array_equal(D, ref)
+
+
+def test_emul_gemm_trim_special_cases(orc):
+    """The trimmed last group changes nothing when it has no pair without a
+    leading digit (s = 2) or when every entry fits one digit (integers in
+    {-8..8}: all later digits are zero); otherwise it differs."""
+    A, B, C = inputs.gemm_operands(87, 6, 5, 40, kind="scaled", phi=4)
+    for b in (7, 8):
+        full, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 2, b=b)
+        trimmed, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 2, b=b, trim=True)
+        assert np.array_equal(full, trimmed)
+    Ai, Bi, _ = inputs.gemm_operands(81, 12, 10, 64, kind="int", with_c=False)
+    ref = (Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float64)
+    for s in (3, 7):
+        D, rc = orc.emul_gemm(1.0, Ai, Bi, 0.0, None, s, b=8, trim=True)
+        assert rc == 0 and np.array_equal(D, ref)
+    full, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 4, b=8)
+    trimmed, _ = orc.emul_gemm(1.0, A, B, 0.0, None, 4, b=8, trim=True)
+    assert not np.array_equal(full, trimmed)
 
 
 def test_emul_gemm_special_cases(orc):
