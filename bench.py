@@ -4,9 +4,11 @@
 Workload (default): C = alpha*A*B + beta*C with M = N = K = 8192, FP64
 row-major operands u * 2^e (u uniform in [-1,1), e uniform in [-phi, phi],
 phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path with 7
-BF16 digit slices: for these inputs its largest elementwise error relative to
-|A||B| is no worse than the native FP64 kernel's, which the run checks over
-the whole result (the "accuracy" object).
+slices of 8-bit digits held in BF16, the last group trimmed to its two
+leading-digit pairs (ALP_SLICE_BF16_B8_TRIM: 23 slice products): for these
+inputs its largest elementwise error relative to |A||B| and its normwise
+error are both no worse than the native FP64 kernel's, which the run checks
+over the whole result (the "accuracy" object).
 One step = one full emulated GEMM: exponent scans, digit splits, the
 tensor-core slice products and the exact recombination -- the same kernels
 alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
@@ -54,10 +56,11 @@ def parse_args():
     ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--nslices", type=int, default=7,
-                    help="digit slices; 7 is no less accurate than native FP64 for the default "
-                         "uniform inputs (checked live against 8 slices), 8 for wide exponent "
-                         "ranges")
-    ap.add_argument("--kind", choices=tuple(KINDS), default="bf16",
+                    help="digit slices; with the default kind 7 is no less accurate than "
+                         "native FP64 for the default uniform inputs (checked live against 8 "
+                         "slices of 7-bit digits); wide exponent ranges need --kind bf16 with 8 "
+                         "or --kind bf16_b8 with 7")
+    ap.add_argument("--kind", choices=tuple(KINDS), default="bf16_b8_trim",
                     help="digit scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
                          "up to 7), bf16_b8_trim (8-bit, last group keeps only its two "
                          "leading-digit pairs)")
@@ -122,9 +125,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(workload):
     """DRAM bytes per launch of the tensor-core kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    summary, if it was taken on the current kernel source and this workload;
+    else None."""
     path = os.path.join(ROOT, TRAFFIC_PROFILE)
     try:
         text = open(path).read()
@@ -135,7 +139,7 @@ def profiled_traffic():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_hash") != kernel_source_hash():
+    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("workload") != workload:
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
@@ -202,13 +206,13 @@ def cpu_oracle_sample(A_rows, B, alpha, target_s):
     n_threads = os.cpu_count() or 1
     K = B.shape[0]
     N = B.shape[1]
-    probe = min(len(A_rows), max(2, n_threads // 4))
+    # one row per thread as the probe, then whole rounds of rows up to the target
+    probe = min(len(A_rows), n_threads)
     t0 = time.perf_counter()
     oracle.gemm(alpha, A_rows[:probe], B, 0.0, nthreads=n_threads)
     dt = time.perf_counter() - t0
-    rows = int(max(1, min(len(A_rows), probe * target_s / max(dt, 1e-3))))
-    rows = max(n_threads, rows // n_threads * n_threads) if rows >= n_threads else rows
-    rows = min(rows, len(A_rows))
+    rounds = max(1, int(target_s / max(dt, 1e-3)))
+    rows = min(len(A_rows), probe * rounds)
     t0 = time.perf_counter()
     oracle.gemm(alpha, A_rows[:rows], B, 0.0, nthreads=n_threads)
     dt = time.perf_counter() - t0
@@ -325,7 +329,7 @@ def run_alp(args):
                 "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
                 "algorithmic_flops_per_launch": pairs * 2.0 * M * N * K,
                 "kernel_ms": round(kern_avg, 3),
-                "traffic": profiled_traffic()}
+                "traffic": profiled_traffic(workload_name(n, s, args.kind, phi))}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": max(3, args.warmup),
@@ -466,7 +470,7 @@ def run_alp(args):
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         # CPU baseline: the long-double oracle on a bounded sample of rows
-        rows = 64
+        rows = 512
         A_rows = A[:rows].cpu().numpy()
         Bh = B.cpu().numpy()
         tf, r, dt, thr = cpu_oracle_sample(A_rows, Bh, alpha, args.cpu_seconds)
