@@ -143,12 +143,13 @@ __device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
     uint64_t X = fixed_point_r0(a, e);
 #pragma unroll
     for (int p = 0; p < S; ++p) {
-        const int64_t q = ((int64_t)X) >> SH;
-        const uint64_t rem = X & ((1ull << SH) - 1);
-        const uint64_t half = 1ull << (SH - 1);
-        const int64_t dd = q + ((rem > half) || (rem == half && (q & 1)) ? 1 : 0);
+        // round half to even of X / 2^SH: floor((X + 2^(SH-1) - 1 + odd) / 2^SH),
+        // odd = the parity of floor(X / 2^SH)
+        const uint64_t odd = (X >> SH) & 1;
+        const int64_t dd = (int64_t)(X + ((1ull << (SH - 1)) - 1) + odd) >> SH;
         d[p] = (int)dd;
-        X = (X - ((uint64_t)dd << SH)) << B;
+        // (X - dd 2^SH) 2^B, |.| <= 2^61; SH + B = 62
+        X = (X << B) - ((uint64_t)dd << 62);
     }
 }
 
@@ -181,6 +182,48 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
         uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
 #pragma unroll
         for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+    }
+}
+
+// As split_rows_kernel with four consecutive k per thread: rows from
+// blockIdx.y (grid stride, no division per element), two 16-byte loads of A
+// when its row is 16-byte aligned, one 8-byte store per digit plane.  Needs
+// out 8-byte aligned (the launch checks).
+template <int S, int B>
+__global__ void __launch_bounds__(256) split_rows4_kernel(const double* __restrict__ X, int64_t R,
+                                                          int64_t K, int64_t ldx,
+                                                          const int32_t* __restrict__ e,
+                                                          __nv_bfloat16* __restrict__ out,
+                                                          int64_t kpad) {
+    const int64_t plane = R * kpad;
+    for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
+        const int er = e[r];
+        const double* xr = X + r * ldx;
+        const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
+        for (int64_t k = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); k < kpad;
+             k += 4 * (int64_t)gridDim.x * blockDim.x) {
+            double a[4];
+            if (xvec && k + 3 < K) {
+                const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
+                const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
+                a[0] = p0.x;
+                a[1] = p0.y;
+                a[2] = p1.x;
+                a[3] = p1.y;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? __ldg(xr + k + u) : 0.0;
+            }
+            int d0[S], d1[S], d2[S], d3[S];
+            split_digits<S, B>(a[0], er, d0);
+            split_digits<S, B>(a[1], er, d1);
+            split_digits<S, B>(a[2], er, d2);
+            split_digits<S, B>(a[3], er, d3);
+            uint2* o = reinterpret_cast<uint2*>(out + r * kpad + k);
+#pragma unroll
+            for (int p = 0; p < S; ++p)
+                o[(p * plane) >> 2] = make_uint2(pack_bf16x2(d0[p], d1[p]), pack_bf16x2(d2[p], d3[p]));
+        }
     }
 }
 
@@ -219,57 +262,91 @@ __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64
 // ---------------------------------------------------------------------------
 // 4. recombination + alpha/beta epilogue
 // ---------------------------------------------------------------------------
-// Nearest double (ties to even) of a 128-bit two's-complement integer,
-// multiplied by 2^E: built from integer operations on the IEEE encoding
-// (FP64 arithmetic is slow on this GPU).  When the scaled result would leave
-// the normal range it falls back to ldexp, which rounds a subnormal result once.
-__device__ __forceinline__ double int128_scaled_to_double_rn(unsigned __int128 x, int E) {
-    const bool neg = (x >> 127) != 0;
-    const unsigned __int128 u = neg ? (unsigned __int128)0 - x : x;
-    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+// Nearest double (ties to even) of the 128-bit two's-complement integer
+// hi:lo, multiplied by 2^E: built from 64-bit integer operations on the IEEE
+// encoding (FP64 arithmetic is slow on this GPU).  When the scaled result
+// would leave the normal range it falls back to ldexp of the rounded value
+// (which rounds a subnormal result a second time, as the definition does).
+__device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_t lo, int E) {
+    const bool neg = hi_s < 0;
+    uint64_t hi = (uint64_t)hi_s;
+    if (neg) {   // magnitude: two's complement negation
+        lo = ~lo + 1;
+        hi = ~hi + (lo == 0 ? 1 : 0);
+    }
     if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
-    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    uint64_t m;
-    int ex = msb;
-    if (msb <= 52) {
-        m = lo << (52 - msb);   // exact
+    // top: the 64 bits below and including the leading one; sticky: any bit below
+    uint64_t top;
+    bool sticky;
+    int msb;
+    if (hi) {
+        const int n = __clzll((long long)hi);
+        top = n ? (hi << n) | (lo >> (64 - n)) : hi;
+        sticky = (n ? lo << n : lo) != 0;
+        msb = 127 - n;
     } else {
-        const int shift = msb - 52;
-        m = (uint64_t)(u >> shift);
-        const unsigned __int128 rem = u & (((unsigned __int128)1 << shift) - 1);
-        const unsigned __int128 halfw = (unsigned __int128)1 << (shift - 1);
-        if (rem > halfw || (rem == halfw && (m & 1))) ++m;
+        const int n = __clzll((long long)lo);
+        top = lo << n;
+        sticky = false;
+        msb = 63 - n;
+    }
+    uint64_t m = top >> 11;                      // 53 bits, leading one at bit 52
+    const uint64_t low = top & 0x7FF;            // 11 bits below them
+    if (low > 0x400 || (low == 0x400 && (sticky || (m & 1)))) {
+        ++m;
         if (m >> 53) {
             m >>= 1;
-            ++ex;
+            ++msb;
         }
     }
-    // m in [2^52, 2^53): value = m * 2^(ex - 52) * 2^E
-    const int be = ex + E + 1023;
+    // m in [2^52, 2^53): value = m * 2^(msb - 52) * 2^E
+    const int be = msb + E + 1023;
     if (be >= 1 && be <= 2046) {
-        const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
+        const uint64_t bits =
+            ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
         return __longlong_as_double((long long)bits);
     }
-    // outside the normal range: the unscaled value is exact in double, scale once
     const double v = __longlong_as_double(
-        (long long)(((uint64_t)neg << 63) | ((uint64_t)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
+        (long long)(((uint64_t)neg << 63) | ((uint64_t)(msb + 1023) << 52) | (m & ((1ull << 52) - 1))));
     return ldexp(v, E);
+}
+
+// X = sum_t v[t] 2^(B (S-1-t)) exactly (Horner, X = X * 2^B + v[t]), then the
+// nearest double times 2^E.  The first terms run in 64 bits (after t + 1 terms
+// |X| < 2^(32 + B t)); the rest carry a 128-bit hi:lo pair.
+template <int S, int B>
+__device__ __forceinline__ double recombine_vals(const int32_t (&v)[S], int E) {
+    constexpr int T64 = (62 - 32) / B + 1;   // terms that fit in 64 bits
+    int64_t x = v[0];
+#pragma unroll
+    for (int t = 1; t < (S < T64 ? S : T64); ++t) x = x * (1ll << B) + v[t];
+    int64_t hi = x >> 63;
+    uint64_t lo = (uint64_t)x;
+#pragma unroll
+    for (int t = T64; t < S; ++t) {
+        const uint64_t l2 = lo << B;
+        const uint64_t h2 = ((uint64_t)hi << B) | (lo >> (64 - B));
+        const int64_t vt = v[t];
+        uint64_t rlo, rhi;
+        asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+            : "=l"(rlo), "=l"(rhi)
+            : "l"(l2), "l"(h2), "l"((uint64_t)vt), "l"((uint64_t)(vt >> 63)));
+        lo = rlo;
+        hi = (int64_t)rhi;
+    }
+    return i128_scaled_to_double_rn(hi, lo, E);
 }
 
 // One block row of threads per matrix row chunk: rows from blockIdx.y (grid
 // stride), two columns per thread from the x dimension (no integer division
-// per element).  The slice count is a template parameter so that the S loads
-// are independent and the sum is a Horner chain, X = X * 2^7 + S^t.
+// per element).
 template <int S, int B>
 __device__ __forceinline__ double recombine_one(const int32_t* __restrict__ g, int64_t gplane,
                                                 int E) {
     int32_t v[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) v[t] = __ldg(g + (int64_t)t * gplane);
-    unsigned __int128 X = (unsigned __int128)(__int128)v[0];
-#pragma unroll
-    for (int t = 1; t < S; ++t) X = (X << B) + (unsigned __int128)(__int128)v[t];
-    return int128_scaled_to_double_rn(X, E);
+    return recombine_vals<S, B>(v, E);
 }
 
 template <int S, int B>
@@ -297,13 +374,68 @@ __global__ void recombine_kernel(const int32_t* __restrict__ G, int64_t gplane, 
     }
 }
 
+// Four columns per thread: the S group sums of four adjacent columns arrive
+// as one 16-byte load per plane (G rows are 256-column padded, so the vector
+// never leaves the row), and C is written as two 16-byte stores when the row
+// of C is 16-byte aligned.  Needs G 16-byte aligned (the launch checks).
+template <int S, int B>
+__global__ void __launch_bounds__(256) recombine4_kernel(
+    const int32_t* __restrict__ G, int64_t gplane, int64_t ldg, const int32_t* __restrict__ e,
+    const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
+    double* __restrict__ C, int64_t ldc) {
+    const int shift0 = (S + 1) * B;
+    for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
+        const int ei = e[i] - shift0;
+        const int32_t* gi = G + i * ldg;
+        double* ci = C + i * ldc;
+        const bool cvec = (reinterpret_cast<uintptr_t>(ci) & 15) == 0;
+        for (int64_t j = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N;
+             j += 4 * (int64_t)gridDim.x * blockDim.x) {
+            int4 v[S];
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                v[t] = __ldg(reinterpret_cast<const int4*>(gi + (int64_t)t * gplane + j));
+            double out[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j + u >= N) break;
+                int32_t c[S];
+#pragma unroll
+                for (int t = 0; t < S; ++t)
+                    c[t] = u == 0 ? v[t].x : u == 1 ? v[t].y : u == 2 ? v[t].z : v[t].w;
+                const double w = recombine_vals<S, B>(c, ei + __ldg(f + j + u));
+                double o = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
+                if (beta != 0.0) o = __fma_rn(beta, ci[j + u], o);
+                out[u] = o;
+            }
+            if (cvec && j + 3 < N) {
+                reinterpret_cast<double2*>(ci + j)[0] = make_double2(out[0], out[1]);
+                reinterpret_cast<double2*>(ci + j)[1] = make_double2(out[2], out[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j + u < N) ci[j + u] = out[u];
+            }
+        }
+    }
+}
+
 template <int B>
 static alp_status launch_recombine_b(int s, dim3 grid, cudaStream_t st, const int32_t* G,
                                      int64_t gplane, int64_t ldg, const int32_t* e,
                                      const int32_t* f, int64_t M, int64_t N, double alpha,
                                      double beta, double* C, int64_t ldc) {
-#define ALP_RECOMBINE_CASE(x) \
-    case x: recombine_kernel<x, B><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc); break;
+    const bool vec = (reinterpret_cast<uintptr_t>(G) & 15) == 0 && gplane % 4 == 0 && ldg % 4 == 0;
+    if (vec) grid.x = (unsigned)((grid.x + 1) / 2);   // four columns per thread instead of two
+#define ALP_RECOMBINE_CASE(x)                                                                     \
+    case x:                                                                                      \
+        if (vec)                                                                                 \
+            recombine4_kernel<x, B><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, \
+                                                          C, ldc);                               \
+        else                                                                                     \
+            recombine_kernel<x, B><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta,  \
+                                                         C, ldc);                                \
+        break;
     switch (s) {
         ALP_RECOMBINE_CASE(1) ALP_RECOMBINE_CASE(2) ALP_RECOMBINE_CASE(3) ALP_RECOMBINE_CASE(4)
         ALP_RECOMBINE_CASE(5) ALP_RECOMBINE_CASE(6) ALP_RECOMBINE_CASE(7) ALP_RECOMBINE_CASE(8)
@@ -382,9 +514,16 @@ template <int B>
 static alp_status emul_split_b(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
                                const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
                                cudaStream_t st) {
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
+    const int64_t bx = (kpad + 1023) / 1024;
+    int64_t by = (int64_t)device_sm_count() * 8 / bx;
+    by = by < 1 ? 1 : by > R ? R : by > 65535 ? 65535 : by;
+    const dim3 grid4((unsigned)bx, (unsigned)by);
 #define ALP_SPLIT_CASE(x)                                                                        \
     case x:                                                                                      \
-        if (!trans)                                                                              \
+        if (!trans && vec)                                                                       \
+            split_rows4_kernel<x, B><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps, out, kpad);      \
+        else if (!trans)                                                                         \
             split_rows_kernel<x, B><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(              \
                 X, R, K, ldx, exps, out, kpad);                                                  \
         else                                                                                     \

@@ -354,3 +354,62 @@ def test_emul_full_size_sampled_rows(alp, orc):
         assert err == alp.ALP_OK
         ref, _ = model(orc, 1.0, A, B, 0.0, None, s, kind, rows=rows)
         assert np.array_equal(got[rows], ref), (s, kind)
+
+
+@pytest.mark.parametrize("kind,s", [("b7", 8), ("b7", 3), ("b8", 7), ("b8", 5)])
+def test_recombine_rounding(alp, kind, s):
+    """alp_emul_recombine on crafted group sums: X = sum_t S^t 2^(b(s+1-t))
+    whose tails are exact ties, just below or above a tie, sticky bits far
+    below, negative, zero, and scalings into the subnormal and overflow
+    ranges; each result must be Python's correctly rounded float(X) scaled by
+    ldexp (one more rounding when subnormal), i.e. the definition."""
+    import math
+    import random
+
+    import torch
+    k, b, _ = KINDS[kind]
+    rnd = random.Random(17 + s + b)
+    vals = []
+    for _ in range(600):
+        nbits = rnd.randrange(1, 31 + b * (s - 1))
+        X = rnd.getrandbits(nbits) | (1 << (nbits - 1))
+        form = rnd.randrange(5)
+        if nbits > 54 and form < 4:
+            # r: the bit just below the 53 kept; forms: exact tie, just below, just
+            # above, and a lone sticky bit somewhere below
+            r = nbits - 54 if form < 3 else rnd.randrange(0, nbits - 54)
+            X = (X >> (r + 1)) << (r + 1)
+            X += [1 << r, (1 << r) - 1, (1 << r) + 1, 1 << r][form]
+        vals.append(-X if rnd.random() < 0.5 else X)
+    vals += [v for v in (0, 1, -1, 2 ** 53 + 1, 2 ** 54 + 2, -(2 ** 54 + 6))
+             if abs(v) < 2 ** (30 + b * (s - 1))]
+    N = len(vals)
+    ldg = (N + 255) // 256 * 256
+    rows = 3
+    G = np.zeros((s, rows, ldg), dtype=np.int32)
+    for j, X in enumerate(vals):
+        # base-2^b digits, the top one signed and unbounded within int32
+        digits = []
+        rest = X
+        for _ in range(s - 1):
+            digits.append(rest & ((1 << b) - 1))
+            rest >>= b
+        assert -2 ** 31 <= rest < 2 ** 31
+        col = [rest] + digits[::-1]
+        for row in range(rows):
+            G[:, row, j] = col
+    e = np.array([0, -1000, 200], dtype=np.int32)       # rows 1, 2: subnormal, overflow
+    f = np.array([rnd.choice([0, 5, -3, 900, -60]) for _ in range(N)], dtype=np.int32)
+    dG, de, df = (torch.from_numpy(x).cuda() for x in (G, e, f))
+    dC = torch.full((rows, N), np.nan, dtype=torch.float64, device="cuda")
+    alp.alp_emul_recombine(rows, N, s, k, dG, ldg, de, df, 1.0, 0.0, dC, N)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()
+    for row in range(rows):
+        for j, X in enumerate(vals):
+            E = int(e[row]) + int(f[j]) - (s + 1) * b
+            try:
+                want = math.ldexp(float(X), E)
+            except OverflowError:
+                want = math.copysign(math.inf, X)
+            assert got[row, j] == want or (want == 0 and got[row, j] == 0), (row, j, X, E)
