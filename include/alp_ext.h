@@ -21,9 +21,11 @@ extern "C" {
  * (bm/(8 tm)) * (bn/(4 tn)) compute warps within the per-(tm,tn) thread cap
  * that keeps the register tile resident; at least 2 stages of
  * (bm+bn)*bk*8 bytes within 227 KiB of shared memory.  Emulated path:
- * {128, 256, 64, cluster, 0, group} with cluster in {1, 2} (blocks sharing each
- * B tile through multicast) and group in {1, 2, 4, 8, 16, 32} (tile-rows per
- * raster group). */
+ * {128, 256, 64, cluster, 0, group} with cluster in {1, 2} (one block per
+ * 128 x 256 tile, or two blocks sharing each B tile through multicast), or
+ * {256, 256, 64, 2, 0, group} (CTA pairs whose tcgen05 MMAs span both SMs on
+ * a 256 x 256 tile; the default), and group in {1, 2, 4, 8, 16, 32}
+ * (tile-rows per raster group). */
 int alp_config_valid(const alp_config* cfg, alp_path path);
 
 /* Shared-memory bytes of the A and B tiles of all stages: stages*(bm+bn)*bk*8

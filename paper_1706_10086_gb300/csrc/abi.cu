@@ -147,7 +147,7 @@ static bool default_native_config(alp_config* out) {
 
 bool default_config(alp_path path, alp_config* out) {
     if (path == ALP_PATH_EMUL) {
-        *out = alp_config{128, 256, 64, 1, 0, 8};   // no B sharing, raster group of 8 tile-rows
+        *out = alp_config{256, 256, 64, 2, 0, 16};   // CTA pairs, raster group of 16 tile-rows
         return true;
     }
     return default_native_config(out);

@@ -663,7 +663,8 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
     alp_config cfg;
     const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
     if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
-                              have ? cfg.stages : 0, have ? cfg.tm : 0, b, sc.trim)) != ALP_OK)
+                              have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
+                              sc.trim)) != ALP_OK)
         return st;
     return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
                             alpha, beta, C, ldc);

@@ -34,32 +34,33 @@ namespace alp {
 alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1,
                              uint64_t d2, uint32_t box0, uint32_t box1);
 
-// Blocks per cluster sharing B tiles when the config does not say (env
-// ALP_EMUL_CLUSTER: 1 or 2; default 1: sharing B measured no faster at 8192^3).
+// Block arrangement when the config does not say (env ALP_EMUL_CLUSTER: 1 =
+// one block per tile, 2 = two blocks sharing B tiles, 3 = CTA pairs sharing
+// each MMA; default 3, the fastest at 8192^3 on GB300).
 static int emul_cluster() {
     static int c = 0;
     if (c == 0) {
-        c = 1;
+        c = kEmulPair;
         if (const char* s = std::getenv("ALP_EMUL_CLUSTER")) {
             const int v = std::atoi(s);
-            if (v == 1 || v == 2) c = v;
+            if (v == kEmulSingle || v == kEmulShareB || v == kEmulPair) c = v;
         }
     }
     return c;
 }
 
-// Tile-rows per raster group (env ALP_EMUL_GROUP_M overrides; default 8, the
-// fastest of {1, 4, 8, 16, 32, 64} at 8192^3 on GB300).
-static int emul_group_m() {
-    static int g = 0;
-    if (g == 0) {
-        g = 8;
+// Tile-rows per raster group (env ALP_EMUL_GROUP_M overrides; default the
+// fastest at 8192^3 on GB300: 16 for CTA pairs, 8 otherwise).
+static int emul_group_m(bool pair) {
+    static int g = -1;
+    if (g < 0) {
+        g = 0;
         if (const char* s = std::getenv("ALP_EMUL_GROUP_M")) {
             const int v = std::atoi(s);
             if (v >= 1 && v <= 4096) g = v;
         }
     }
-    return g;
+    return g > 0 ? g : pair ? 16 : 8;
 }
 
 // Whether the last partial wave is split (env ALP_EMUL_TAIL_SPLIT=0 turns it
@@ -158,6 +159,59 @@ __device__ __forceinline__ void store4_sub_and_zero(int32_t* g, uint32_t bias, u
         : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
         : "l"(g), "r"(bias), "r"(do_store)
         : "memory");
+}
+
+// Epilogue warps (2..9): for each finished chunk, drain this warp's 32 TMEM
+// lanes x 128 columns of accumulator b into exact int32 sums, hand the
+// accumulator back (an arrive on acce[b] of this block, or, when acce_remote
+// is nonzero, on the mbarrier at that shared::cluster address), and at the
+// end of a group store S^t to G[t-2].
+__device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const uint32_t* jobs,
+                                              int njobs, uint32_t tmem_base, uint64_t* accf,
+                                              uint64_t* acce, uint32_t acce_remote, int m0,
+                                              int n0, int warp, int lane, uint64_t tmo,
+                                              volatile int* abort_flag) {
+    const int quarter = warp & 3;          // TMEM lanes this warp may access
+    const int half = (warp - 2) >> 2;      // columns [128*half, 128*half + 128)
+    const int row = quarter * 32 + lane;
+    const int gm = m0 + row;
+    uint32_t acc[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) acc[i] = 0;
+    uint32_t nchunks = 0;
+    int t_group = 2;
+    for (int job = 0; job < njobs; ++job) {
+        const uint32_t b = job & 1;
+        if (!mbar_wait_bounded(&accf[b], (job >> 1) & 1, tmo, abort_flag, prm.err)) break;
+        tc_fence_after();
+        const uint32_t taddr =
+            tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_drain32_exact(taddr + c * 32, &acc[c * 32]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            if (acce_remote) mbar_arrive_cluster(acce_remote + b * 8);
+            else mbar_arrive(&acce[b]);
+        }
+        ++nchunks;
+        const uint32_t jd = jobs[job];
+        if (job_last(jd)) {
+            t_group = job_p(jd) + job_q(jd);
+            const uint32_t bias = nchunks * kChunkBias;
+            // G rows are padded to whole 256-column tiles, so the strip is in
+            // bounds; rows past M are not stored.  Each asm block stores
+            // (acc - bias) and zeroes acc in place.
+            int32_t* g = prm.G + (int64_t)(t_group - 2) * prm.gplane + (int64_t)gm * prm.ldg +
+                         n0 + half * 128;
+            const uint32_t do_store = gm < prm.M ? 1u : 0u;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                store4_sub_and_zero(g + 4 * i, bias, do_store, acc[4 * i], acc[4 * i + 1],
+                                    acc[4 * i + 2], acc[4 * i + 3]);
+            nchunks = 0;
+        }
+    }
 }
 
 // CL = 1: one block per tile.  CL = 2: clusters of two blocks on vertically
@@ -325,45 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
         }
     } else {
-        // ---------------- epilogue: TMEM -> exact int32 group sums ----------------
-        const int quarter = warp & 3;          // TMEM lanes this warp may access
-        const int half = (warp - 2) >> 2;      // columns [128*half, 128*half + 128)
-        const int row = quarter * 32 + lane;
-        const int gm = m0 + row;
-        uint32_t acc[128];
-#pragma unroll
-        for (int i = 0; i < 128; ++i) acc[i] = 0;
-        uint32_t nchunks = 0;
-        int t_group = 2;
-        for (int job = 0; job < njobs; ++job) {
-            const uint32_t b = job & 1;
-            if (!mbar_wait_bounded(&accf[b], (job >> 1) & 1, tmo, abort_flag, prm.err)) break;
-            tc_fence_after();
-            const uint32_t taddr =
-                tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) tmem_drain32_exact(taddr + c * 32, &acc[c * 32]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[b]);
-            ++nchunks;
-            const uint32_t jd = jobs[job];
-            if (job_last(jd)) {
-                t_group = job_p(jd) + job_q(jd);
-                const uint32_t bias = nchunks * kChunkBias;
-                // G rows are padded to whole 256-column tiles, so the strip is in
-                // bounds; rows past M are not stored.  Each asm block stores
-                // (acc - bias) and zeroes acc in place.
-                int32_t* g = prm.G + (int64_t)(t_group - 2) * prm.gplane + (int64_t)gm * prm.ldg +
-                             n0 + half * 128;
-                const uint32_t do_store = gm < prm.M ? 1u : 0u;
-#pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    store4_sub_and_zero(g + 4 * i, bias, do_store, acc[4 * i], acc[4 * i + 1],
-                                        acc[4 * i + 2], acc[4 * i + 3]);
-                nchunks = 0;
-            }
-        }
+        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0], 0u, m0, n0, warp, lane, tmo,
+                      abort_flag);
     }
     tc_fence_before();
     __syncwarp();
@@ -373,6 +390,179 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// CTA-pair variant (tcgen05 .cta_group::2): a cluster of two blocks computes
+// a 256 x 256 tile with M = 256, N = 256 MMAs issued by one thread of block 0.
+// Block r holds rows [m0 + 128 r, +128) of A and rows [n0 + 128 r, +128) of
+// the K-major B per stage (16 + 16 KB, 6 stages), and its TMEM receives rows
+// m0 + 128 r.. of the tile, so each SM stages half the B bytes of the
+// one-block kernel per MMA.  Both blocks' copies complete on block 0's "full"
+// barriers (its producer expects the bytes of both); the MMA thread releases
+// stages and chunks in both blocks by multicast commits; block 1's epilogue
+// hands accumulators back on block 0's "acce" barriers.
+constexpr int kPairStages = 6;
+constexpr uint32_t kPairBTile = kBTile / 2;
+constexpr uint32_t kPairStageBytes = kATile + kPairBTile;
+constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + 1024 /*align*/ + 256 /*barriers*/ +
+                               4 * kMaxJobs;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    emul_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                          const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
+    unsigned char* tiles = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPairStages * kPairStageBytes);
+    uint64_t* empty = full + kPairStages;
+    uint64_t* accf = empty + kPairStages;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* njobs_slot = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag + 1));
+    uint32_t* jobs = reinterpret_cast<uint32_t*>(smem + kPairStages * kPairStageBytes + 256);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPairStages; ++i) {
+            mbar_init(&full[i], 1);    // block 0's producer; bytes of both blocks
+            mbar_init(&empty[i], 1);   // one multicast commit per round
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 2 * kEpiWarps);   // epilogue warps of both blocks
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        // the tail split counts clusters: both blocks of a pair take the same piece
+        int t_lo = 2, t_hi = prm.s + 1;
+        const int cid = (int)blockIdx.x / 2;
+        if (cid >= prm.n_full) {
+            const int pc = (cid - prm.n_full) % prm.pieces;
+            const uint32_t r = (uint32_t)(prm.t_ranges >> (8 * pc)) & 0xffu;
+            t_lo = (int)(r & 15u);
+            t_hi = (int)(r >> 4);
+        }
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, t_lo, t_hi,
+                                 jobs);
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();   // both blocks' barriers and TMEM exist before any signal
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int njobs = *njobs_slot;
+
+    // grouped raster in units of 256-row tile pairs (as the B-sharing clusters)
+    int m0, n0;
+    {
+        const int tiles_mc = (prm.tiles_m + 1) / 2;
+        const int gm = prm.group_m / 2 > 0 ? prm.group_m / 2 : 1;
+        const int cid = (int)blockIdx.x / 2;
+        const int pid = cid < prm.n_full ? cid : prm.n_full + (cid - prm.n_full) / prm.pieces;
+        const int in_group = gm * prm.tiles_n;
+        const int first_m = (pid / in_group) * gm;
+        const int gsz = min(tiles_mc - first_m, gm);
+        const int local = pid % in_group;
+        m0 = ((first_m + local % gsz) * 2 + (int)rank) * kTM;
+        n0 = (local / gsz) * kTN;
+    }
+    const uint64_t tmo = prm.timeout_ns;
+    const uint32_t full0 = cluster_addr(full, 0);   // block 0's full barriers
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both blocks) ----------------
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int j = 0; j < njobs && ok; ++j) {
+                const uint32_t jd = jobs[j];
+                for (int kb = job_kb(jd); kb < job_ke(jd); ++kb, ++it) {
+                    const uint32_t st = it % kPairStages, round = it / kPairStages;
+                    if (it >= (uint32_t)kPairStages &&
+                        !mbar_wait_bounded(&empty[st], (round - 1) & 1, tmo, abort_flag, prm.err)) {
+                        ok = false;
+                        break;
+                    }
+                    if (leader) mbar_arrive_expect_tx(&full[st], 2 * kPairStageBytes);
+                    unsigned char* a = tiles + st * kPairStageBytes;
+                    tma_load_3d_pair(a, &tmA, full0 + st * 8, kb * kTK, m0, job_p(jd) - 1);
+                    tma_load_3d_pair(a + kATile, &tmB, full0 + st * 8, kb * kTK,
+                                     n0 + (int)rank * (kTN / 2), job_q(jd) - 1);
+                }
+            }
+            // the MMAs of every issued stage must have consumed it (so this
+            // block's copies have landed) and its release reached this block
+            for (uint32_t j = it > (uint32_t)kPairStages ? it - kPairStages : 0; j < it; ++j)
+                mbar_wait_bounded(&empty[j % kPairStages], (j / kPairStages) & 1, tmo, nullptr,
+                                  prm.err, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (block 0) ----------------
+            const uint32_t idesc = idesc_bf16_f32(2 * kTM, kTN);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int job = 0; job < njobs && ok; ++job) {
+                const uint32_t jd = jobs[job];
+                const uint32_t b = job & 1;
+                if (job >= 2 &&
+                    !mbar_wait_bounded(&acce[b], ((job >> 1) - 1) & 1, tmo, abort_flag, prm.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + b * kTN;
+                uint32_t accumulate = 0;
+                for (int kb = job_kb(jd); kb < job_ke(jd); ++kb, ++it) {
+                    const uint32_t st = it % kPairStages, round = it / kPairStages;
+                    if (!mbar_wait_bounded(&full[st], round & 1, tmo, abort_flag, prm.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(tiles + st * kPairStageBytes);
+                    const uint64_t adesc = sw128_kmajor_desc(a_addr);
+                    const uint64_t bdesc = sw128_kmajor_desc(a_addr + kATile);
+#pragma unroll
+                    for (int kk = 0; kk < kTK / 16; ++kk) {
+                        umma_bf16_pair(d_tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, accumulate);
+                        accumulate = 1;
+                    }
+                    umma_commit_pair(&empty[st], 3);
+                }
+                if (!ok) break;
+                umma_commit_pair(&accf[b], 3);
+            }
+            // all MMAs must have completed before TMEM and shared memory go away,
+            // and both blocks' hand-backs of the last two chunks must have arrived
+            umma_commit_pair(done, 1);
+            mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
+            for (int job = njobs > 2 ? njobs - 2 : 0; job < njobs; ++job)
+                mbar_wait_bounded(&acce[job & 1], (job >> 1) & 1, tmo, nullptr, prm.err, false);
+        }
+    } else {
+        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0],
+                      leader ? 0u : cluster_addr(acce, 0), m0, n0, warp, lane, tmo, abort_flag);
+    }
+    tc_fence_before();
+    __syncwarp();
+    cluster_sync_all();   // no block leaves while its peer's MMAs or signals may reach it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, kTmemCols);
     }
 }
 
@@ -466,7 +656,10 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
             }
         if (njobs > kMaxJobs || kblocks > 1023) return ALP_ERR_UNSUPPORTED;
     }
-    const int cl = (cluster == 1 || cluster == 2) ? cluster : emul_cluster();
+    const int arr = (cluster == kEmulSingle || cluster == kEmulShareB || cluster == kEmulPair)
+                        ? cluster
+                        : emul_cluster();
+    const int cl = arr == kEmulSingle ? 1 : 2;   // blocks per cluster
     CUtensorMap ta, tb;
     alp_status st = make_tmap_3d_bf16(&ta, da, (uint64_t)kpad, (uint64_t)M, (uint64_t)s, kTK, kTM);
     if (st != ALP_OK) return st;
@@ -486,7 +679,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     if (tiles_m * tiles_n > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     p.tiles_m = (int)tiles_m;
     p.tiles_n = (int)tiles_n;
-    p.group_m = group_m > 0 ? group_m : emul_group_m();
+    p.group_m = group_m > 0 ? group_m : emul_group_m(arr == kEmulPair);
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
     const int tiles = (int)(tiles_m * tiles_n);
@@ -511,15 +704,32 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
         emul_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(ta, tb, p);
         return cuda_status(cudaGetLastError());
     }
-    cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const bool pair = arr == kEmulPair;
+    const int smem_bytes = pair ? kPairSmemBytes : kSmemBytes;
+    const int64_t pair_tiles = ((tiles_m + 1) / 2) * tiles_n;
+    int64_t clusters = pair_tiles;
+    if (pair && emul_tail_split_on()) {   // in units of pairs, half the SMs each
+        const TailSplit ts = tail_split((int)pair_tiles, s, num_sms() / 2, trim);
+        p.n_full = ts.n_full;
+        p.pieces = ts.pieces;
+        p.t_ranges = 0;
+        for (int i = 0; i < ts.pieces; ++i)
+            p.t_ranges |= (uint64_t)(ts.t_lo[i] | ts.t_hi[i] << 4) << (8 * i);
+        if (ts.n_full < pair_tiles) clusters = ts.n_full + (pair_tiles - ts.n_full) * ts.pieces;
+    }
+    cudaError_t e = pair ? cudaFuncSetAttribute(emul_gemm_pair_kernel,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                smem_bytes)
+                         : cudaFuncSetAttribute(emul_gemm_kernel<2>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                smem_bytes);
     if (e != cudaSuccess) return cuda_status(e);
-    const int64_t grid = 2 * ((tiles_m + 1) / 2) * tiles_n;
+    const int64_t grid = 2 * (pair ? clusters : pair_tiles);
     if (grid > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)grid);
     lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = kSmemBytes;
+    lc.dynamicSmemBytes = smem_bytes;
     lc.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -528,7 +738,8 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     attr[0].val.clusterDim.z = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    e = cudaLaunchKernelEx(&lc, emul_gemm_kernel<2>, ta, tb, p);
+    e = pair ? cudaLaunchKernelEx(&lc, emul_gemm_pair_kernel, ta, tb, p)
+             : cudaLaunchKernelEx(&lc, emul_gemm_kernel<2>, ta, tb, p);
     return cuda_status(e);
 }
 

@@ -70,6 +70,7 @@ std::vector<alp_config> emul_configs() {
     std::vector<alp_config> v;
     for (int cl = 1; cl <= 2; ++cl)
         for (int g : kGroups) v.push_back(alp_config{128, 256, 64, cl, 0, g});
+    for (int g : kGroups) v.push_back(alp_config{256, 256, 64, 2, 0, g});   // CTA pairs
     return v;
 }
 
@@ -175,7 +176,8 @@ bool time_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_confi
     const auto* db = reinterpret_cast<const __nv_bfloat16*>(base + ba);
     int32_t* G = reinterpret_cast<int32_t*>(base + ba + bb);
     auto launch = [&]() {
-        return emul_slice_gemm(M, N, Kp, s, da, db, kpad, G, ldg, st, cfg.stages, cfg.tm);
+        return emul_slice_gemm(M, N, Kp, s, da, db, kpad, G, ldg, st, cfg.stages,
+                               emul_arrangement_of(cfg));
     };
     if (!time_launch(launch, st, runs, meas_best, meas_median)) return false;
     *est_ms = *meas_best * ((double)K / (double)Kp);

@@ -124,14 +124,17 @@ def test_emul_8bit_digits_bit_exact_vs_model(alp, orc, shape, kind, s, phi):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("cluster,group", [(1, 1), (1, 8), (2, 1), (2, 4), (2, 32)])
-def test_emul_every_config_bit_exact(alp, orc, cluster, group):
-    """Each emulated config (blocks sharing B tiles, raster group), forced
-    through the tuned cache, on a shape with an odd number of tile-rows."""
+@pytest.mark.parametrize("bm,cluster,group", [(128, 1, 1), (128, 1, 8), (128, 2, 1), (128, 2, 4),
+                                              (128, 2, 32), (256, 2, 1), (256, 2, 8), (256, 2, 32)])
+def test_emul_every_config_bit_exact(alp, orc, bm, cluster, group):
+    """Each emulated config (one block per tile, blocks sharing B tiles, CTA
+    pairs sharing each MMA; raster group), forced through the tuned cache, on
+    a shape with an odd number of tile-rows and ragged edges."""
     M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
-    cfg = (128, 256, 64, cluster, 0, group)
+    cfg = (bm, 256, 64, cluster, 0, group)
     assert alp.alp_config_valid(cfg, alp.ALP_PATH_EMUL)
-    A, B, C = inputs.gemm_operands(3600 + cluster * 100 + group, M, N, K, kind="scaled", phi=8)
+    A, B, C = inputs.gemm_operands(3600 + bm + cluster * 100 + group, M, N, K, kind="scaled",
+                                   phi=8)
     alp.alp_tune_set_cached(M, N, K, alp.ALP_PATH_EMUL, cfg)
     try:
         runs = (("b7", 8), ("b8", 7), ("b8t", 7))
