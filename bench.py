@@ -374,7 +374,7 @@ def run_alp(args):
         hC = torch.empty(n, n, dtype=torch.float64).pin_memory()
         sets = [(torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)) for _ in range(2)]
         copy = torch.cuda.Stream(dev)
-        ksteps = max(2, min(args.steps, 6))
+        ksteps = max(2, args.steps)
 
         def run_e2e(k):
             ev = lambda: torch.cuda.Event(enable_timing=True)

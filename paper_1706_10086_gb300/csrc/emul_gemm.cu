@@ -20,10 +20,9 @@
 // first digit) products -- 1024 / 2048 / 4096 for b = 7, 256 / 512 / 1024 for
 // b = 8 -- has |partial sum| <= 2^24: every value the f32 accumulator takes
 // is an integer f32 holds exactly, so no MMA rounds.  The drain converts each
-// chunk's integer exactly into a 32-bit running sum (tmem_drain32_exact); the
-// sum minus chunks * kChunkBias is the exact group sum S^t (mod 2^32
-// arithmetic, and |S^t| < 2^31 for the K limits).  At the end of each group
-// the block writes S^t to G[t-2] (int32).
+// chunk's integer exactly (cvt) and adds it into a 32-bit running sum, the
+// exact group sum S^t (|S^t| < 2^31 for the K limits).  At the end of each
+// group the block writes S^t to G[t-2] (int32).
 #include <cstdlib>
 
 #include "emul.cuh"
@@ -144,20 +143,18 @@ __device__ __forceinline__ int job_p(uint32_t j) { return (int)((j >> 20) & 7u) 
 __device__ __forceinline__ int job_q(uint32_t j) { return (int)((j >> 23) & 7u) + 1; }
 __device__ __forceinline__ bool job_last(uint32_t j) { return (j >> 26) & 1u; }
 
-// g[0..3] = a[0..3] - bias (if do_store), then a[0..3] = 0.
-__device__ __forceinline__ void store4_sub_and_zero(int32_t* g, uint32_t bias, uint32_t do_store,
-                                                    uint32_t& a0, uint32_t& a1, uint32_t& a2,
-                                                    uint32_t& a3) {
+// g[0..3] = a[0..3] (if do_store), then a[0..3] = 0.
+__device__ __forceinline__ void store4_and_zero(int32_t* g, uint32_t do_store, uint32_t& a0,
+                                                uint32_t& a1, uint32_t& a2, uint32_t& a3) {
     asm volatile(
         "{\n"
-        " .reg .b32 t<4>;\n .reg .pred p;\n"
-        " setp.ne.u32 p, %6, 0;\n"
-        " sub.u32 t0, %0, %5;\n sub.u32 t1, %1, %5;\n sub.u32 t2, %2, %5;\n sub.u32 t3, %3, %5;\n"
-        " @p st.global.v4.b32 [%4], {t0, t1, t2, t3};\n"
+        " .reg .pred p;\n"
+        " setp.ne.u32 p, %5, 0;\n"
+        " @p st.global.v4.b32 [%4], {%0, %1, %2, %3};\n"
         " mov.b32 %0, 0;\n mov.b32 %1, 0;\n mov.b32 %2, 0;\n mov.b32 %3, 0;\n"
         "}\n"
         : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
-        : "l"(g), "r"(bias), "r"(do_store)
+        : "l"(g), "r"(do_store)
         : "memory");
 }
 
@@ -178,7 +175,6 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
     uint32_t acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0;
-    uint32_t nchunks = 0;
     int t_group = 2;
     for (int job = 0; job < njobs; ++job) {
         const uint32_t b = job & 1;
@@ -187,29 +183,26 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
         const uint32_t taddr =
             tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tmem_drain32_exact(taddr + c * 32, &acc[c * 32]);
+        for (int c = 0; c < 4; ++c) tmem_drain32_cvt(taddr + c * 32, &acc[c * 32]);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
             if (acce_remote) mbar_arrive_cluster(acce_remote + b * 8);
             else mbar_arrive(&acce[b]);
         }
-        ++nchunks;
         const uint32_t jd = jobs[job];
         if (job_last(jd)) {
             t_group = job_p(jd) + job_q(jd);
-            const uint32_t bias = nchunks * kChunkBias;
             // G rows are padded to whole 256-column tiles, so the strip is in
-            // bounds; rows past M are not stored.  Each asm block stores
-            // (acc - bias) and zeroes acc in place.
+            // bounds; rows past M are not stored.  Each asm block stores acc
+            // and zeroes it in place.
             int32_t* g = prm.G + (int64_t)(t_group - 2) * prm.gplane + (int64_t)gm * prm.ldg +
                          n0 + half * 128;
             const uint32_t do_store = gm < prm.M ? 1u : 0u;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-                store4_sub_and_zero(g + 4 * i, bias, do_store, acc[4 * i], acc[4 * i + 1],
-                                    acc[4 * i + 2], acc[4 * i + 3]);
-            nchunks = 0;
+                store4_and_zero(g + 4 * i, do_store, acc[4 * i], acc[4 * i + 1], acc[4 * i + 2],
+                                acc[4 * i + 3]);
         }
     }
 }
