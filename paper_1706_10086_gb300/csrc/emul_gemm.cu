@@ -559,18 +559,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Streaming multiprocessors of the current device (one block of this kernel
-// fits per SM).
-int num_sms() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n;
-}
-
 }  // namespace
 
 // Tail split of a launch of `tiles` tiles on `sms` SMs (one block each): the
@@ -680,7 +668,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.pieces = 1;
     p.t_ranges = 2u | (uint32_t)(s + 1) << 4;
     if (cl == 1 && emul_tail_split_on()) {
-        const TailSplit ts = tail_split(tiles, s, num_sms(), trim);
+        const TailSplit ts = tail_split(tiles, s, device_sm_count(), trim);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
         p.t_ranges = 0;
@@ -702,7 +690,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     const int64_t pair_tiles = ((tiles_m + 1) / 2) * tiles_n;
     int64_t clusters = pair_tiles;
     if (pair && emul_tail_split_on()) {   // in units of pairs, half the SMs each
-        const TailSplit ts = tail_split((int)pair_tiles, s, num_sms() / 2, trim);
+        const TailSplit ts = tail_split((int)pair_tiles, s, device_sm_count() / 2, trim);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
         p.t_ranges = 0;
