@@ -140,7 +140,10 @@ __device__ __forceinline__ void run_tile(const TileProblem& pr, int64_t m0, int6
     tile_ldg<TM, TN>(pr, m0, n0, bm, bn, bk, smem, vec2);
 }
 
-__global__ void __launch_bounds__(kBatchedThreads, 1)
+// MAXT: the largest bm and bn the class table may hold.  With MAXT = 64 only
+// the register tiles up to 4 x 4 are compiled, which fit two blocks per SM.
+template <int MAXT>
+__global__ void __launch_bounds__(kBatchedThreads, MAXT <= 64 ? 2 : 1)
     batched_persistent_kernel(BatchArgs a, Plan pl, ClassTable tab) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int64_t s_tile;
@@ -182,9 +185,14 @@ __global__ void __launch_bounds__(kBatchedThreads, 1)
         const int tm = bm / 16, tn = bn / 16;
 #define ALP_BATCHED_CASE(x, y) \
     if (tm == x && tn == y) run_tile<x, y>(pr, m0, n0, bm, bn, bk, smem, vec2);
-        ALP_BATCHED_CASE(2, 2) else ALP_BATCHED_CASE(2, 4) else ALP_BATCHED_CASE(2, 8)
-        else ALP_BATCHED_CASE(4, 2) else ALP_BATCHED_CASE(4, 4) else ALP_BATCHED_CASE(4, 8)
-        else ALP_BATCHED_CASE(8, 2) else ALP_BATCHED_CASE(8, 4) else ALP_BATCHED_CASE(8, 8)
+        if (MAXT <= 64) {
+            ALP_BATCHED_CASE(2, 2) else ALP_BATCHED_CASE(2, 4) else ALP_BATCHED_CASE(4, 2)
+            else ALP_BATCHED_CASE(4, 4)
+        } else {
+            ALP_BATCHED_CASE(2, 2) else ALP_BATCHED_CASE(2, 4) else ALP_BATCHED_CASE(2, 8)
+            else ALP_BATCHED_CASE(4, 2) else ALP_BATCHED_CASE(4, 4) else ALP_BATCHED_CASE(4, 8)
+            else ALP_BATCHED_CASE(8, 2) else ALP_BATCHED_CASE(8, 4) else ALP_BATCHED_CASE(8, 8)
+        }
 #undef ALP_BATCHED_CASE
     }
 }
@@ -207,6 +215,17 @@ PlanLayout plan_layout(int64_t count) {
     return L;
 }
 
+// Largest bm or bn among the classes in `present` (bit c: class c has tiles).
+int max_tile(const ClassTable& t, unsigned present) {
+    int m = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        if (!(present >> c & 1u)) continue;
+        m = t.bm[c] > m ? t.bm[c] : m;
+        m = t.bn[c] > m ? t.bn[c] : m;
+    }
+    return m;
+}
+
 int max_smem(const ClassTable& t) {
     int m = 0;
     for (int c = 0; c < kClasses; ++c) {
@@ -214,6 +233,25 @@ int max_smem(const ClassTable& t) {
         m = b > m ? b : m;
     }
     return m;
+}
+
+// The persistent kernel for `tiles` tiles on `sms` SMs, as many blocks as fit.
+// When the classes present use tiles of at most 64 x 64 it runs the variant
+// that fits two blocks per SM.
+alp_status launch_persistent(const BatchArgs& a, const Plan& pl, const ClassTable& tab,
+                             int64_t tiles, unsigned present, int sms, cudaStream_t stream) {
+    const int smem = max_smem(tab);
+    auto kernel = max_tile(tab, present) <= 64 ? batched_persistent_kernel<64>
+                                               : batched_persistent_kernel<128>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBatchedThreads, smem);
+    if (occ < 1) occ = 1;
+    int64_t grid = (int64_t)sms * occ;
+    if (grid > tiles) grid = tiles;
+    kernel<<<(unsigned)grid, kBatchedThreads, smem, stream>>>(a, pl, tab);
+    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace
@@ -233,27 +271,18 @@ alp_status batched_launch(const BatchArgs& a, const int64_t* hM, const int64_t* 
     // grid size from the host copies (performance only: the persistent loop
     // covers any number of tiles)
     int64_t tiles = 0;
+    unsigned present = 0;
     for (int64_t p = 0; p < a.count; ++p) {
         if (hM[p] <= 0 || hN[p] <= 0) continue;
         const int c = class_of(hM[p], hN[p]);
         tiles += ((hM[p] + tab.bm[c] - 1) / tab.bm[c]) * ((hN[p] + tab.bn[c] - 1) / tab.bn[c]);
+        present |= 1u << c;
     }
     batched_plan_kernel<<<1, kPlanThreads, 0, stream>>>(a, pl, tab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     if (tiles == 0) return ALP_OK;
-    const int smem = max_smem(tab);
-    e = cudaFuncSetAttribute(batched_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_persistent_kernel, kBatchedThreads,
-                                                  smem);
-    if (occ < 1) occ = 1;
-    int64_t grid = (int64_t)device_sm_count() * occ;
-    if (grid > tiles) grid = tiles;
-    batched_persistent_kernel<<<(unsigned)grid, kBatchedThreads, smem, stream>>>(a, pl, tab);
-    return cuda_status(cudaGetLastError());
+    return launch_persistent(a, pl, tab, tiles, present, device_sm_count(), stream);
 }
 
 }  // namespace alp
@@ -464,29 +493,21 @@ extern "C" alp_status alp_gemm_batched_varsize_noalloc(
     pl.meta = reinterpret_cast<int64_t*>(ws + L.off_meta);
     pl.counter = reinterpret_cast<unsigned long long*>(ws + L.off_counter);
     int64_t tiles = 0;
+    unsigned present = 0;
     for (int64_t p = 0; p < count; ++p) {
         if (hM[p] <= 0 || hN[p] <= 0) continue;
         const int c = class_of(hM[p], hN[p]);
         tiles += ((hM[p] + tab.bm[c] - 1) / tab.bm[c]) * ((hN[p] + tab.bn[c] - 1) / tab.bn[c]);
+        present |= 1u << c;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     batched_plan_kernel<<<1, kPlanThreads, 0, s>>>(a, pl, tab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     if (tiles == 0) return ALP_OK;
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return ALP_ERR_CUDA;
-    const int smem = max_smem(tab);
-    e = cudaFuncSetAttribute(batched_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_persistent_kernel, kBatchedThreads,
-                                                  smem);
-    if (occ < 1) occ = 1;
-    int64_t grid = (int64_t)sms * occ;
-    if (grid > tiles) grid = tiles;
-    batched_persistent_kernel<<<(unsigned)grid, kBatchedThreads, smem, s>>>(a, pl, tab);
-    return cuda_status(cudaGetLastError());
+    return launch_persistent(a, pl, tab, tiles, present, sms, s);
 }

@@ -320,6 +320,43 @@ def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
         if log:
             log(f"class {c}: {n} problems, default {old} {times.get(tuple(old), float('nan')):.3f} ms"
                 f" -> {win} {times[win]:.3f} ms")
+    # Each class was timed alone; in one batch a single 128-wide tile anywhere
+    # puts every class on the one-block-per-SM kernel.  Time the whole batch
+    # with the per-class winners and with the best tiles of at most 64 and keep
+    # the faster table.
+    small = {c: min((k for k in v[2] if max(k[0], k[1]) <= 64), key=lambda k: (v[2][k], k))
+             for c, v in out.items()}
+    if any(out[c][0] != small[c] for c in out):
+        n = len(M)
+        t = lambda a, dt=torch.int64: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+        args = (n, t(M), t(N), t(K), t(np.full(n, alpha), torch.float64), t(np.asarray(pA)),
+                t(K), t(np.asarray(pB)), t(N), t(np.full(n, beta), torch.float64),
+                t(np.asarray(pC)), t(N), M, N, K)
+        ws = alp.alp_gemm_batched_workspace(n, M, N, K)
+        work = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+
+        def whole(table):
+            for c, cfg in table.items():
+                alp.alp_batched_set_class_config(c, *cfg)
+            alp.alp_gemm_batched_varsize(*args, work, ws, stream=stream)
+            best = float("inf")
+            for _ in range(runs):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                alp.alp_gemm_batched_varsize(*args, work, ws, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best
+        t_win = whole({c: v[0] for c, v in out.items()})
+        t_small = whole(small)
+        if log:
+            log(f"whole batch: per-class winners {t_win:.3f} ms, tiles <= 64 {t_small:.3f} ms")
+        chosen = small if t_small < t_win else {c: v[0] for c, v in out.items()}
+        for c, cfg in chosen.items():
+            alp.alp_batched_set_class_config(c, *cfg)
+            out[c] = (cfg, out[c][2][cfg], out[c][2])
     return out
 
 
