@@ -141,9 +141,10 @@ __device__ __forceinline__ void run_tile(const TileProblem& pr, int64_t m0, int6
 }
 
 // MAXT: the largest bm and bn the class table may hold.  With MAXT = 64 only
-// the register tiles up to 4 x 4 are compiled, which fit two blocks per SM.
+// the register tiles up to 4 x 4 are compiled, which fit two blocks per SM;
+// with MAXT = 32 only 2 x 2, three blocks per SM.
 template <int MAXT>
-__global__ void __launch_bounds__(kBatchedThreads, MAXT <= 64 ? 2 : 1)
+__global__ void __launch_bounds__(kBatchedThreads, MAXT <= 32 ? 3 : MAXT <= 64 ? 2 : 1)
     batched_persistent_kernel(BatchArgs a, Plan pl, ClassTable tab) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int64_t s_tile;
@@ -185,7 +186,9 @@ __global__ void __launch_bounds__(kBatchedThreads, MAXT <= 64 ? 2 : 1)
         const int tm = bm / 16, tn = bn / 16;
 #define ALP_BATCHED_CASE(x, y) \
     if (tm == x && tn == y) run_tile<x, y>(pr, m0, n0, bm, bn, bk, smem, vec2);
-        if (MAXT <= 64) {
+        if (MAXT <= 32) {
+            ALP_BATCHED_CASE(2, 2)
+        } else if (MAXT <= 64) {
             ALP_BATCHED_CASE(2, 2) else ALP_BATCHED_CASE(2, 4) else ALP_BATCHED_CASE(4, 2)
             else ALP_BATCHED_CASE(4, 4)
         } else {
@@ -236,13 +239,15 @@ int max_smem(const ClassTable& t) {
 }
 
 // The persistent kernel for `tiles` tiles on `sms` SMs, as many blocks as fit.
-// When the classes present use tiles of at most 64 x 64 it runs the variant
-// that fits two blocks per SM.
+// When the classes present use tiles of at most 64 x 64 (32 x 32) it runs the
+// variant that fits two (three) blocks per SM.
 alp_status launch_persistent(const BatchArgs& a, const Plan& pl, const ClassTable& tab,
                              int64_t tiles, unsigned present, int sms, cudaStream_t stream) {
     const int smem = max_smem(tab);
-    auto kernel = max_tile(tab, present) <= 64 ? batched_persistent_kernel<64>
-                                               : batched_persistent_kernel<128>;
+    const int mt = max_tile(tab, present);
+    auto kernel = mt <= 32   ? batched_persistent_kernel<32>
+                  : mt <= 64 ? batched_persistent_kernel<64>
+                             : batched_persistent_kernel<128>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_status(e);
     int occ = 0;

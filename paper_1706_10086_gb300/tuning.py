@@ -320,13 +320,18 @@ def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
         if log:
             log(f"class {c}: {n} problems, default {old} {times.get(tuple(old), float('nan')):.3f} ms"
                 f" -> {win} {times[win]:.3f} ms")
-    # Each class was timed alone; in one batch a single 128-wide tile anywhere
-    # puts every class on the one-block-per-SM kernel.  Time the whole batch
-    # with the per-class winners and with the best tiles of at most 64 and keep
-    # the faster table.
-    small = {c: min((k for k in v[2] if max(k[0], k[1]) <= 64), key=lambda k: (v[2][k], k))
-             for c, v in out.items()}
-    if any(out[c][0] != small[c] for c in out):
+    # Each class was timed alone; in one batch the largest tile of any class
+    # decides the persistent kernel's variant (128: one block per SM, 64: two,
+    # 32: three).  Time the whole batch with the per-class winners and with the
+    # best tiles of at most 64 and of at most 32, and keep the fastest table.
+    def capped(cap):
+        return {c: min((k for k in v[2] if max(k[0], k[1]) <= cap), key=lambda k: (v[2][k], k))
+                for c, v in out.items()}
+    tables = [{c: v[0] for c, v in out.items()}]
+    for cap in (64, 32):
+        if min(tiles) <= cap and capped(cap) not in tables:
+            tables.append(capped(cap))
+    if len(tables) > 1:
         n = len(M)
         t = lambda a, dt=torch.int64: torch.tensor(np.asarray(a), dtype=dt, device=dev)
         args = (n, t(M), t(N), t(K), t(np.full(n, alpha), torch.float64), t(np.asarray(pA)),
@@ -349,11 +354,11 @@ def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
                 e1.synchronize()
                 best = min(best, e0.elapsed_time(e1))
             return best
-        t_win = whole({c: v[0] for c, v in out.items()})
-        t_small = whole(small)
+        ts = [whole(tb) for tb in tables]
         if log:
-            log(f"whole batch: per-class winners {t_win:.3f} ms, tiles <= 64 {t_small:.3f} ms")
-        chosen = small if t_small < t_win else {c: v[0] for c, v in out.items()}
+            log("whole batch: " + ", ".join(f"{max(max(k[0], k[1]) for k in tb.values())}-wide "
+                                            f"{t:.3f} ms" for tb, t in zip(tables, ts)))
+        chosen = tables[int(np.argmin(ts))]
         for c, cfg in chosen.items():
             alp.alp_batched_set_class_config(c, *cfg)
             out[c] = (cfg, out[c][2][cfg], out[c][2])
