@@ -55,10 +55,12 @@ alp_status alp_debug_inject_skip(int kt);
 /* ---- autotuner helpers --------------------------------------------------- */
 
 /* Time of one config for (M, N, K) on `path`, in ms: the best of `runs`
- * CUDA-event-timed launches after one warm-up.  use_proxy = 1 times one wave
- * of blocks with K capped at 256 and scales by the waves and by K / 256 (the
- * estimate alp_tune records); use_proxy = 0 times the whole problem.  For the
- * emulated path the tensor-core stage is timed.  Allocates its own scratch. */
+ * CUDA-event-timed launches after one warm-up.  use_proxy = 1 estimates (the
+ * estimate alp_tune records): native, one wave of blocks with K capped at 256,
+ * scaled by the waves and by K / 256; emulated, the tensor-core stage on the
+ * whole grid with K capped at 2048 (env ALP_TUNE_PROXY_K_EMUL), scaled by
+ * K / cap.  use_proxy = 0 times the whole problem (for the emulated path, its
+ * tensor-core stage).  Allocates its own scratch. */
 alp_status alp_tune_time_config(int64_t M, int64_t N, int64_t K, alp_path path,
                                 const alp_config* cfg, int use_proxy, int runs, double* est_ms);
 /* Puts cfg into the tuned cache for (M, N, K, path) (what alp_tune(EXHAUSTIVE)

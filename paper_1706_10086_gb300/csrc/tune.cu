@@ -43,7 +43,18 @@ bool model_predict(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* o
 
 namespace {
 constexpr int64_t kProxyK = 256;        // K cap of the native timing proxy
-constexpr int64_t kProxyKEmul = 256;    // K cap of the emulated timing proxy
+// K cap of the emulated timing proxy (env ALP_TUNE_PROXY_K_EMUL, a multiple of
+// 64 in [64, 32768]; default 2048).  Measured on GB300 against full-K timings
+// of 5 shapes: a cap of 256 over-estimated by 2-3x and ranked the one-block
+// kernel above the CTA pairs (wrong by 30 %); 1024 ranked right but
+// over-estimated by about 1.3x; 2048 came within 1-12 %.
+int64_t proxy_k_emul() {
+    if (const char* s = std::getenv("ALP_TUNE_PROXY_K_EMUL")) {
+        const long long v = std::atoll(s);
+        if (v >= 64 && v <= 32768 && v % 64 == 0) return v;
+    }
+    return 2048;
+}
 constexpr int kTimedRuns = 10;          // the paper keeps the best of ten runs
 
 std::mutex g_tmu;
@@ -165,7 +176,7 @@ bool time_config(int64_t M, int64_t N, int64_t K, alp_path path, const alp_confi
     }
     // emulated path: the tensor-core stage (its cost dominates), full grid
     const int s = kMaxSlices;
-    const int64_t Kp = use_proxy ? std::min(K, kProxyKEmul) : K;
+    const int64_t Kp = use_proxy ? std::min(K, proxy_k_emul()) : K;
     const int64_t kpad = (Kp + kEmulBK - 1) / kEmulBK * kEmulBK;
     const int64_t ldg = (N + 255) / 256 * 256;
     const size_t ba = up256((size_t)s * M * kpad * 2), bb = up256((size_t)s * N * kpad * 2);
@@ -203,7 +214,7 @@ void db_append(int64_t M, int64_t N, int64_t K, alp_path path, const std::vector
                   "\"proxy\": %s, \"kcap\": %lld, \"winner\": %d, \"configs\": [",
                   name, (long long)M, (long long)N, (long long)K,
                   path == ALP_PATH_NATIVE ? "native" : "emul", proxy ? "true" : "false",
-                  (long long)(path == ALP_PATH_NATIVE ? kProxyK : kProxyKEmul), winner);
+                  (long long)(path == ALP_PATH_NATIVE ? kProxyK : proxy_k_emul()), winner);
     line += buf;
     for (size_t i = 0; i < cs.size(); ++i) {
         std::snprintf(buf, sizeof buf, "%s[%d, %d, %d, %d, %d, %d, %.6g, %.6g, %.6g]",
@@ -325,7 +336,7 @@ alp_status alp_tune(int64_t M, int64_t N, int64_t K, alp_path path, alp_tune_mod
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (winner < 0) return ALP_ERR_CUDA;
-    const bool proxy = path == ALP_PATH_NATIVE ? (K > kProxyK) : (K > kProxyKEmul);
+    const bool proxy = path == ALP_PATH_NATIVE ? (K > kProxyK) : (K > proxy_k_emul());
     db_append(M, N, K, path, cs, est, best, med, winner, proxy);
     cache_config(M, N, K, path, cs[winner]);
     *out = cs[winner];

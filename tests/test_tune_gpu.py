@@ -51,6 +51,20 @@ def test_timing_proxy_tracks_full_runs(alp):
             assert abs(est / full - 1) < 0.15, (M, N, K, cfg, est, full)
 
 
+def test_emulated_proxy_ranks_like_full_runs(alp):
+    """The emulated timing proxy (K capped at 2048) against whole-problem
+    timings: within 20 %, and it ranks the CTA-pair config above the
+    one-block config as the full runs do."""
+    E = alp.ALP_PATH_EMUL
+    single, pair = (128, 256, 64, 1, 0, 8), (256, 256, 64, 2, 0, 16)
+    for (M, N, K) in [(4096, 4096, 4096), (2048, 8192, 4096)]:
+        est = {c: alp.alp_tune_time_config(M, N, K, E, c, True, 3) for c in (single, pair)}
+        full = {c: alp.alp_tune_time_config(M, N, K, E, c, False, 2) for c in (single, pair)}
+        for c in (single, pair):
+            assert abs(est[c] / full[c] - 1) < 0.2, (M, N, K, c, est[c], full[c])
+        assert (est[pair] < est[single]) == (full[pair] < full[single]), (est, full)
+
+
 def test_predict_needs_model(alp):
     alp.alp_tune_unload_model()
     st, _, _ = alp.alp_tune(512, 512, 512, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_PREDICT,
