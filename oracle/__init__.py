@@ -56,10 +56,12 @@ def lib():
             L.orc_split.argtypes = [i64, i64, vp, i64, vp, i32, i32, vp, vp]
             L.orc_emul_gemm.argtypes = [i64, i64, i64, f64, vp, i64, vp, i64, f64, vp, i64,
                                         vp, i64, i32, i32, i32, vp, i64, i32]
+            L.orc_emul_gemm_f32.argtypes = L.orc_emul_gemm.argtypes
             L.orc_int128_to_double.argtypes = [i64, ctypes.c_uint64]
             L.orc_int128_to_double.restype = ctypes.c_double
             for fn in ("orc_gemm_f64", "orc_absgemm", "orc_row_exponents", "orc_col_exponents",
-                       "orc_split", "orc_emul_gemm", "orc_long_double_digits"):
+                       "orc_split", "orc_emul_gemm", "orc_emul_gemm_f32",
+                       "orc_long_double_digits"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -165,6 +167,24 @@ def emul_gemm(alpha, A, B, beta, C, s, b=BF16_DIGIT_BITS, rows=None, nthreads=No
                              _threads(nthreads))
     assert rc in (0, 2), rc
     return D, rc
+
+
+def emul_gemm_f32(alpha, A, B, beta, C, s, b=8, rows=None, nthreads=None, trim=False):
+    """The emulated GEMM for FP32 operands (float32 arrays, float alpha and
+    beta), bit-exact model of the GPU's FP32 path.  Returns (D float32, status)."""
+    A32, B32 = np.asarray(A, dtype=np.float32), np.asarray(B, dtype=np.float32)
+    M, K = A32.shape
+    N = B32.shape[1]
+    C32 = np.zeros((M, N), np.float32) if C is None else np.asarray(C, dtype=np.float32)
+    A64, B64, C64 = (_f64(x.astype(np.float64)) for x in (A32, B32, C32))
+    ridx = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = M if ridx is None else len(ridx)
+    D = np.empty((nr, N))
+    rc = lib().orc_emul_gemm_f32(M, N, K, float(np.float32(alpha)), _ptr(A64), K, _ptr(B64), N,
+                                 float(np.float32(beta)), _ptr(C64), N, _ptr(D), N, int(s), int(b),
+                                 int(bool(trim)), _ptr(ridx), nr, _threads(nthreads))
+    assert rc in (0, 2), rc
+    return D.astype(np.float32), rc
 
 
 def int128_to_double(x: int) -> float:

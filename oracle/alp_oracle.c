@@ -14,6 +14,7 @@
  *   orc_emul_gemm     the emulated FP64 GEMM end to end: exponents, digits,
  *                     exact integer slice products, FP64 recombination in its
  *                     fixed order.  The GPU must reproduce it bit for bit.
+ *   orc_emul_gemm_f32 the same for FP32 operands and an FP32 result.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math, no
  * contraction, so every expression rounds exactly where it is written).
@@ -225,6 +226,7 @@ typedef struct {
     const int16_t *dA, *dB;   /* [s][nrows][K] (row r of the output), [s][N][K] */
     int64_t nra;
     const int32_t *e, *f;
+    int out_f32;              /* FP32 result: float rounding, float alpha and beta */
 } emul_ctx;
 
 static void emul_row(void* p, int64_t r) {
@@ -234,7 +236,10 @@ static void emul_row(void* p, int64_t r) {
     const int s = g->s, b = g->b;
     for (int64_t j = 0; j < g->N; ++j) {
         if (g->alpha == 0.0 || g->K == 0) {
-            d[j] = (g->beta == 0.0) ? 0.0 : g->beta * g->C[i * g->ldc + j];
+            if (g->out_f32)
+                d[j] = (g->beta == 0.0) ? 0.0 : (double)((float)g->beta * (float)g->C[i * g->ldc + j]);
+            else
+                d[j] = (g->beta == 0.0) ? 0.0 : g->beta * g->C[i * g->ldc + j];
             continue;
         }
         __int128 X = 0;                                     /* exact */
@@ -249,6 +254,14 @@ static void emul_row(void* p, int64_t r) {
                 for (int64_t k = 0; k < g->K; ++k) S += (int64_t)a[k] * (int64_t)bb[k];
             }
             X += (__int128)S * ((__int128)1 << ((s + 1 - t) * b));
+        }
+        if (g->out_f32) {
+            /* |X| < 2^63 for s * b <= 32: (float) of the int64 rounds once */
+            float v = ldexpf((float)(int64_t)X, g->e[i] + g->f[j] - (s + 1) * b);
+            float out = (float)g->alpha * v;
+            if (g->beta != 0.0) out = fmaf((float)g->beta, (float)g->C[i * g->ldc + j], out);
+            d[j] = (double)out;
+            continue;
         }
         double v = ldexp((double)X, g->e[i] + g->f[j] - (s + 1) * b);   /* (double) rounds once */
         double out = g->alpha * v;
@@ -277,17 +290,11 @@ static void split_row(void* p, int64_t r) {
     }
 }
 
-/* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range);
- * trim = 1 selects the trimmed last group.  Returns 0, or 2 when A or B holds
- * an Inf or NaN (the emulated path does not support them), 1 on bad sizes. */
-int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
-                  const double* A, int64_t lda, const double* B, int64_t ldb,
-                  double beta, const double* C, int64_t ldc,
-                  double* D, int64_t ldd, int s, int b, int trim,
-                  const int64_t* rows, int64_t nrows, int nthreads) {
-    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 15 || s * b > 90 ||
-        (trim != 0 && trim != 1))
-        return 1;
+static int emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double beta, const double* C, int64_t ldc,
+                     double* D, int64_t ldd, int s, int b, int trim,
+                     const int64_t* rows, int64_t nrows, int nthreads, int out_f32) {
     const int64_t nra = rows ? nrows : M;
     int32_t* e = (int32_t*)calloc((size_t)(M > 0 ? M : 1), sizeof(int32_t));
     int32_t* f = (int32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
@@ -304,10 +311,43 @@ int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
     for_rows(nra, nthreads, split_row, &sa);
     split_ctx sb = {Bt, K, K, f, NULL, s, b, dB, N};
     for_rows(N, nthreads, split_row, &sb);
-    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, trim, dA, dB, nra, e, f};
+    emul_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, s, b, trim, dA, dB, nra, e, f,
+                  out_f32};
     for_rows(nra, nthreads, emul_row, &g);
     free(Bt); free(dA); free(dB); free(e); free(f);
     return 0;
+}
+
+/* Emulated GEMM with s digits of b bits (s*b + 32 < 127 keeps X in range);
+ * trim = 1 selects the trimmed last group.  Returns 0, or 2 when A or B holds
+ * an Inf or NaN (the emulated path does not support them), 1 on bad sizes. */
+int orc_emul_gemm(int64_t M, int64_t N, int64_t K, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb,
+                  double beta, const double* C, int64_t ldc,
+                  double* D, int64_t ldd, int s, int b, int trim,
+                  const int64_t* rows, int64_t nrows, int nthreads) {
+    if (M < 0 || N < 0 || K < 0 || s < 1 || s > 16 || b < 1 || b > 15 || s * b > 90 ||
+        (trim != 0 && trim != 1))
+        return 1;
+    return emul_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, b, trim, rows,
+                     nrows, nthreads, 0);
+}
+
+/* The same for FP32 operands (A, B, C, alpha and beta hold float values,
+ * passed as double, which is exact): the digits and the exact integer sum X
+ * are those above; the result is v = ldexpf((float)X, e_i + f_j - (s+1) b)
+ * (one rounding, a second only when v is subnormal), out = (float)alpha * v,
+ * then fmaf((float)beta, C_ij, out) when beta != 0, all in float arithmetic.
+ * s * b <= 32 keeps |X| below 2^63.  D receives the float results. */
+int orc_emul_gemm_f32(int64_t M, int64_t N, int64_t K, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double beta, const double* C, int64_t ldc,
+                      double* D, int64_t ldd, int s, int b, int trim,
+                      const int64_t* rows, int64_t nrows, int nthreads) {
+    if (M < 0 || N < 0 || K < 0 || s < 1 || b < 1 || s * b > 32 || (trim != 0 && trim != 1))
+        return 1;
+    return emul_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, b, trim, rows,
+                     nrows, nthreads, 1);
 }
 
 /* Significand bits of long double on this host (64 on x86_64, 113 on aarch64),

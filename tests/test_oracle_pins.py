@@ -372,3 +372,123 @@ def test_emul_gemm_rows_match_full(orc):
     full, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 6)
     part, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 6, rows=np.array([8, 2]))
     assert np.array_equal(part, full[[8, 2]])
+
+
+# ---- the FP32 variant of the emulated GEMM --------------------------------
+
+U32 = 2.0 ** -24
+
+
+def fraction_to_f32(x: Fraction) -> np.float32:
+    """Nearest float32 to the rational x (ties to even, gradual underflow,
+    overflow to infinity): the plain definition of one FP32 rounding."""
+    if x == 0:
+        return np.float32(0.0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)                       # below 2^-126: the subnormal spacing 2^-149
+    unit = Fraction(2) ** (e - 23)
+    q, r = divmod(a, unit)
+    q = int(q)
+    r = r / unit
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    v = Fraction(q) * unit
+    if v >= Fraction(2) ** 128:
+        return np.float32(sign * np.inf)
+    return np.float32(sign * float(v))       # q * unit has at most 25 bits: exact in double
+
+
+def fraction_emul_f32(alpha, A, B, beta, C, s, b, trim=False):
+    """The FP32 emulated GEMM in exact rationals: the digits and the integer X
+    of fraction_emul, then (float)X, ldexpf, the float alpha product and the
+    fused beta term, each rounded by fraction_to_f32."""
+    M, K = A.shape
+    N = B.shape[1]
+    e = [math.frexp(float(np.max(np.abs(A[i]))))[1] if np.any(A[i]) else 0 for i in range(M)]
+    f = [math.frexp(float(np.max(np.abs(B[:, j]))))[1] if np.any(B[:, j]) else 0
+         for j in range(N)]
+    dA = [[fraction_digits(float(A[i, k]), e[i], s, b) for k in range(K)] for i in range(M)]
+    dB = [[fraction_digits(float(B[k, j]), f[j], s, b) for k in range(K)] for j in range(N)]
+    out = np.empty((M, N), dtype=np.float32)
+    for i in range(M):
+        for j in range(N):
+            X = 0
+            for p in range(1, s + 1):
+                for q in range(1, s + 2 - p):
+                    if trim and p + q == s + 1 and min(p, q) > 1:
+                        continue
+                    X += sum(dA[i][k][p - 1] * dB[j][k][q - 1] for k in range(K)) \
+                        * 2 ** ((s + 1 - p - q) * b)
+            v = fraction_to_f32(Fraction(X))
+            w = fraction_to_f32(Fraction(float(v)) * Fraction(2) ** (e[i] + f[j] - (s + 1) * b))
+            o = fraction_to_f32(Fraction(float(np.float32(alpha))) * Fraction(float(w)))
+            if beta != 0.0:
+                o = fraction_to_f32(Fraction(float(np.float32(beta))) * Fraction(float(C[i, j]))
+                                    + Fraction(float(o)))
+            out[i, j] = o
+    return out
+
+
+def test_fraction_to_f32_matches_numpy_on_doubles():
+    """The rounding helper against numpy's double -> float32 cast (one rounding
+    when the source is a double), ties and subnormals included."""
+    vals = [1.0, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, -(1.0 + 2.0 ** -23 + 2.0 ** -24),
+            2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -150, 2.0 ** -127 + 2.0 ** -150, 3.4e38, 3.5e38]
+    rng = np.random.default_rng(5)
+    vals += list(rng.standard_normal(200) * 2.0 ** rng.integers(-140, 120, 200))
+    with np.errstate(over="ignore"):
+        for v in vals:
+            assert fraction_to_f32(Fraction(v)) == np.float32(v) or (
+                np.isinf(np.float32(v)) and np.isinf(fraction_to_f32(Fraction(v)))), v
+
+
+@pytest.mark.parametrize("s,b,trim,phi", [(2, 8, 0, 0), (3, 8, 0, 0), (3, 8, 0, 8), (3, 8, 1, 4),
+                                          (4, 8, 0, 16), (3, 7, 0, 0), (4, 7, 0, 8)])
+def test_emul_gemm_f32_bit_exact_against_rationals(orc, s, b, trim, phi):
+    M, N, K = 4, 3, 9
+    A, B, C = inputs.gemm_operands(190 + s + phi, M, N, K, kind="scaled", phi=phi)
+    A, B, C = (x.astype(np.float32) for x in (A, B, C))
+    D, rc = orc.emul_gemm_f32(1.5, A, B, 0.5, C, s, b=b, trim=trim)
+    assert rc == 0 and D.dtype == np.float32
+    ref = fraction_emul_f32(1.5, A, B, 0.5, C, s, b, trim)
+    assert np.array_equal(D, ref)
+
+
+@pytest.mark.parametrize("s,b", [(3, 8), (4, 7)])
+def test_emul_gemm_f32_within_one_rounding_of_exact(orc, s, b):
+    """With s b >= 24 + the exponent spread, the digits hold the FP32 inputs
+    exactly and the kept pairs lose at most K 2^(-s b) of the scale, so the
+    result is the exact product rounded once, up to that tiny term."""
+    M, N, K = 6, 5, 40
+    A, B, _ = inputs.gemm_operands(210 + s, M, N, K, kind="scaled", phi=0, with_c=False)
+    A, B = A.astype(np.float32), B.astype(np.float32)
+    D, _ = orc.emul_gemm_f32(1.0, A, B, 0.0, None, s, b=b)
+    E = exact_gemm(1.0, A.astype(np.float64), B.astype(np.float64), 0.0, None)
+    e, _ = orc.row_exponents(A.astype(np.float64))
+    f, _ = orc.col_exponents(B.astype(np.float64))
+    for i in range(M):
+        for j in range(N):
+            scale = Fraction(2) ** int(e[i] + f[j])
+            tail = scale * K * Fraction(2) ** (-s * b) * (1 + Fraction(26, 100) * s)
+            assert abs(Fraction(float(D[i, j])) - E[i][j]) <= \
+                Fraction(U32 / 2) * abs(Fraction(float(D[i, j]))) + tail, (i, j)
+
+
+def test_emul_gemm_f32_integer_and_special_cases(orc):
+    Ai, Bi, _ = inputs.gemm_operands(81, 12, 10, 64, kind="int", with_c=False)
+    ref = (Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float32)
+    for s in (2, 3, 4):
+        D, rc = orc.emul_gemm_f32(1.0, Ai, Bi, 0.0, None, s)
+        assert rc == 0 and np.array_equal(D, ref)
+    A, B, C = (x.astype(np.float32) for x in inputs.gemm_operands(83, 4, 3, 5))
+    D, rc = orc.emul_gemm_f32(0.0, np.full_like(A, np.nan), B, 0.5, C, 3)
+    assert rc == 0 and np.array_equal(D, np.float32(0.5) * C)
+    D, rc = orc.emul_gemm_f32(1.0, A, B, 0.0, np.full_like(C, np.nan), 3)
+    assert rc == 0 and not np.isnan(D).any()
+    A2 = A.copy()
+    A2[1, 1] = np.inf
+    assert orc.emul_gemm_f32(1.0, A2, B, 0.0, None, 3)[1] == 2
