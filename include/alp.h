@@ -170,6 +170,37 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
                               double alpha, double beta, double* C, int64_t ldc, void* stream);
 
 /*
+ * Emulated FP32 GEMM (the paper evaluates single precision throughout,
+ * Sect. 3): C = alpha*A*B + beta*C with float operands, the same digit split,
+ * slice products and exact integer sums as alp_gemm_f64_emul, and the result
+ * rounded once to float:  X = sum_t S^t 2^(b(nslices+1-t)) (exact, |X| < 2^63),
+ * C = (float)alpha * ldexpf(RN_float(X), e_i + f_j - b(nslices+1))
+ * (+ fmaf(beta, C, .) when beta != 0).  nslices in 2..4 (nslices * b <= 32);
+ * three slices of 8-bit digits (six products) give results within about
+ * 0.05 float ulps of |A||B| of the correctly rounded product.  Same
+ * workspace layout, kinds, K limits and errors as alp_gemm_f64_emul; floats
+ * 4-byte aligned.
+ */
+alp_status alp_gemm_f32_emul(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                             int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                             int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,
+                             size_t workspace_bytes, void* stream);
+size_t alp_gemm_f32_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind);
+/* Its stages: the exponent scan and split of alp_emul_exponents and
+ * alp_emul_split for float operands (values converted exactly to double), and
+ * the FP32 recombination of alp_emul_slice_products' group sums. */
+alp_status alp_emul_exponents_f32(int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                                  int trans, int32_t* exps, void* stream);
+alp_status alp_emul_split_f32(int64_t R, int64_t K, const float* X, int64_t ldx, int trans,
+                              const int32_t* exps, int nslices, alp_slice_kind kind,
+                              void* out_bf16, int64_t kpad, void* stream);
+alp_status alp_emul_recombine_f32(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
+                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const int32_t* f, float alpha, float beta, float* C,
+                                  int64_t ldc, void* stream);
+
+/*
  * Batched variable-size native GEMM: `count` independent problems
  *   C_p = alpha_p * A_p * B_p + beta_p * C_p,  p = 0..count-1,
  * all arrays (sizes, scalars, pointers, leading dims) in DEVICE memory, plus

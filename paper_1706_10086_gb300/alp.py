@@ -59,6 +59,7 @@ _lock = threading.Lock()
 _lib = None
 
 _i64, _f64, _vp, _int = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+_f32 = ctypes.c_float
 _SIGS = {
     "alp_status_string": ([_int], ctypes.c_char_p),
     "alp_gemm_f64": ([_i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp, _i64,
@@ -73,6 +74,13 @@ _SIGS = {
     "alp_emul_recombine": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64,
                             _vp],
                            _int),
+    "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
+                           _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_emul_exponents_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
+    "alp_emul_split_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _i64, _vp], _int),
+    "alp_emul_recombine_f32": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f32, _f32, _vp, _i64,
+                                _vp], _int),
     "alp_gemm_batched_varsize": ([_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_batched_workspace": ([_i64, _vp, _vp, _vp], ctypes.c_size_t),
@@ -215,6 +223,38 @@ def alp_emul_recombine(M, N, nslices, kind, G, ldg, e, f, alpha, beta, C, ldc, s
     st = lib().alp_emul_recombine(M, N, int(nslices), int(kind), _p(G), ldg, _p(e), _p(f),
                                   float(alpha), float(beta), _p(C), ldc, _s(stream))
     return _check(st, "alp_emul_recombine", raise_on_error)
+
+
+def alp_gemm_f32_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,
+                      kind=ALP_SLICE_BF16_B8, workspace=None, workspace_bytes=0, stream=None,
+                      raise_on_error=True):
+    st = lib().alp_gemm_f32_emul(M, N, K, float(alpha), _p(A), lda, _p(B), ldb, float(beta),
+                                 _p(C), ldc, int(nslices), int(kind), _p(workspace),
+                                 int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f32_emul", raise_on_error)
+
+
+def alp_gemm_f32_emul_workspace(M, N, K, nslices, kind=ALP_SLICE_BF16_B8):
+    return int(lib().alp_gemm_f32_emul_workspace(M, N, K, int(nslices), int(kind)))
+
+
+def alp_emul_exponents_f32(rows, cols, X, ldx, trans, exps, stream=None, raise_on_error=True):
+    st = lib().alp_emul_exponents_f32(rows, cols, _p(X), ldx, int(trans), _p(exps), _s(stream))
+    return _check(st, "alp_emul_exponents_f32", raise_on_error)
+
+
+def alp_emul_split_f32(R, K, X, ldx, trans, exps, nslices, kind, out, kpad, stream=None,
+                       raise_on_error=True):
+    st = lib().alp_emul_split_f32(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices),
+                                  int(kind), _p(out), kpad, _s(stream))
+    return _check(st, "alp_emul_split_f32", raise_on_error)
+
+
+def alp_emul_recombine_f32(M, N, nslices, kind, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
+                           raise_on_error=True):
+    st = lib().alp_emul_recombine_f32(M, N, int(nslices), int(kind), _p(G), ldg, _p(e), _p(f),
+                                      float(alpha), float(beta), _p(C), ldc, _s(stream))
+    return _check(st, "alp_emul_recombine_f32", raise_on_error)
 
 
 def alp_gemm_batched_varsize(count, dM, dN, dK, dalpha, dA, dlda, dB, dldb, dbeta, dC, dldc,

@@ -41,17 +41,25 @@ __device__ __forceinline__ int frexp_exponent_of_bits(uint64_t mb) {
     return ex - 1022;
 }
 
-// One warp per row of a row-major R x K matrix.
-__global__ void scan_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K, int64_t ldx,
+// |x| as the bits of a double (FP32 operands convert exactly, so frexp and
+// the digits are the same as for the double of equal value).
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+    return (uint64_t)__double_as_longlong(x) & kAbsMask;
+}
+__device__ __forceinline__ uint64_t abs_bits(float x) { return abs_bits((double)x); }
+
+// One warp per row of a row-major R x K matrix (T = double or float).
+template <typename T>
+__global__ void scan_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K, int64_t ldx,
                                  int32_t* __restrict__ e, int* err) {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= R) return;
-    const uint64_t* p = reinterpret_cast<const uint64_t*>(X + row * ldx);
+    const T* p = X + row * ldx;
     uint64_t mx = 0;
     bool bad = false;
     for (int64_t k = lane; k < K; k += 32) {
-        const uint64_t v = __ldg(p + k) & kAbsMask;
+        const uint64_t v = abs_bits(__ldg(p + k));
         if ((v >> 52) == 0x7FF) bad = true;
         else mx = v > mx ? v : mx;
     }
@@ -71,7 +79,8 @@ __global__ void scan_rows_kernel(const double* __restrict__ X, int64_t R, int64_
 constexpr int kColChunk = 256;
 constexpr int32_t kNoExp = (int32_t)0x80808080;
 
-__global__ void scan_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N, int64_t ldx,
+template <typename T>
+__global__ void scan_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N, int64_t ldx,
                                  int32_t* __restrict__ f, int* err) {
     __shared__ uint64_t red[8][32];
     const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
@@ -80,9 +89,8 @@ __global__ void scan_cols_kernel(const double* __restrict__ X, int64_t K, int64_
     uint64_t mx = 0;
     bool bad = false;
     if (j < N) {
-        const uint64_t* p = reinterpret_cast<const uint64_t*>(X);
         for (int64_t k = k0 + threadIdx.y; k < k1; k += 8) {
-            const uint64_t v = __ldg(p + k * ldx + j) & kAbsMask;
+            const uint64_t v = abs_bits(__ldg(X + k * ldx + j));
             if ((v >> 52) == 0x7FF) bad = true;
             else mx = v > mx ? v : mx;
         }
@@ -164,8 +172,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
 
 // A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
 // thread handles two consecutive k.
-template <int S, int B>
-__global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64_t K,
+template <typename T, int S, int B>
+__global__ void split_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K,
                                   int64_t ldx, const int32_t* __restrict__ e,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
     const int64_t half = kpad >> 1;
@@ -177,8 +185,8 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
         const int64_t k = (idx - r * half) * 2;
         const int er = e[r];
         int d0[S], d1[S];
-        split_digits<S, B>(k < K ? __ldg(X + r * ldx + k) : 0.0, er, d0);
-        split_digits<S, B>(k + 1 < K ? __ldg(X + r * ldx + k + 1) : 0.0, er, d1);
+        split_digits<S, B>(k < K ? (double)__ldg(X + r * ldx + k) : 0.0, er, d0);
+        split_digits<S, B>(k + 1 < K ? (double)__ldg(X + r * ldx + k + 1) : 0.0, er, d1);
         uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
 #pragma unroll
         for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
@@ -189,8 +197,8 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t R, int64
 // blockIdx.y (grid stride, no division per element), two 16-byte loads of A
 // when its row is 16-byte aligned, one 8-byte store per digit plane.  Needs
 // out 8-byte aligned (the launch checks).
-template <int S, int B>
-__global__ void __launch_bounds__(256) split_rows4_kernel(const double* __restrict__ X, int64_t R,
+template <typename T, int S, int B>
+__global__ void __launch_bounds__(256) split_rows4_kernel(const T* __restrict__ X, int64_t R,
                                                           int64_t K, int64_t ldx,
                                                           const int32_t* __restrict__ e,
                                                           __nv_bfloat16* __restrict__ out,
@@ -198,21 +206,29 @@ __global__ void __launch_bounds__(256) split_rows4_kernel(const double* __restri
     const int64_t plane = R * kpad;
     for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
         const int er = e[r];
-        const double* xr = X + r * ldx;
+        const T* xr = X + r * ldx;
         const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
         for (int64_t k = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); k < kpad;
              k += 4 * (int64_t)gridDim.x * blockDim.x) {
             double a[4];
             if (xvec && k + 3 < K) {
-                const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
-                const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
-                a[0] = p0.x;
-                a[1] = p0.y;
-                a[2] = p1.x;
-                a[3] = p1.y;
+                if constexpr (sizeof(T) == 8) {
+                    const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
+                    const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
+                    a[0] = p0.x;
+                    a[1] = p0.y;
+                    a[2] = p1.x;
+                    a[3] = p1.y;
+                } else {
+                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(xr + k));
+                    a[0] = p0.x;
+                    a[1] = p0.y;
+                    a[2] = p0.z;
+                    a[3] = p0.w;
+                }
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? __ldg(xr + k + u) : 0.0;
+                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? (double)__ldg(xr + k + u) : 0.0;
             }
             int d0[S], d1[S], d2[S], d3[S];
             split_digits<S, B>(a[0], er, d0);
@@ -229,8 +245,8 @@ __global__ void __launch_bounds__(256) split_rows4_kernel(const double* __restri
 
 // B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
 // shared memory so that reads run along j and writes along k.
-template <int S, int B>
-__global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64_t N,
+template <typename T, int S, int B>
+__global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
                                   int64_t ldx, const int32_t* __restrict__ f,
                                   __nv_bfloat16* __restrict__ out, int64_t kpad) {
     __shared__ double t[32][65];
@@ -239,7 +255,7 @@ __global__ void split_cols_kernel(const double* __restrict__ X, int64_t K, int64
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int64_t k = k0 + ty + 8 * r, j = j0 + tx;
-        t[tx][ty + 8 * r] = (k < K && j < N) ? __ldg(X + k * ldx + j) : 0.0;
+        t[tx][ty + 8 * r] = (k < K && j < N) ? (double)__ldg(X + k * ldx + j) : 0.0;
     }
     __syncthreads();
     const int64_t plane = N * kpad;
@@ -492,26 +508,27 @@ static int grid_for(int64_t work, int threads) {
     return (int)(b < 1 ? 1 : b);
 }
 
-alp_status emul_exponents(int64_t rows, int64_t cols, const double* X, int64_t ldx, int trans,
+template <typename T>
+alp_status emul_exponents(int64_t rows, int64_t cols, const T* X, int64_t ldx, int trans,
                           int32_t* exps, cudaStream_t st) {
     int* err = device_error_word();
     if (!trans) {
         const int wpb = 8;
-        scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), 32 * wpb, 0, st>>>(X, rows, cols,
-                                                                                  ldx, exps, err);
+        scan_rows_kernel<T><<<(unsigned)((rows + wpb - 1) / wpb), 32 * wpb, 0, st>>>(
+            X, rows, cols, ldx, exps, err);
         return cuda_status(cudaGetLastError());
     }
     // trans: X is cols x rows row-major (K x N); exponents per column (rows = N)
     const int64_t N = rows, K = cols;
     if (cudaMemsetAsync(exps, 0x80, (size_t)N * 4, st) != cudaSuccess) return ALP_ERR_CUDA;
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + kColChunk - 1) / kColChunk));
-    if (K > 0) scan_cols_kernel<<<grid, dim3(32, 8), 0, st>>>(X, K, N, ldx, exps, err);
+    if (K > 0) scan_cols_kernel<T><<<grid, dim3(32, 8), 0, st>>>(X, K, N, ldx, exps, err);
     zero_empty_columns_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, exps);
     return cuda_status(cudaGetLastError());
 }
 
-template <int B>
-static alp_status emul_split_b(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+template <typename T, int B>
+static alp_status emul_split_b(int64_t R, int64_t K, const T* X, int64_t ldx, int trans,
                                const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
                                cudaStream_t st) {
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
@@ -522,12 +539,12 @@ static alp_status emul_split_b(int64_t R, int64_t K, const double* X, int64_t ld
 #define ALP_SPLIT_CASE(x)                                                                        \
     case x:                                                                                      \
         if (!trans && vec)                                                                       \
-            split_rows4_kernel<x, B><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps, out, kpad);      \
+            split_rows4_kernel<T, x, B><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps, out, kpad);   \
         else if (!trans)                                                                         \
-            split_rows_kernel<x, B><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(              \
+            split_rows_kernel<T, x, B><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(           \
                 X, R, K, ldx, exps, out, kpad);                                                  \
         else                                                                                     \
-            split_cols_kernel<x, B><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)),     \
+            split_cols_kernel<T, x, B><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)),  \
                                       256, 0, st>>>(X, K, R, ldx, exps, out, kpad);              \
         break;
     switch (s) {
@@ -539,12 +556,120 @@ static alp_status emul_split_b(int64_t R, int64_t K, const double* X, int64_t ld
     return cuda_status(cudaGetLastError());
 }
 
-alp_status emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
+template <typename T>
+alp_status emul_split(int64_t R, int64_t K, const T* X, int64_t ldx, int trans,
                       const int32_t* exps, int s, __nv_bfloat16* out, int64_t kpad,
                       cudaStream_t st, int b) {
-    if (b == 7) return emul_split_b<7>(R, K, X, ldx, trans, exps, s, out, kpad, st);
-    if (b == 8) return emul_split_b<8>(R, K, X, ldx, trans, exps, s, out, kpad, st);
+    if (b == 7) return emul_split_b<T, 7>(R, K, X, ldx, trans, exps, s, out, kpad, st);
+    if (b == 8) return emul_split_b<T, 8>(R, K, X, ldx, trans, exps, s, out, kpad, st);
     return ALP_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 results (alp_gemm_f32_emul): with s b <= 32 the exact sum X fits in 64
+// bits; it is rounded once to float (cvt.rn.f32.s64), scaled by 2^E (by the
+// exponent field while the result stays normal, else by ldexpf, which rounds
+// a subnormal result a second time, as the definition does), then alpha and
+// the fused beta term in float.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float i64_scaled_to_float_rn(int64_t x, int E) {
+    float v;
+    asm("cvt.rn.f32.s64 %0, %1;" : "=f"(v) : "l"(x));
+    if (v == 0.0f) return v;
+    const uint32_t bits = __float_as_uint(v);
+    const int ne = (int)((bits >> 23) & 0xFF) + E;
+    if (ne >= 1 && ne <= 254) return __uint_as_float((bits & 0x807FFFFFu) | ((uint32_t)ne << 23));
+    return ldexpf(v, E);
+}
+
+template <int S, int B>
+__global__ void __launch_bounds__(256) recombine_f32_kernel(
+    const int32_t* __restrict__ G, int64_t gplane, int64_t ldg, const int32_t* __restrict__ e,
+    const int32_t* __restrict__ f, int64_t M, int64_t N, float alpha, float beta,
+    float* __restrict__ C, int64_t ldc, bool gvec) {
+    const int shift0 = (S + 1) * B;
+    for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
+        const int ei = e[i] - shift0;
+        const int32_t* gi = G + i * ldg;
+        float* ci = C + i * ldc;
+        const bool cvec = (reinterpret_cast<uintptr_t>(ci) & 15) == 0;
+        for (int64_t j = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N;
+             j += 4 * (int64_t)gridDim.x * blockDim.x) {
+            int4 v[S];
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                const int32_t* g = gi + (int64_t)t * gplane + j;
+                if (gvec) v[t] = __ldg(reinterpret_cast<const int4*>(g));
+                else v[t] = make_int4(__ldg(g), __ldg(g + 1), __ldg(g + 2), __ldg(g + 3));
+            }
+            float out[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j + u >= N) break;
+                int64_t X = 0;
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+                    const int32_t c = u == 0 ? v[t].x : u == 1 ? v[t].y : u == 2 ? v[t].z : v[t].w;
+                    X = X * (1ll << B) + c;
+                }
+                const float w = i64_scaled_to_float_rn(X, ei + __ldg(f + j + u));
+                float o = (alpha == 1.0f) ? w : (alpha == -1.0f) ? -w : __fmul_rn(alpha, w);
+                if (beta != 0.0f) o = __fmaf_rn(beta, ci[j + u], o);
+                out[u] = o;
+            }
+            if (cvec && j + 3 < N) {
+                *reinterpret_cast<float4*>(ci + j) = make_float4(out[0], out[1], out[2], out[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j + u < N) ci[j + u] = out[u];
+            }
+        }
+    }
+}
+
+template <int B>
+static alp_status launch_recombine_f32_b(int s, dim3 grid, cudaStream_t st, const int32_t* G,
+                                         int64_t gplane, int64_t ldg, const int32_t* e,
+                                         const int32_t* f, int64_t M, int64_t N, float alpha,
+                                         float beta, float* C, int64_t ldc) {
+    const bool gvec = (reinterpret_cast<uintptr_t>(G) & 15) == 0 && gplane % 4 == 0 && ldg % 4 == 0;
+    grid.x = (unsigned)((grid.x + 1) / 2);   // four columns per thread
+#define ALP_RECOMBINE_F32_CASE(x)                                                                 \
+    case x:                                                                                      \
+        recombine_f32_kernel<x, B><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta,  \
+                                                         C, ldc, gvec);                          \
+        break;
+    switch (s) {
+        ALP_RECOMBINE_F32_CASE(1) ALP_RECOMBINE_F32_CASE(2) ALP_RECOMBINE_F32_CASE(3)
+        ALP_RECOMBINE_F32_CASE(4)
+        default: return ALP_ERR_INVALID_ARG;
+    }
+#undef ALP_RECOMBINE_F32_CASE
+    return cuda_status(cudaGetLastError());
+}
+
+static alp_status launch_recombine_f32(int s, int b, dim3 grid, cudaStream_t st, const int32_t* G,
+                                       int64_t gplane, int64_t ldg, const int32_t* e,
+                                       const int32_t* f, int64_t M, int64_t N, float alpha,
+                                       float beta, float* C, int64_t ldc) {
+    if (b == 7)
+        return launch_recombine_f32_b<7>(s, grid, st, G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc);
+    if (b == 8)
+        return launch_recombine_f32_b<8>(s, grid, st, G, gplane, ldg, e, f, M, N, alpha, beta, C, ldc);
+    return ALP_ERR_INVALID_ARG;
+}
+
+// C = beta C for FP32 (alpha == 0 or K == 0): beta == 0 writes zeros.
+__global__ void scale_f32_kernel(float* __restrict__ C, int64_t ldc, int64_t M, int64_t N,
+                                 float beta) {
+    const int64_t total = M * N;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / N, j = idx - i * N;
+        float* c = C + i * ldc + j;
+        *c = beta == 0.0f ? 0.0f : __fmul_rn(beta, *c);
+    }
 }
 
 }  // namespace alp
@@ -668,6 +793,106 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
         return st;
     return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
                             alpha, beta, C, ldc);
+}
+
+// ---- FP32 operands and results ----
+
+size_t alp_gemm_f32_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                   alp_slice_kind kind) {
+    EmulScheme sc;
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 2 ||
+        nslices > emul_max_slices_f32(sc.b))
+        return 0;
+    return emul_layout(M, N, K, nslices).bytes;
+}
+
+alp_status alp_emul_exponents_f32(int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                                  int trans, int32_t* exps, void* stream) {
+    if (rows < 0 || cols < 0 || !exps || (rows > 0 && cols > 0 && !X)) return ALP_ERR_INVALID_ARG;
+    if (rows == 0) return ALP_OK;
+    if (!trans && ldx < cols) return ALP_ERR_INVALID_ARG;
+    if (trans && ldx < rows) return ALP_ERR_INVALID_ARG;
+    return emul_exponents(rows, cols, X, ldx, trans, exps, reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_emul_split_f32(int64_t R, int64_t K, const float* X, int64_t ldx, int trans,
+                              const int32_t* exps, int nslices, alp_slice_kind kind,
+                              void* out_bf16, int64_t kpad, void* stream) {
+    EmulScheme sc;
+    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > emul_max_slices_f32(sc.b) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
+        (R > 0 && K > 0 && !X))
+        return ALP_ERR_INVALID_ARG;
+    if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
+    if (trans && ldx < R) return ALP_ERR_INVALID_ARG;
+    if (R == 0 || kpad == 0) return ALP_OK;
+    return emul_split(R, K, X, ldx, trans, exps, nslices,
+                      reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
+                      reinterpret_cast<cudaStream_t>(stream), sc.b);
+}
+
+alp_status alp_emul_recombine_f32(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
+                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const int32_t* f, float alpha, float beta, float* C,
+                                  int64_t ldc, void* stream) {
+    EmulScheme sc;
+    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > emul_max_slices_f32(sc.b) || ldg < N || ldc < N)
+        return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
+    return launch_recombine_f32(nslices, sc.b, recombine_grid(M, N),
+                                reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M,
+                                N, alpha, beta, C, ldc);
+}
+
+alp_status alp_gemm_f32_emul(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                             int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                             int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,
+                             size_t workspace_bytes, void* stream) {
+    if (M < 0 || N < 0 || K < 0) return ALP_ERR_INVALID_ARG;
+    if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
+    EmulScheme sc;
+    if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
+    const int b = sc.b;
+    if (nslices < 2 || nslices > emul_max_slices_f32(b)) return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (lda < K || ldb < N || ldc < N || !C) return ALP_ERR_INVALID_ARG;
+    const bool reads_ab = alpha != 0.0f && K > 0;
+    if (reads_ab && (!A || !B)) return ALP_ERR_INVALID_ARG;
+    if (((uintptr_t)C & 3) || (reads_ab && (((uintptr_t)A & 3) || ((uintptr_t)B & 3))))
+        return ALP_ERR_INVALID_ARG;   // floats must be naturally aligned
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!reads_ab) {
+        int64_t blocks = (M * N + 255) / 256;
+        const int64_t cap = (int64_t)device_sm_count() * 8;
+        blocks = blocks > cap ? cap : blocks < 1 ? 1 : blocks;
+        scale_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(C, ldc, M, N, beta);
+        return cuda_status(cudaGetLastError());
+    }
+    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    const EmulLayout L = emul_layout(M, N, K, nslices);
+    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
+        return ALP_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
+    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
+    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
+    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
+    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
+    alp_status st;
+    if ((st = emul_exponents(M, K, A, lda, 0, e, s)) != ALP_OK) return st;
+    if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
+    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
+    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
+    alp_config cfg;
+    const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
+    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
+                              have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
+                              sc.trim)) != ALP_OK)
+        return st;
+    return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M,
+                                N, alpha, beta, C, ldc);
 }
 
 }  // extern "C"

@@ -16,6 +16,8 @@ constexpr int kEmulBK = 64;        // K elements per pipeline stage (128 bytes o
 // Most slices per digit width: the split's 62-bit fixed point stays exact
 // while (s - 1) * b + 2 <= 62 - b.
 inline int emul_max_slices(int b) { return b == 8 ? 7 : 8; }
+// FP32 results: s b <= 32 keeps the exact sum in 64 bits.
+inline int emul_max_slices_f32(int b) { return 32 / b; }
 // Largest K per call: the int32 group sums |S^t| <= K * 2^(2b-2) * (t + 1),
 // t <= s + 1, stay below 2^31 (b = 7: K <= 32768; b = 8: K <= 14336).
 inline int64_t emul_max_k(int b) { return b == 8 ? 14336 : 32768; }
