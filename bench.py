@@ -70,12 +70,13 @@ def parse_args():
     ap.add_argument("--no-native", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", choices=("emul8192", "batched", "native_scan"),
+    ap.add_argument("--workload", choices=("emul8192", "batched", "native_scan", "sgemm8192"),
                     default="emul8192",
                     help="emul8192 (default, the headline), batched (4096 variable-size "
-                         "problems, persistent graph launch vs a loop of launches) or "
+                         "problems, persistent graph launch vs a loop of launches), "
                          "native_scan (native FP64 GEMM at N = 1024..16384, default and "
-                         "autotuned config)")
+                         "autotuned config) or sgemm8192 (emulated FP32 GEMM, 3 slices of 8-bit "
+                         "digits, against the vendor FP32 GEMM)")
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true",
                     help="batched: keep the default class tiles instead of autotuning them")
@@ -664,6 +665,131 @@ def run_native_scan(args):
                       "rows": rows}), flush=True)
 
 
+def run_sgemm(args):
+    """Emulated FP32 GEMM, M = N = K = 8192, u in [-1,1) as float, alpha = 1,
+    beta = 0: one step = the scans, splits, tensor-core slice products and FP32
+    recombination (the kernels alp_gemm_f32_emul launches, stage by stage).
+    Beside it, the vendor library's FP32 GEMM (TF32 off) on the same operands,
+    and both results' errors against the emulated FP64 product (8 slices of
+    7-bit digits) rounded nowhere (compared in double)."""
+    import torch
+
+    from paper_1706_10086_gb300 import alp
+    n = args.n
+    s = 3
+    kind = alp.ALP_SLICE_BF16_B8
+    M = N = K = n
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    A64, B64 = make_inputs(torch, n, 0, 1706 + 4, dev)
+    A, B = A64.float(), B64.float()
+    A64, B64 = A.double(), B.double()          # the exact values of the float operands
+    C = torch.empty(n, n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    kpad = (K + 63) // 64 * 64
+    ldg = (N + 255) // 256 * 256
+    da = torch.empty(s * M * kpad, dtype=torch.bfloat16, device=dev)
+    db = torch.empty(s * N * kpad, dtype=torch.bfloat16, device=dev)
+    G = torch.empty(s * M * ldg, dtype=torch.int32, device=dev)
+    e = torch.empty(M, dtype=torch.int32, device=dev)
+    f = torch.empty(N, dtype=torch.int32, device=dev)
+
+    def step(ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        rec(0)
+        alp.alp_emul_exponents_f32(M, K, A, K, 0, e, stream)
+        alp.alp_emul_exponents_f32(N, K, B, N, 1, f, stream)
+        alp.alp_emul_split_f32(M, K, A, K, 0, e, s, kind, da, kpad, stream)
+        alp.alp_emul_split_f32(N, K, B, N, 1, f, s, kind, db, kpad, stream)
+        rec(1)
+        alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
+        rec(2)
+        alp.alp_emul_recombine_f32(M, N, s, kind, G, ldg, e, f, 1.0, 0.0, C, N, stream)
+        rec(3)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error(stream) == alp.ALP_OK
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(ev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps))
+    flops = 2.0 * M * N * K
+    pairs = s * (s + 1) // 2
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = pairs * flops / (kern_ms * 1e-3) / 1e12
+    # the vendor FP32 GEMM on the same float operands (a comparison, not this library)
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Cv = A @ B
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        Cv = A @ B
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.backends.cuda.matmul.allow_tf32 = old
+    vend_ms = e0.elapsed_time(e1) / 3
+    # accuracy over the whole result against the FP64 emulated product of the
+    # same (float) values, relative to |A||B| from the native FP64 kernel
+    Cref = torch.empty(n, n, dtype=torch.float64, device=dev)
+    ws8 = alp.alp_gemm_f64_emul_workspace(M, N, K, 8, alp.ALP_SLICE_BF16)
+    work8 = torch.empty(ws8, dtype=torch.uint8, device=dev)
+    alp.alp_gemm_f64_emul(M, N, K, 1.0, A64, K, B64, N, 0.0, Cref, N, 8, alp.ALP_SLICE_BF16,
+                          work8, ws8, stream)
+    del work8
+    absAB = torch.empty_like(Cref)
+    alp.alp_gemm_f64(M, N, K, 1.0, A64.abs(), K, B64.abs(), N, 0.0, absAB, N, stream=stream)
+    torch.cuda.synchronize()
+    u = 2.0 ** -24
+
+    def errs(X):
+        d = (X.double() - Cref).abs()
+        return {"max_componentwise_u32": float((d / absAB).max()) / u,
+                "normwise": float(torch.linalg.norm(d) / torch.linalg.norm(Cref))}
+    out = {"metric": "FP32-accurate GEMM TFLOP/s (emulated on BF16 tensor cores) at N=8192",
+           "value": round(flops * args.steps / (total_ms * 1e-3) / 1e12, 3), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic (seeded torch generator on the GPU, u~U[-1,1) as float)",
+           "config": {"workload": f"emulated_sgemm_{n}_bf16_b8x{s}slices", "M": M, "N": N,
+                      "K": K, "nslices": s, "slice_kind": "bf16_b8", "digit_pairs": pairs,
+                      "l2": "inputs 0.5 GB > 129 MB L2; no flush"},
+           "stage_ms_median": {
+               "scans_and_splits": round(statistics.median(ev[i][0].elapsed_time(ev[i][1])
+                                                           for i in range(args.steps)), 4),
+               "slice_products": round(statistics.median(ev[i][1].elapsed_time(ev[i][2])
+                                                         for i in range(args.steps)), 4),
+               "recombine": round(statistics.median(ev[i][2].elapsed_time(ev[i][3])
+                                                    for i in range(args.steps)), 4)},
+           "roofline": {"bound": "tensor", "kernel": "emul_gemm_pair_kernel (tcgen05 bf16)",
+                        "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                        "frac": round(achieved / peak, 4),
+                        "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
+                        "algorithmic_flops_per_launch": pairs * flops,
+                        "kernel_ms": round(kern_ms, 3), "traffic": None},
+           "vendor_fp32": {"tflops": round(flops / (vend_ms * 1e-3) / 1e12, 3),
+                           "ms": round(vend_ms, 3), "note": "torch.matmul FP32, TF32 off"},
+           "accuracy": {"reference": "emulated FP64 product (8 slices of 7-bit digits)",
+                        "emulated_fp32": errs(C), "vendor_fp32": errs(Cv)},
+           "gpu_launches": 7 * args.steps, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -672,6 +798,8 @@ def main():
         run_batched(args)
     elif args.workload == "native_scan":
         run_native_scan(args)
+    elif args.workload == "sgemm8192":
+        run_sgemm(args)
     else:
         run_alp(args)
 
