@@ -187,6 +187,22 @@ alp_status alp_gemm_f32_emul(int64_t M, int64_t N, int64_t K, float alpha, const
                              size_t workspace_bytes, void* stream);
 size_t alp_gemm_f32_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind);
+/* Transposed operands for the emulated GEMMs (BLAS op(X)): C = alpha op(A)
+ * op(B) + beta C, op(X) = X for trans 0 and X^T for trans 1.  op(A) is M x K:
+ * A is stored M x K (lda >= K) or K x M (lda >= M); op(B) is K x N: B is
+ * stored K x N (ldb >= N) or N x K (ldb >= K); all row-major.  Same results
+ * bit for bit as alp_gemm_f64_emul / alp_gemm_f32_emul on the transposed
+ * matrices; other trans values return ALP_ERR_INVALID_ARG. */
+alp_status alp_gemm_f64_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                double alpha, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double beta, double* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream);
+alp_status alp_gemm_f32_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                float alpha, const float* A, int64_t lda, const float* B,
+                                int64_t ldb, float beta, float* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream);
 /* Its stages: the exponent scan and split of alp_emul_exponents and
  * alp_emul_split for float operands (values converted exactly to double), and
  * the FP32 recombination of alp_emul_slice_products' group sums. */

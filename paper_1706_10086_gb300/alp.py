@@ -77,6 +77,10 @@ _SIGS = {
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
                            _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_gemm_f64_emul_ex": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
+                              _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f32_emul_ex": ([_int, _int, _i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp,
+                              _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_emul_exponents_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
     "alp_emul_split_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _i64, _vp], _int),
     "alp_emul_recombine_f32": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f32, _f32, _vp, _i64,
@@ -236,6 +240,24 @@ def alp_gemm_f32_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,
 
 def alp_gemm_f32_emul_workspace(M, N, K, nslices, kind=ALP_SLICE_BF16_B8):
     return int(lib().alp_gemm_f32_emul_workspace(M, N, K, int(nslices), int(kind)))
+
+
+def alp_gemm_f64_emul_ex(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                         nslices, kind=ALP_SLICE_BF16, workspace=None, workspace_bytes=0,
+                         stream=None, raise_on_error=True):
+    st = lib().alp_gemm_f64_emul_ex(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                                    _p(B), ldb, float(beta), _p(C), ldc, int(nslices), int(kind),
+                                    _p(workspace), int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f64_emul_ex", raise_on_error)
+
+
+def alp_gemm_f32_emul_ex(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                         nslices, kind=ALP_SLICE_BF16_B8, workspace=None, workspace_bytes=0,
+                         stream=None, raise_on_error=True):
+    st = lib().alp_gemm_f32_emul_ex(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                                    _p(B), ldb, float(beta), _p(C), ldc, int(nslices), int(kind),
+                                    _p(workspace), int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f32_emul_ex", raise_on_error)
 
 
 def alp_emul_exponents_f32(rows, cols, X, ldx, trans, exps, stream=None, raise_on_error=True):

@@ -672,6 +672,74 @@ __global__ void scale_f32_kernel(float* __restrict__ C, int64_t ldc, int64_t M, 
     }
 }
 
+// The emulated GEMM for double or float operands: C = alpha op(A) op(B) +
+// beta C with op(X) = X (trans 0) or X^T (trans 1).  A transposed A is split
+// by columns of its storage and a transposed B by rows, which is the K-major
+// digit layout the tensor-core stage reads, so transposes cost nothing.
+template <typename T>
+alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
+                          int64_t lda, const T* B, int64_t ldb, T beta, T* C, int64_t ldc,
+                          int nslices, alp_slice_kind kind, void* workspace,
+                          size_t workspace_bytes, cudaStream_t s) {
+    constexpr bool kF32 = sizeof(T) == 4;
+    if (M < 0 || N < 0 || K < 0 || (ta != 0 && ta != 1) || (tb != 0 && tb != 1))
+        return ALP_ERR_INVALID_ARG;
+    if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
+    EmulScheme sc;
+    if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
+    const int b = sc.b;
+    const int smin = kF32 ? 2 : kMinSlices;
+    const int smax = kF32 ? emul_max_slices_f32(b) : emul_max_slices(b);
+    if (nslices < smin || nslices > smax) return ALP_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N || !C) return ALP_ERR_INVALID_ARG;
+    const bool reads_ab = alpha != T(0) && K > 0;
+    if (reads_ab && (!A || !B)) return ALP_ERR_INVALID_ARG;
+    if (((uintptr_t)C % sizeof(T)) ||
+        (reads_ab && (((uintptr_t)A % sizeof(T)) || ((uintptr_t)B % sizeof(T)))))
+        return ALP_ERR_INVALID_ARG;   // elements must be naturally aligned
+    if (!reads_ab) {
+        if constexpr (kF32) {
+            int64_t blocks = (M * N + 255) / 256;
+            const int64_t cap = (int64_t)device_sm_count() * 8;
+            blocks = blocks > cap ? cap : blocks < 1 ? 1 : blocks;
+            scale_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(C, ldc, M, N, beta);
+            return cuda_status(cudaGetLastError());
+        } else {
+            return native_scale(M, N, beta, C, ldc, s);
+        }
+    }
+    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    const EmulLayout L = emul_layout(M, N, K, nslices);
+    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
+        return ALP_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
+    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
+    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
+    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
+    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
+    // rows of op(A): rows of A, or columns of its K x M storage; columns of
+    // op(B): columns of B, or rows of its N x K storage
+    alp_status st;
+    if ((st = emul_exponents(M, K, A, lda, ta, e, s)) != ALP_OK) return st;
+    if ((st = emul_exponents(N, K, B, ldb, 1 - tb, f, s)) != ALP_OK) return st;
+    if ((st = emul_split(M, K, A, lda, ta, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
+    if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
+    alp_config cfg;
+    const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
+    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
+                              have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
+                              sc.trim)) != ALP_OK)
+        return st;
+    if constexpr (kF32)
+        return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e,
+                                    f, M, N, alpha, beta, C, ldc);
+    else
+        return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f,
+                                M, N, alpha, beta, C, ldc);
+}
+
 }  // namespace alp
 
 using namespace alp;
@@ -761,38 +829,19 @@ alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, cons
                              int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                              int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,
                              size_t workspace_bytes, void* stream) {
-    alp_status st = validate_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    if (st != ALP_OK) return st;
-    if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
-    EmulScheme sc;
-    if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
-    const int b = sc.b;
-    if (nslices < kMinSlices || nslices > emul_max_slices(b)) return ALP_ERR_INVALID_ARG;
-    if (M == 0 || N == 0) return ALP_OK;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (alpha == 0.0 || K == 0) return native_scale(M, N, beta, C, ldc, s);
-    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
-    const EmulLayout L = emul_layout(M, N, K, nslices);
-    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
-        return ALP_ERR_WORKSPACE;
-    char* ws = static_cast<char*>(workspace);
-    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
-    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
-    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
-    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
-    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
-    if ((st = emul_exponents(M, K, A, lda, 0, e, s)) != ALP_OK) return st;
-    if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
-    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
-    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
-    alp_config cfg;
-    const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
-    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
-                              have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
-                              sc.trim)) != ALP_OK)
-        return st;
-    return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M, N,
-                            alpha, beta, C, ldc);
+    return emul_gemm_impl<double>(0, 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,
+                                  kind, workspace, workspace_bytes,
+                                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_gemm_f64_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                double alpha, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double beta, double* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    return emul_gemm_impl<double>(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                  nslices, kind, workspace, workspace_bytes,
+                                  reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ---- FP32 operands and results ----
@@ -850,49 +899,19 @@ alp_status alp_gemm_f32_emul(int64_t M, int64_t N, int64_t K, float alpha, const
                              int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                              int64_t ldc, int nslices, alp_slice_kind kind, void* workspace,
                              size_t workspace_bytes, void* stream) {
-    if (M < 0 || N < 0 || K < 0) return ALP_ERR_INVALID_ARG;
-    if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
-    EmulScheme sc;
-    if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
-    const int b = sc.b;
-    if (nslices < 2 || nslices > emul_max_slices_f32(b)) return ALP_ERR_INVALID_ARG;
-    if (M == 0 || N == 0) return ALP_OK;
-    if (lda < K || ldb < N || ldc < N || !C) return ALP_ERR_INVALID_ARG;
-    const bool reads_ab = alpha != 0.0f && K > 0;
-    if (reads_ab && (!A || !B)) return ALP_ERR_INVALID_ARG;
-    if (((uintptr_t)C & 3) || (reads_ab && (((uintptr_t)A & 3) || ((uintptr_t)B & 3))))
-        return ALP_ERR_INVALID_ARG;   // floats must be naturally aligned
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (!reads_ab) {
-        int64_t blocks = (M * N + 255) / 256;
-        const int64_t cap = (int64_t)device_sm_count() * 8;
-        blocks = blocks > cap ? cap : blocks < 1 ? 1 : blocks;
-        scale_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(C, ldc, M, N, beta);
-        return cuda_status(cudaGetLastError());
-    }
-    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
-    const EmulLayout L = emul_layout(M, N, K, nslices);
-    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
-        return ALP_ERR_WORKSPACE;
-    char* ws = static_cast<char*>(workspace);
-    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
-    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
-    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
-    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
-    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
-    alp_status st;
-    if ((st = emul_exponents(M, K, A, lda, 0, e, s)) != ALP_OK) return st;
-    if ((st = emul_exponents(N, K, B, ldb, 1, f, s)) != ALP_OK) return st;
-    if ((st = emul_split(M, K, A, lda, 0, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
-    if ((st = emul_split(N, K, B, ldb, 1, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
-    alp_config cfg;
-    const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
-    if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
-                              have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
-                              sc.trim)) != ALP_OK)
-        return st;
-    return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f, M,
-                                N, alpha, beta, C, ldc);
+    return emul_gemm_impl<float>(0, 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,
+                                 kind, workspace, workspace_bytes,
+                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+alp_status alp_gemm_f32_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                float alpha, const float* A, int64_t lda, const float* B,
+                                int64_t ldb, float beta, float* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    return emul_gemm_impl<float>(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                 nslices, kind, workspace, workspace_bytes,
+                                 reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -162,3 +162,21 @@ def test_emul_f32_full_size_sampled_rows(alp, orc):
     rows = np.array([0, 4097, 8191])
     ref, _ = model(orc, 1.0, A, B, 0.0, None, 3, "b8", rows=rows)
     assert np.array_equal(got[rows], ref)
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+def test_emul_f32_transposed_operands_bit_exact(alp, orc, ta, tb):
+    import torch
+    M, N, K = 257, 300, 333
+    A, B, C = f32(*inputs.gemm_operands(4500 + 2 * ta + tb, M, N, K, kind="scaled", phi=4))
+    As = np.ascontiguousarray(A.T) if ta else A
+    Bs = np.ascontiguousarray(B.T) if tb else B
+    dA, dB, dC = (torch.from_numpy(x).cuda() for x in (As, Bs, C))
+    ws = alp.alp_gemm_f32_emul_workspace(M, N, K, 3, alp.ALP_SLICE_BF16_B8)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f32_emul_ex(ta, tb, M, N, K, 1.5, dA, As.shape[1], dB, Bs.shape[1], 0.5, dC, N,
+                             3, alp.ALP_SLICE_BF16_B8, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = model(orc, 1.5, A, B, 0.5, C, 3, "b8")
+    assert np.array_equal(dC.cpu().numpy(), ref)

@@ -416,3 +416,34 @@ def test_recombine_rounding(alp, kind, s):
             except OverflowError:
                 want = math.copysign(math.inf, X)
             assert got[row, j] == want or (want == 0 and got[row, j] == 0), (row, j, X, E)
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("kind,s", [("b7", 8), ("b8t", 7)])
+def test_emul_transposed_operands_bit_exact(alp, orc, ta, tb, kind, s):
+    """alp_gemm_f64_emul_ex with op(A) = A^T and/or op(B) = B^T, padded leading
+    dimensions: the oracle's result on the transposed matrices."""
+    import torch
+    M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
+    A, B, C = inputs.gemm_operands(4400 + 2 * ta + tb, M, N, K, kind="scaled", phi=8)
+    As = np.ascontiguousarray(A.T) if ta else A            # stored K x M or M x K
+    Bs = np.ascontiguousarray(B.T) if tb else B            # stored N x K or K x N
+    lda, ldb = As.shape[1] + 3, Bs.shape[1] + 5
+    dA = torch.full((As.shape[0], lda), float("nan"), dtype=torch.float64, device="cuda")
+    dA[:, :As.shape[1]] = torch.from_numpy(As)
+    dB = torch.full((Bs.shape[0], ldb), float("nan"), dtype=torch.float64, device="cuda")
+    dB[:, :Bs.shape[1]] = torch.from_numpy(Bs)
+    dC = torch.from_numpy(C).cuda()
+    k = KINDS[kind][0]
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, s, k)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f64_emul_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N, s, k, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = model(orc, 1.5, A, B, 0.5, C, s, kind)
+    assert np.array_equal(dC.cpu().numpy(), ref)
+    bad = alp.alp_gemm_f64_emul_ex(ta, tb, M, N, K, 1.5, dA, (M if ta else K) - 1, dB, ldb, 0.5,
+                                   dC, N, s, k, work, ws, raise_on_error=False)
+    assert bad == alp.ALP_ERR_INVALID_ARG
+    assert alp.alp_gemm_f64_emul_ex(2, 0, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N, s, k, work,
+                                    ws, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
