@@ -101,6 +101,19 @@ alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha,
                         const double* A, int64_t lda, const double* B, int64_t ldb,
                         double beta, double* C, int64_t ldc,
                         const alp_config* cfg, void* stream);
+/* Transposed operands for the native GEMM: C = alpha op(A) op(B) + beta C with
+ * op(X) = X (trans 0) or X^T (trans 1), storage as for alp_gemm_f64_emul_ex.
+ * A transposed operand is first packed row-major into `workspace` (one read
+ * and one write of it, small against the 2 M N K FP64 flops), then the product
+ * runs as alp_gemm_f64 with `cfg`; results are bit-identical to alp_gemm_f64
+ * on the transposed matrices.  workspace >= alp_gemm_f64_ex_workspace(...),
+ * 256-byte aligned (none needed, and none read, when neither is transposed). */
+alp_status alp_gemm_f64_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                           double alpha, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double beta, double* C, int64_t ldc,
+                           const alp_config* cfg, void* workspace, size_t workspace_bytes,
+                           void* stream);
+size_t alp_gemm_f64_ex_workspace(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K);
 
 /*
  * Emulated FP64 GEMM (not in the paper; error-free splitting after Ozaki,

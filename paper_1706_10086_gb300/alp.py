@@ -77,6 +77,9 @@ _SIGS = {
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
                            _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_gemm_f64_ex": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
+                         _i64, ctypes.POINTER(alp_config), _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f64_ex_workspace": ([_int, _int, _i64, _i64, _i64], ctypes.c_size_t),
     "alp_gemm_f64_emul_ex": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
                               _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_ex": ([_int, _int, _i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp,
@@ -189,6 +192,22 @@ def alp_gemm_f64(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None, stream=
     st = lib().alp_gemm_f64(M, N, K, float(alpha), _p(A), lda, _p(B), ldb, float(beta), _p(C),
                             ldc, ctypes.byref(c) if c is not None else None, _s(stream))
     return _check(st, "alp_gemm_f64", raise_on_error)
+
+
+def alp_gemm_f64_ex(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None,
+                    workspace=None, workspace_bytes=0, stream=None, raise_on_error=True):
+    c = None
+    if cfg is not None:
+        c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    st = lib().alp_gemm_f64_ex(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                               _p(B), ldb, float(beta), _p(C), ldc,
+                               ctypes.byref(c) if c is not None else None, _p(workspace),
+                               int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f64_ex", raise_on_error)
+
+
+def alp_gemm_f64_ex_workspace(trans_a, trans_b, M, N, K):
+    return int(lib().alp_gemm_f64_ex_workspace(int(trans_a), int(trans_b), M, N, K))
 
 
 def alp_gemm_f64_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices, kind, workspace,

@@ -18,6 +18,8 @@ alp_status native_launch(const alp_config& cfg, bool use_tma, int64_t M, int64_t
                          double alpha, const double* A, int64_t lda, const double* B,
                          int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t stream,
                          int inject_skip_kt, int64_t grid_limit);
+alp_status native_transpose(const double* X, int64_t R, int64_t Cn, int64_t ldx, double* out,
+                            int64_t ldo, cudaStream_t stream);
 alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ldc,
                         cudaStream_t stream);
 // tune.cu: tuned cache, then cost model, then default.
@@ -213,6 +215,66 @@ alp_status alp_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const dou
                         (lda % 2 == 0) && (ldb % 2 == 0);
     return native_launch(c, tma_ok, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s,
                          inject_skip_kt(), 0);
+}
+
+// Bytes of the workspace of alp_gemm_f64_ex: a packed op(A) (M x K) when
+// trans_a, then a packed op(B) (K x N) when trans_b, each 256-byte aligned.
+static size_t ex_bytes_a(int ta, int64_t M, int64_t K) {
+    return ta ? (((size_t)M * (size_t)K * 8 + 255) & ~(size_t)255) : 0;
+}
+static size_t ex_bytes_b(int tb, int64_t K, int64_t N) {
+    return tb ? (((size_t)K * (size_t)N * 8 + 255) & ~(size_t)255) : 0;
+}
+
+size_t alp_gemm_f64_ex_workspace(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K) {
+    if (M < 0 || N < 0 || K < 0 || (trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1))
+        return 0;
+    return ex_bytes_a(trans_a, M, K) + ex_bytes_b(trans_b, K, N);
+}
+
+alp_status alp_gemm_f64_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                           double alpha, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double beta, double* C, int64_t ldc,
+                           const alp_config* cfg, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+    if (M < 0 || N < 0 || K < 0 || (trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1))
+        return ALP_ERR_INVALID_ARG;
+    if (!trans_a && !trans_b)
+        return alp_gemm_f64(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg, stream);
+    if (M == 0 || N == 0) return ALP_OK;
+    if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N) || ldc < N || !C)
+        return ALP_ERR_INVALID_ARG;
+    const bool reads_ab = alpha != 0.0 && K > 0;
+    if (reads_ab && (!A || !B)) return ALP_ERR_INVALID_ARG;
+    if (((uintptr_t)C & 7) || (reads_ab && (((uintptr_t)A & 7) || ((uintptr_t)B & 7))))
+        return ALP_ERR_INVALID_ARG;
+    if (!reads_ab)
+        return alp_gemm_f64(M, N, K, alpha, nullptr, K, nullptr, N, beta, C, ldc, cfg, stream);
+    const size_t ba = ex_bytes_a(trans_a, M, K), bb = ex_bytes_b(trans_b, K, N);
+    if (!workspace || workspace_bytes < ba + bb || ((uintptr_t)workspace & 255))
+        return ALP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the transposed operands are packed row-major into the workspace (one
+    // read and one write of 8 bytes per element, against 2 M N K flops of
+    // FP64 DMMA work), then the product runs as alp_gemm_f64
+    char* ws = static_cast<char*>(workspace);
+    const double* Aop = A;
+    const double* Bop = B;
+    int64_t lda_op = lda, ldb_op = ldb;
+    alp_status st;
+    if (trans_a) {
+        double* At = reinterpret_cast<double*>(ws);
+        if ((st = native_transpose(A, K, M, lda, At, K, s)) != ALP_OK) return st;
+        Aop = At;
+        lda_op = K;
+    }
+    if (trans_b) {
+        double* Bt = reinterpret_cast<double*>(ws + ba);
+        if ((st = native_transpose(B, N, K, ldb, Bt, N, s)) != ALP_OK) return st;
+        Bop = Bt;
+        ldb_op = N;
+    }
+    return alp_gemm_f64(M, N, K, alpha, Aop, lda_op, Bop, ldb_op, beta, C, ldc, cfg, stream);
 }
 
 alp_status alp_get_device_error(void* stream) {

@@ -208,6 +208,33 @@ static alp_status launch_tm_tn(const alp_config& cfg, int stages, bool use_tma, 
     return cuda_status(cudaGetLastError());
 }
 
+// out (C x R, row stride ldo) = X^T for a row-major R x C matrix X (row
+// stride ldx): 32 x 32 tiles through shared memory, reads and writes along rows.
+__global__ void transpose_kernel(const double* __restrict__ X, int64_t R, int64_t Cn, int64_t ldx,
+                                 double* __restrict__ out, int64_t ldo) {
+    __shared__ double t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < R && c < Cn) ? X[r * ldx + c] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < Cn && r < R) out[c * ldo + r] = t[threadIdx.x][i];
+    }
+}
+
+alp_status native_transpose(const double* X, int64_t R, int64_t Cn, int64_t ldx, double* out,
+                            int64_t ldo, cudaStream_t stream) {
+    if (R == 0 || Cn == 0) return ALP_OK;
+    const int64_t gy = (R + 31) / 32, gx = (Cn + 31) / 32;
+    if (gy > 65535 || gx > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
+    transpose_kernel<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, stream>>>(X, R, Cn, ldx,
+                                                                                   out, ldo);
+    return cuda_status(cudaGetLastError());
+}
+
 alp_status native_scale(int64_t M, int64_t N, double beta, double* C, int64_t ldc,
                         cudaStream_t stream) {
     const int64_t total = M * N;

@@ -128,3 +128,39 @@ def test_stream_ordering_and_error_word(alp, orc):
         got, _ = run_gemm(alp, A, B, C, 1.0, 1.0, stream=s)
     assert np.array_equal(got, orc.gemm(1.0, A, B, 1.0, C))
     assert alp.alp_get_device_error() == alp.ALP_OK
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+def test_native_transposed_operands(alp, orc, ta, tb):
+    """alp_gemm_f64_ex: bit-identical to alp_gemm_f64 on the transposed matrices
+    (same kernel, same config), within the bound of the oracle; padded leading
+    dimensions; a missing workspace is refused."""
+    import torch
+    M, N, K = 300, 260, 270
+    A, B, C = inputs.gemm_operands(5100 + 2 * ta + tb, M, N, K)
+    As = np.ascontiguousarray(A.T) if ta else A
+    Bs = np.ascontiguousarray(B.T) if tb else B
+    lda, ldb = As.shape[1] + 2, Bs.shape[1] + 4
+    dA = torch.full((As.shape[0], lda), float("nan"), dtype=torch.float64, device="cuda")
+    dA[:, :As.shape[1]] = torch.from_numpy(As)
+    dB = torch.full((Bs.shape[0], ldb), float("nan"), dtype=torch.float64, device="cuda")
+    dB[:, :Bs.shape[1]] = torch.from_numpy(Bs)
+    cfg = (64, 128, 64, 4, 4, 0)
+    dC = torch.from_numpy(C).cuda()
+    ws = alp.alp_gemm_f64_ex_workspace(ta, tb, M, N, K)
+    assert ws >= 8 * (ta * M * K + tb * K * N)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f64_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N, cfg=cfg,
+                        workspace=work, workspace_bytes=ws)
+    ref = torch.from_numpy(C).cuda()
+    alp.alp_gemm_f64(M, N, K, 1.5, torch.from_numpy(A).cuda(), K, torch.from_numpy(B).cuda(), N,
+                     0.5, ref, N, cfg=cfg)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()
+    assert np.array_equal(got, ref.cpu().numpy())
+    exact = orc.gemm(1.5, A, B, 0.5, C)
+    bound = orc.error_bound(1.5, orc.absgemm(A, B), 0.5, C, K)
+    assert np.all(np.abs(got - exact) <= bound)
+    assert alp.alp_gemm_f64_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N,
+                               raise_on_error=False) == alp.ALP_ERR_WORKSPACE
+    assert alp.alp_gemm_f64_ex_workspace(2, 0, M, N, K) == 0
