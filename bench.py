@@ -240,6 +240,7 @@ def make_inputs(torch, n, phi, seed, device):
 
 
 def run_alp(args):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -420,6 +421,32 @@ def run_alp(args):
                       "d2h_bytes_per_step": int(hC.numel() * 8),
                       "overlap": "copies on a second stream, two operand sets"}
         del sets
+
+    if not args.no_e2e and alp.alp_host_access()[0]:
+        # end to end with the operands left in host memory: the device reads
+        # A and B and writes C through the host's page tables (NVLink-C2C on a
+        # Grace host); no copies, one call per step
+        hA2 = A.cpu().numpy()
+        hB2 = B.cpu().numpy()
+        hC2 = np.empty((n, n))
+        ks = max(2, args.steps)
+        call = lambda: alp.alp_gemm_f64_emul(M, N, K, alpha, hA2.ctypes.data, K, hB2.ctypes.data,
+                                             N, beta, hC2.ctypes.data, N, s, kind, work, wsb,
+                                             stream)
+        call()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ks):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert alp.alp_get_device_error(stream) == alp.ALP_OK
+        hd_ms = e0.elapsed_time(e1) / ks
+        out["e2e_host_resident"] = {
+            "value": round(flops_step / (hd_ms * 1e-3) / 1e12, 3), "unit": UNIT,
+            "ms_per_step": round(hd_ms, 3), "steps": ks,
+            "note": "A, B, C in pageable host memory, read and written by the kernels in place"}
+        del hA2, hB2, hC2
 
     if not args.no_native:
         # native DMMA path, alpha = 1.5, beta = 0.5 on the same operands

@@ -174,6 +174,19 @@ alp_status alp_gemm_batched_varsize_noalloc(int64_t count, const int64_t* dM, co
 alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,
                                int* pieces, int* t_lo, int* t_hi);
 
+/* ---- host-resident operands ---------------------------------------------- */
+
+/* Whether kernels on the current device may read and write host memory
+ * through the host's own page tables (a Grace host over NVLink-C2C): *pageable
+ * = 1 when any host pointer (pageable or pinned) is valid in a kernel,
+ * *host_page_tables = 1 when that access uses the host's page tables (no
+ * migration).  When *pageable is 1, the emulated GEMMs accept host pointers
+ * for A, B and C: the exponent scans and splits read A and B where they are
+ * and the recombination writes C there (the workspace stays on the device,
+ * the tensor-core stage reads only it).  The native GEMM's TMA loads need
+ * device memory.  Host-only query. */
+alp_status alp_host_access(int* pageable, int* host_page_tables);
+
 /* ---- FP64 peak probe ----------------------------------------------------- */
 
 /* Measured FP64 throughput of this GPU: kind 0 = m16n8k4 DMMA chains (the

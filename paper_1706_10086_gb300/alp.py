@@ -77,6 +77,7 @@ _SIGS = {
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
                            _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_host_access": ([ctypes.POINTER(_int), ctypes.POINTER(_int)], _int),
     "alp_gemm_f64_ex": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
                          _i64, ctypes.POINTER(alp_config), _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f64_ex_workspace": ([_int, _int, _i64, _i64, _i64], ctypes.c_size_t),
@@ -192,6 +193,13 @@ def alp_gemm_f64(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None, stream=
     st = lib().alp_gemm_f64(M, N, K, float(alpha), _p(A), lda, _p(B), ldb, float(beta), _p(C),
                             ldc, ctypes.byref(c) if c is not None else None, _s(stream))
     return _check(st, "alp_gemm_f64", raise_on_error)
+
+
+def alp_host_access():
+    """(pageable, host_page_tables) of the current device (see alp_ext.h)."""
+    a, b = _int(0), _int(0)
+    _check(lib().alp_host_access(ctypes.byref(a), ctypes.byref(b)), "alp_host_access", True)
+    return a.value, b.value
 
 
 def alp_gemm_f64_ex(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None,

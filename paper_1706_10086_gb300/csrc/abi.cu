@@ -277,6 +277,21 @@ alp_status alp_gemm_f64_ex(int trans_a, int trans_b, int64_t M, int64_t N, int64
     return alp_gemm_f64(M, N, K, alpha, Aop, lda_op, Bop, ldb_op, beta, C, ldc, cfg, stream);
 }
 
+alp_status alp_host_access(int* pageable, int* host_page_tables) {
+    if (!pageable || !host_page_tables) return ALP_ERR_INVALID_ARG;
+    int d = 0, a = 0, b = 0;
+    if (cudaGetDevice(&d) != cudaSuccess ||
+        cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, d) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, d) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return ALP_ERR_CUDA;
+    }
+    *pageable = a ? 1 : 0;
+    *host_page_tables = b ? 1 : 0;
+    return ALP_OK;
+}
+
 alp_status alp_get_device_error(void* stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int* w = device_error_word();

@@ -447,3 +447,27 @@ def test_emul_transposed_operands_bit_exact(alp, orc, ta, tb, kind, s):
     assert bad == alp.ALP_ERR_INVALID_ARG
     assert alp.alp_gemm_f64_emul_ex(2, 0, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N, s, k, work,
                                     ws, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
+
+
+def test_emul_host_resident_operands(alp, orc):
+    """On a device that reads host memory through the host's page tables
+    (alp_host_access), A, B and C may live in ordinary (pageable) host memory:
+    the scans and splits read them there, the recombination writes C there.
+    Same bits as with device-resident operands; skipped elsewhere."""
+    import torch
+    pageable, _ = alp.alp_host_access()
+    if not pageable:
+        pytest.skip("this device does not access pageable host memory")
+    M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
+    A, B, C = inputs.gemm_operands(4600, M, N, K, kind="scaled", phi=8)
+    A, B = np.ascontiguousarray(A), np.ascontiguousarray(B)
+    hC = np.ascontiguousarray(C.copy())
+    k = alp.ALP_SLICE_BF16_B8_TRIM
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, 7, k)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f64_emul(M, N, K, 1.5, A.ctypes.data, K, B.ctypes.data, N, 0.5, hC.ctypes.data,
+                          N, 7, k, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = orc.emul_gemm(1.5, A, B, 0.5, C, 7, b=8, trim=True)
+    assert np.array_equal(hC, ref)
