@@ -57,10 +57,12 @@ def lib():
             L.orc_emul_gemm.argtypes = [i64, i64, i64, f64, vp, i64, vp, i64, f64, vp, i64,
                                         vp, i64, i32, i32, i32, vp, i64, i32]
             L.orc_emul_gemm_f32.argtypes = L.orc_emul_gemm.argtypes
+            L.orc_crt_gemm.argtypes = [i64, i64, i64, f64, vp, i64, vp, i64, f64, vp, i64, vp, i64,
+                                       i32, vp, i64, i32]
             L.orc_int128_to_double.argtypes = [i64, ctypes.c_uint64]
             L.orc_int128_to_double.restype = ctypes.c_double
             for fn in ("orc_gemm_f64", "orc_absgemm", "orc_row_exponents", "orc_col_exponents",
-                       "orc_split", "orc_emul_gemm", "orc_emul_gemm_f32",
+                       "orc_split", "orc_emul_gemm", "orc_emul_gemm_f32", "orc_crt_gemm",
                        "orc_long_double_digits"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
@@ -185,6 +187,25 @@ def emul_gemm_f32(alpha, A, B, beta, C, s, b=8, rows=None, nthreads=None, trim=F
                                  int(bool(trim)), _ptr(ridx), nr, _threads(nthreads))
     assert rc in (0, 2), rc
     return D.astype(np.float32), rc
+
+
+def crt_gemm(alpha, A, B, beta, C, k, rows=None, nthreads=None):
+    """The modular (CRT) emulated GEMM: the exact product of the operands
+    rounded to k-bit integers per row and column, rounded once.  Returns
+    (D, status)."""
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = np.zeros((M, N))
+    C = _f64(C)
+    ridx = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = M if ridx is None else len(ridx)
+    D = np.empty((nr, N))
+    rc = lib().orc_crt_gemm(M, N, K, float(alpha), _ptr(A), K, _ptr(B), N, float(beta), _ptr(C),
+                            N, _ptr(D), N, int(k), _ptr(ridx), nr, _threads(nthreads))
+    assert rc in (0, 2), rc
+    return D, rc
 
 
 def int128_to_double(x: int) -> float:

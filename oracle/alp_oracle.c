@@ -15,6 +15,9 @@
  *                     exact integer slice products, FP64 recombination in its
  *                     fixed order.  The GPU must reproduce it bit for bit.
  *   orc_emul_gemm_f32 the same for FP32 operands and an FP32 result.
+ *   orc_crt_gemm      the modular variant: the exact product of the operands
+ *                     rounded to k-bit integers per row and column, rounded
+ *                     once to FP64.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math, no
  * contraction, so every expression rounds exactly where it is written).
@@ -348,6 +351,86 @@ int orc_emul_gemm_f32(int64_t M, int64_t N, int64_t K, double alpha,
         return 1;
     return emul_gemm(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, b, trim, rows,
                      nrows, nthreads, 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* O2b: the modular (CRT) variant of the emulated FP64 GEMM, after Ozaki,    */
+/* Uchino and Imamura's scheme II, in the reading this library uses: with    */
+/* the row and column exponents e_i, f_j of O2,                              */
+/*   A'_ik = nearest integer (ties to even) to A_ik 2^(k - e_i),             */
+/*   B'_kj = nearest integer (ties to even) to B_kj 2^(k - f_j),             */
+/*   P_ij  = sum_k A'_ik B'_kj   (exact),                                    */
+/*   out   = alpha * ldexp((double)P_ij, e_i + f_j - 2k)  (one rounding;     */
+/*           a second only when subnormal), then fma(beta, C_ij, out).       */
+/* The GPU computes P from its residues modulo pairwise coprime moduli and   */
+/* the Chinese remainder theorem; this is the plain definition it must meet  */
+/* bit for bit.  |A'| <= 2^k, so |P| <= K 2^(2k); the caller keeps that      */
+/* below 2^125.                                                              */
+
+typedef struct {
+    int64_t M, N, K;
+    double alpha, beta;
+    const double* C;
+    int64_t ldc;
+    double* D;
+    int64_t ldd;
+    const int64_t* rows;
+    int k;
+    const int64_t *iA, *iB;   /* [nrows][K] scaled rows of A, [N][K] scaled columns of B */
+    const int32_t *e, *f;
+} crt_ctx;
+
+static void crt_row(void* p, int64_t r) {
+    crt_ctx* g = (crt_ctx*)p;
+    const int64_t i = g->rows ? g->rows[r] : r;
+    double* d = g->D + r * g->ldd;
+    for (int64_t j = 0; j < g->N; ++j) {
+        if (g->alpha == 0.0 || g->K == 0) {
+            d[j] = (g->beta == 0.0) ? 0.0 : g->beta * g->C[i * g->ldc + j];
+            continue;
+        }
+        __int128 P = 0;
+        const int64_t* a = g->iA + r * g->K;
+        const int64_t* b = g->iB + j * g->K;
+        for (int64_t kk = 0; kk < g->K; ++kk) P += (__int128)a[kk] * (__int128)b[kk];
+        double v = ldexp((double)P, g->e[i] + g->f[j] - 2 * g->k);
+        double out = g->alpha * v;
+        if (g->beta != 0.0) out = fma(g->beta, g->C[i * g->ldc + j], out);
+        d[j] = out;
+    }
+}
+
+/* Nearest integer (ties to even) to x 2^(k - e): ldexp is exact unless the
+ * result is below the normal range, where the nearest integer is 0 anyway. */
+static int64_t scaled_int(double x, int32_t e, int k) {
+    return (int64_t)nearbyint(ldexp(x, k - e));
+}
+
+int orc_crt_gemm(int64_t M, int64_t N, int64_t K, double alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb,
+                 double beta, const double* C, int64_t ldc,
+                 double* D, int64_t ldd, int k,
+                 const int64_t* rows, int64_t nrows, int nthreads) {
+    if (M < 0 || N < 0 || K < 0 || k < 1 || k > 60) return 1;
+    if (K > 0 && (int)(2 * k) + (int)ceil(log2((double)K)) > 125) return 1;
+    const int64_t nra = rows ? nrows : M;
+    int32_t* e = (int32_t*)calloc((size_t)(M > 0 ? M : 1), sizeof(int32_t));
+    int32_t* f = (int32_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
+    int bad = orc_row_exponents(M, K, A, lda, e) | orc_col_exponents(K, N, B, ldb, f);
+    if (bad && alpha != 0.0) { free(e); free(f); return 2; }
+    size_t na = (size_t)nra * (size_t)K, nb = (size_t)N * (size_t)K;
+    int64_t* iA = (int64_t*)malloc((na ? na : 1) * sizeof(int64_t));
+    int64_t* iB = (int64_t*)malloc((nb ? nb : 1) * sizeof(int64_t));
+    for (int64_t r = 0; r < nra; ++r) {
+        const int64_t i = rows ? rows[r] : r;
+        for (int64_t kk = 0; kk < K; ++kk) iA[r * K + kk] = scaled_int(A[i * lda + kk], e[i], k);
+    }
+    for (int64_t j = 0; j < N; ++j)
+        for (int64_t kk = 0; kk < K; ++kk) iB[j * K + kk] = scaled_int(B[kk * ldb + j], f[j], k);
+    crt_ctx g = {M, N, K, alpha, beta, C, ldc, D, ldd, rows, k, iA, iB, e, f};
+    for_rows(nra, nthreads, crt_row, &g);
+    free(iA); free(iB); free(e); free(f);
+    return 0;
 }
 
 /* Significand bits of long double on this host (64 on x86_64, 113 on aarch64),

@@ -492,3 +492,82 @@ def test_emul_gemm_f32_integer_and_special_cases(orc):
     A2 = A.copy()
     A2[1, 1] = np.inf
     assert orc.emul_gemm_f32(1.0, A2, B, 0.0, None, 3)[1] == 2
+
+
+# ---- the modular (CRT) variant of the emulated GEMM ------------------------
+
+def fraction_crt(alpha, A, B, beta, C, k):
+    """The CRT variant evaluated in exact rationals: k-bit integers by
+    round-half-even of A 2^(k-e_i) and B 2^(k-f_j), their exact product, one
+    rounding by Python's int -> float, math.ldexp, alpha in double, the fused
+    beta term rounded once."""
+    M, K = A.shape
+    N = B.shape[1]
+    e = [math.frexp(float(np.max(np.abs(A[i]))))[1] if np.any(A[i]) else 0 for i in range(M)]
+    f = [math.frexp(float(np.max(np.abs(B[:, j]))))[1] if np.any(B[:, j]) else 0
+         for j in range(N)]
+    iA = [[round(Fraction(A[i, kk]) * Fraction(2) ** (k - e[i])) for kk in range(K)]
+          for i in range(M)]
+    iB = [[round(Fraction(B[kk, j]) * Fraction(2) ** (k - f[j])) for kk in range(K)]
+          for j in range(N)]
+    out = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            P = sum(a * b for a, b in zip(iA[i], iB[j]))
+            v = alpha * math.ldexp(float(P), e[i] + f[j] - 2 * k)
+            if beta != 0.0:
+                v = float(Fraction(beta) * Fraction(C[i, j]) + Fraction(v))
+            out[i, j] = v
+    return out
+
+
+@pytest.mark.parametrize("k,phi", [(12, 0), (30, 4), (47, 0), (51, 8), (55, 32)])
+def test_crt_gemm_bit_exact_against_rationals(orc, k, phi):
+    M, N, K = 4, 3, 9
+    A, B, C = inputs.gemm_operands(300 + k + phi, M, N, K, kind="scaled", phi=phi)
+    A[0, 0] = 3 * 2.0 ** -60                              # far below the row's scale
+    D, rc = orc.crt_gemm(1.5, A, B, 0.5, C, k)
+    assert rc == 0
+    assert np.array_equal(D, fraction_crt(1.5, A, B, 0.5, C, k))
+
+
+@pytest.mark.parametrize("k", [40, 51])
+def test_crt_gemm_within_derived_bound(orc, k):
+    """|A' 2^(e-k) - A| <= 2^(e-k-1) entrywise, so the product differs from
+    the exact one by at most sum_k (2^(e_i-k-1) |B_kj| + |A_ik| 2^(f_j-k-1) +
+    2^(e_i+f_j-2k-2)), plus the final roundings."""
+    M, N, K = 5, 4, 23
+    A, B, C = inputs.gemm_operands(320 + k, M, N, K, kind="scaled", phi=8)
+    D, _ = orc.crt_gemm(1.5, A, B, 0.5, C, k)
+    E = exact_gemm(1.5, A, B, 0.5, C)
+    e, _ = orc.row_exponents(A)
+    f, _ = orc.col_exponents(B)
+    for i in range(M):
+        for j in range(N):
+            t = sum(Fraction(2) ** int(e[i] - k - 1) * abs(Fraction(B[kk, j])) +
+                    abs(Fraction(A[i, kk])) * Fraction(2) ** int(f[j] - k - 1) +
+                    Fraction(2) ** int(e[i] + f[j] - 2 * k - 2) for kk in range(K))
+            bud = Fraction(3) / Fraction(2) * t + Fraction(3 * U) * abs(Fraction(D[i, j])) + \
+                Fraction(U) * abs(Fraction(0.5) * Fraction(C[i, j]))
+            assert abs(Fraction(D[i, j]) - E[i][j]) <= bud, (i, j)
+
+
+def test_crt_gemm_exact_cases(orc):
+    """Integer entries in {-8..8} are k-bit integers exactly (k >= 4): the
+    result is the exact product; rows sampling matches; zero rows stay zero;
+    Inf is reported."""
+    Ai, Bi, _ = inputs.gemm_operands(81, 12, 10, 64, kind="int", with_c=False)
+    ref = (Ai.astype(np.int64) @ Bi.astype(np.int64)).astype(np.float64)
+    for k in (4, 20, 51):
+        D, rc = orc.crt_gemm(1.0, Ai, Bi, 0.0, None, k)
+        assert rc == 0 and np.array_equal(D, ref)
+    A, B, C = inputs.gemm_operands(85, 9, 7, 30, kind="scaled", phi=8)
+    full, _ = orc.crt_gemm(1.5, A, B, 0.5, C, 51)
+    part, _ = orc.crt_gemm(1.5, A, B, 0.5, C, 51, rows=np.array([8, 2]))
+    assert np.array_equal(part, full[[8, 2]])
+    Z = A.copy()
+    Z[3] = 0.0
+    D, _ = orc.crt_gemm(1.0, Z, B, 0.0, None, 51)
+    assert np.all(D[3] == 0.0)
+    Z[1, 1] = np.inf
+    assert orc.crt_gemm(1.0, Z, B, 0.0, None, 51)[1] == 2
