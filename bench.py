@@ -45,7 +45,7 @@ KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_
 TRAFFIC_PROFILE = "profiles/emul_gemm_kernel_8192.md"
 # slice kinds of alp_gemm_f64_emul: name -> (enum value, digit pairs for s slices)
 KINDS = {"bf16": (1, lambda s: s * (s + 1) // 2), "bf16_b8": (2, lambda s: s * (s + 1) // 2),
-         "bf16_b8_trim": (3, lambda s: s * (s - 1) // 2 + 2)}
+         "bf16_b8_trim": (3, lambda s: s * (s - 1) // 2 + 2), "bf16_crt": (4, lambda s: s)}
 
 
 def parse_args():
@@ -55,15 +55,17 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--nslices", type=int, default=7,
-                    help="digit slices; with the default kind 7 is no less accurate than "
-                         "native FP64 for the default uniform inputs (checked live against 8 "
-                         "slices of 7-bit digits); wide exponent ranges need --kind bf16 with 8 "
-                         "or --kind bf16_b8 with 7")
+    ap.add_argument("--nslices", type=int, default=None,
+                    help="digit slices (moduli for bf16_crt); default 7, or 15 for bf16_crt. "
+                         "With the default kind 7 is no less accurate than native FP64 for "
+                         "the default uniform inputs (checked live against 8 slices of 7-bit "
+                         "digits); wide exponent ranges need --kind bf16 with 8 or --kind "
+                         "bf16_b8 with 7")
     ap.add_argument("--kind", choices=tuple(KINDS), default="bf16_b8_trim",
-                    help="digit scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
+                    help="scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
                          "up to 7), bf16_b8_trim (8-bit, last group keeps only its two "
-                         "leading-digit pairs)")
+                         "leading-digit pairs), bf16_crt (residues modulo 4..16 moduli, one "
+                         "product each)")
     ap.add_argument("--phi", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
@@ -83,6 +85,8 @@ def parse_args():
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no API check, native, e2e or CPU legs): for ncu")
     a = ap.parse_args()
+    if a.nslices is None:
+        a.nslices = 15 if a.kind == "bf16_crt" else 7
     if a.profile:
         a.no_native = a.no_e2e = a.no_cpu = True
     return a
@@ -283,7 +287,10 @@ def run_alp(args):
         rec(4)
         alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
         rec(5)
-        alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)
+        if kind == alp.ALP_SLICE_BF16_CRT:
+            alp.alp_emul_recombine_crt(M, N, K, s, G, ldg, e, f, alpha, beta, C, N, stream)
+        else:
+            alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)
         rec(6)
 
     for _ in range(max(3, args.warmup)):

@@ -57,8 +57,10 @@ typedef enum alp_slice_kind {
     ALP_SLICE_INT8 = 0,        /* not available on sm_103a: tcgen05 has no kind::i8 there */
     ALP_SLICE_BF16 = 1,        /* digits of 7 bits held exactly in bf16; 3..8 slices, K <= 32768 */
     ALP_SLICE_BF16_B8 = 2,     /* digits of 8 bits held exactly in bf16; 3..7 slices, K <= 14336 */
-    ALP_SLICE_BF16_B8_TRIM = 3 /* as ALP_SLICE_BF16_B8, but the last group t = nslices+1 keeps
+    ALP_SLICE_BF16_B8_TRIM = 3, /* as ALP_SLICE_BF16_B8, but the last group t = nslices+1 keeps
                                   only the pairs with a leading digit, (1, s) and (s, 1) */
+    ALP_SLICE_BF16_CRT = 4     /* modular scheme: residues modulo nslices (4..16) pairwise
+                                  coprime moduli, one product per modulus (see below) */
 } alp_slice_kind;
 
 typedef enum alp_path { ALP_PATH_NATIVE = 0, ALP_PATH_EMUL = 1 } alp_path;
@@ -181,6 +183,37 @@ alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
 alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
                               const int32_t* G, int64_t ldg, const int32_t* e, const int32_t* f,
                               double alpha, double beta, double* C, int64_t ldc, void* stream);
+
+/*
+ * The modular scheme, ALP_SLICE_BF16_CRT (not in the paper; after Ozaki,
+ * Uchino and Imamura's scheme II, 2024).  With n = nslices moduli m_1..m_n,
+ * the first n of 256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217,
+ * 211, 199, 197, 193 (pairwise coprime, product Mn), and
+ * k = alp_emul_crt_bits(K, n), the largest k <= 60 with K 2^(2k+2) <= Mn:
+ *   A'_ik = RN(A_ik 2^(k - e_i)), B'_kj = RN(B_kj 2^(k - f_j)) (integers,
+ *   |.| <= 2^k, e_i and f_j the exponents above),
+ *   P = A' B' exact (|P| <= K 2^(2k) <= Mn / 4),
+ *   C = alpha * RN(P 2^(e_i + f_j - 2k))  (+ fma(beta, C, .) when beta != 0).
+ * P is reached through its residues: the split writes out[l][r][k] = A'_rk mod
+ * m_{l+1}, moved to [-128, 127] (exact in bf16); the tensor-core stage writes
+ * Q_l = sum_k a_l b_l (int32, Q_l = P mod m_l) into G[l-1]; the recombination
+ * takes the Chinese remainder reconstruction in 128-bit integers and rounds
+ * once.  n products of K digits instead of the digit scheme's s(s+1)/2.
+ * n in 4..16, K <= 32768; FP64 only (the FP32 calls return
+ * ALP_ERR_UNSUPPORTED for this kind).  The error is about
+ * K 2^(-k) max|A_i.| max|B_.j| per element, from the two operand roundings:
+ * for K = 8192 and similar magnitudes, 15 moduli (k = 51) stay below native
+ * FP64's error.  alp_gemm_f64_emul, alp_gemm_f64_emul_ex, the workspace
+ * query, alp_emul_split and alp_emul_slice_products accept the kind;
+ * alp_emul_recombine does not (it has no K): use alp_emul_recombine_crt,
+ * whose G holds n planes of sums with |Q_l| < 2^30 (the slice-product stage
+ * writes |Q_l| <= K 2^14 <= 2^29).
+ */
+int alp_emul_crt_bits(int64_t K, int nmoduli);   /* k above; 0 if invalid */
+alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
+                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const int32_t* f, double alpha, double beta, double* C,
+                                  int64_t ldc, void* stream);
 
 /*
  * Emulated FP32 GEMM (the paper evaluates single precision throughout,

@@ -29,6 +29,7 @@ ALP_SLICE_INT8 = 0
 ALP_SLICE_BF16 = 1
 ALP_SLICE_BF16_B8 = 2
 ALP_SLICE_BF16_B8_TRIM = 3
+ALP_SLICE_BF16_CRT = 4
 # alp_path
 ALP_PATH_NATIVE = 0
 ALP_PATH_EMUL = 1
@@ -74,6 +75,9 @@ _SIGS = {
     "alp_emul_recombine": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64,
                             _vp],
                            _int),
+    "alp_emul_crt_bits": ([_i64, _int], _int),
+    "alp_emul_recombine_crt": ([_i64, _i64, _i64, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp,
+                                _i64, _vp], _int),
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
                            _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
@@ -254,6 +258,17 @@ def alp_emul_recombine(M, N, nslices, kind, G, ldg, e, f, alpha, beta, C, ldc, s
     st = lib().alp_emul_recombine(M, N, int(nslices), int(kind), _p(G), ldg, _p(e), _p(f),
                                   float(alpha), float(beta), _p(C), ldc, _s(stream))
     return _check(st, "alp_emul_recombine", raise_on_error)
+
+
+def alp_emul_crt_bits(K, nmoduli):
+    return int(lib().alp_emul_crt_bits(K, int(nmoduli)))
+
+
+def alp_emul_recombine_crt(M, N, K, nmoduli, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
+                           raise_on_error=True):
+    st = lib().alp_emul_recombine_crt(M, N, K, int(nmoduli), _p(G), ldg, _p(e), _p(f),
+                                      float(alpha), float(beta), _p(C), ldc, _s(stream))
+    return _check(st, "alp_emul_recombine_crt", raise_on_error)
 
 
 def alp_gemm_f32_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,

@@ -18,6 +18,7 @@
 #include "alp_ext.h"
 #include "alp_internal.cuh"
 #include "emul.cuh"
+#include "emul_split.cuh"
 
 namespace alp {
 
@@ -110,223 +111,8 @@ __global__ void zero_empty_columns_kernel(int64_t N, int32_t* __restrict__ f) {
 }
 
 // ---------------------------------------------------------------------------
-// 2. split
-// ---------------------------------------------------------------------------
-// Digits of a * 2^-e.  r0 = a * 2^-e is held as a 64-bit fixed-point number
-// with 62 fraction bits, rounded to odd (truncate, then set the last bit if
-// anything was cut off): every later rounding happens at least 2 bits above
-// that last bit, so the digits equal those of the exact value ((s-1) b + 2 <=
-// 62 - b).  Each step is d = round-half-even(X / 2^(62-b)), X = (X - d 2^(62-b))
-// * 2^b, which is x = r * 2^b, d = nearest integer (ties to even), r = x - d in
-// fixed point.
-__device__ __forceinline__ uint64_t fixed_point_r0(double a, int e) {
-    const uint64_t bits = (uint64_t)__double_as_longlong(a);
-    const bool neg = (bits >> 63) != 0;
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    uint64_t m = bits & ((1ull << 52) - 1);
-    int E;
-    if (ex == 0x7FF) {
-        m = 0;
-        E = 0;   // Inf/NaN: reported by the scan; digits 0
-    } else if (ex == 0) {
-        E = -1074;
-    } else {
-        m |= 1ull << 52;
-        E = ex - 1075;
-    }
-    const int sh = E - e + 62;
-    uint64_t Y;
-    if (m == 0) Y = 0;
-    else if (sh >= 0) Y = m << (sh > 63 ? 63 : sh);
-    else if (sh > -64) {
-        const int r = -sh;
-        Y = (m >> r) | ((m & ((1ull << r) - 1)) != 0 ? 1ull : 0ull);
-    } else Y = 1;   // nonzero but below 2^-62: sticky bit only
-    return neg ? (0ull - Y) : Y;   // two's complement of the signed value
-}
-
-template <int S, int B>
-__device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
-    constexpr int SH = 62 - B;   // the digit's unit in the fixed point
-    uint64_t X = fixed_point_r0(a, e);
-#pragma unroll
-    for (int p = 0; p < S; ++p) {
-        // round half to even of X / 2^SH: floor((X + 2^(SH-1) - 1 + odd) / 2^SH),
-        // odd = the parity of floor(X / 2^SH)
-        const uint64_t odd = (X >> SH) & 1;
-        const int64_t dd = (int64_t)(X + ((1ull << (SH - 1)) - 1) + odd) >> SH;
-        d[p] = (int)dd;
-        // (X - dd 2^SH) 2^B, |.| <= 2^61; SH + B = 62
-        X = (X << B) - ((uint64_t)dd << 62);
-    }
-}
-
-// Two digits (|v| <= 256) as packed bf16: the float 1.5*2^23 + v - 1.5*2^23
-// is exactly v, and its upper 16 bits are its bf16 encoding (at most 9
-// significant bits), so no conversion instruction is needed.
-__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-    const float fl = __int_as_float(0x4B400000 + lo) - 12582912.0f;
-    const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
-    return __byte_perm((uint32_t)__float_as_int(fl), (uint32_t)__float_as_int(fh), 0x7632);
-}
-
-// A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
-// thread handles two consecutive k.
-template <typename T, int S, int B>
-__global__ void split_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K,
-                                  int64_t ldx, const int32_t* __restrict__ e,
-                                  __nv_bfloat16* __restrict__ out, int64_t kpad) {
-    const int64_t half = kpad >> 1;
-    const int64_t total = R * half;
-    const int64_t plane = R * kpad;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx / half;
-        const int64_t k = (idx - r * half) * 2;
-        const int er = e[r];
-        int d0[S], d1[S];
-        split_digits<S, B>(k < K ? (double)__ldg(X + r * ldx + k) : 0.0, er, d0);
-        split_digits<S, B>(k + 1 < K ? (double)__ldg(X + r * ldx + k + 1) : 0.0, er, d1);
-        uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
-#pragma unroll
-        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
-    }
-}
-
-// As split_rows_kernel with four consecutive k per thread: rows from
-// blockIdx.y (grid stride, no division per element), two 16-byte loads of A
-// when its row is 16-byte aligned, one 8-byte store per digit plane.  Needs
-// out 8-byte aligned (the launch checks).
-template <typename T, int S, int B>
-__global__ void __launch_bounds__(256) split_rows4_kernel(const T* __restrict__ X, int64_t R,
-                                                          int64_t K, int64_t ldx,
-                                                          const int32_t* __restrict__ e,
-                                                          __nv_bfloat16* __restrict__ out,
-                                                          int64_t kpad) {
-    const int64_t plane = R * kpad;
-    for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
-        const int er = e[r];
-        const T* xr = X + r * ldx;
-        const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
-        for (int64_t k = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); k < kpad;
-             k += 4 * (int64_t)gridDim.x * blockDim.x) {
-            double a[4];
-            if (xvec && k + 3 < K) {
-                if constexpr (sizeof(T) == 8) {
-                    const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
-                    const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
-                    a[0] = p0.x;
-                    a[1] = p0.y;
-                    a[2] = p1.x;
-                    a[3] = p1.y;
-                } else {
-                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(xr + k));
-                    a[0] = p0.x;
-                    a[1] = p0.y;
-                    a[2] = p0.z;
-                    a[3] = p0.w;
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? (double)__ldg(xr + k + u) : 0.0;
-            }
-            int d0[S], d1[S], d2[S], d3[S];
-            split_digits<S, B>(a[0], er, d0);
-            split_digits<S, B>(a[1], er, d1);
-            split_digits<S, B>(a[2], er, d2);
-            split_digits<S, B>(a[3], er, d3);
-            uint2* o = reinterpret_cast<uint2*>(out + r * kpad + k);
-#pragma unroll
-            for (int p = 0; p < S; ++p)
-                o[(p * plane) >> 2] = make_uint2(pack_bf16x2(d0[p], d1[p]), pack_bf16x2(d2[p], d3[p]));
-        }
-    }
-}
-
-// B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
-// shared memory so that reads run along j and writes along k.
-template <typename T, int S, int B>
-__global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
-                                  int64_t ldx, const int32_t* __restrict__ f,
-                                  __nv_bfloat16* __restrict__ out, int64_t kpad) {
-    __shared__ double t[32][65];
-    const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 warps
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int64_t k = k0 + ty + 8 * r, j = j0 + tx;
-        t[tx][ty + 8 * r] = (k < K && j < N) ? (double)__ldg(X + k * ldx + j) : 0.0;
-    }
-    __syncthreads();
-    const int64_t plane = N * kpad;
-#pragma unroll
-    for (int jj = ty; jj < 32; jj += 8) {
-        const int64_t j = j0 + jj;
-        if (j >= N) continue;
-        const int fj = f[j];
-        int d0[S], d1[S];
-        split_digits<S, B>(t[jj][2 * tx], fj, d0);
-        split_digits<S, B>(t[jj][2 * tx + 1], fj, d1);
-        const int64_t k = k0 + 2 * tx;
-        if (k >= kpad) continue;
-        uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
-#pragma unroll
-        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // 4. recombination + alpha/beta epilogue
 // ---------------------------------------------------------------------------
-// Nearest double (ties to even) of the 128-bit two's-complement integer
-// hi:lo, multiplied by 2^E: built from 64-bit integer operations on the IEEE
-// encoding (FP64 arithmetic is slow on this GPU).  When the scaled result
-// would leave the normal range it falls back to ldexp of the rounded value
-// (which rounds a subnormal result a second time, as the definition does).
-__device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_t lo, int E) {
-    const bool neg = hi_s < 0;
-    uint64_t hi = (uint64_t)hi_s;
-    if (neg) {   // magnitude: two's complement negation
-        lo = ~lo + 1;
-        hi = ~hi + (lo == 0 ? 1 : 0);
-    }
-    if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
-    // top: the 64 bits below and including the leading one; sticky: any bit below
-    uint64_t top;
-    bool sticky;
-    int msb;
-    if (hi) {
-        const int n = __clzll((long long)hi);
-        top = n ? (hi << n) | (lo >> (64 - n)) : hi;
-        sticky = (n ? lo << n : lo) != 0;
-        msb = 127 - n;
-    } else {
-        const int n = __clzll((long long)lo);
-        top = lo << n;
-        sticky = false;
-        msb = 63 - n;
-    }
-    uint64_t m = top >> 11;                      // 53 bits, leading one at bit 52
-    const uint64_t low = top & 0x7FF;            // 11 bits below them
-    if (low > 0x400 || (low == 0x400 && (sticky || (m & 1)))) {
-        ++m;
-        if (m >> 53) {
-            m >>= 1;
-            ++msb;
-        }
-    }
-    // m in [2^52, 2^53): value = m * 2^(msb - 52) * 2^E
-    const int be = msb + E + 1023;
-    if (be >= 1 && be <= 2046) {
-        const uint64_t bits =
-            ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
-        return __longlong_as_double((long long)bits);
-    }
-    const double v = __longlong_as_double(
-        (long long)(((uint64_t)neg << 63) | ((uint64_t)(msb + 1023) << 52) | (m & ((1ull << 52) - 1))));
-    return ldexp(v, E);
-}
-
 // X = sum_t v[t] 2^(B (S-1-t)) exactly (Horner, X = X * 2^B + v[t]), then the
 // nearest double times 2^E.  The first terms run in 64 bits (after t + 1 terms
 // |X| < 2^(32 + B t)); the rest carry a 128-bit hi:lo pair.
@@ -539,13 +325,15 @@ static alp_status emul_split_b(int64_t R, int64_t K, const T* X, int64_t ldx, in
 #define ALP_SPLIT_CASE(x)                                                                        \
     case x:                                                                                      \
         if (!trans && vec)                                                                       \
-            split_rows4_kernel<T, x, B><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps, out, kpad);   \
+            split_rows4_kernel<T, x, DigitSplit<B>><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps,  \
+                                                                           out, kpad, {});    \
         else if (!trans)                                                                         \
-            split_rows_kernel<T, x, B><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>(           \
-                X, R, K, ldx, exps, out, kpad);                                                  \
+            split_rows_kernel<T, x, DigitSplit<B>><<<grid_for(R * (kpad / 2), 256), 256, 0, st>>>( \
+                X, R, K, ldx, exps, out, kpad, {});                                              \
         else                                                                                     \
-            split_cols_kernel<T, x, B><<<dim3((unsigned)((R + 31) / 32), (unsigned)(kpad / 64)),  \
-                                      256, 0, st>>>(X, K, R, ldx, exps, out, kpad);              \
+            split_cols_kernel<T, x, DigitSplit<B>><<<dim3((unsigned)((R + 31) / 32),              \
+                                                          (unsigned)(kpad / 64)),                \
+                                      256, 0, st>>>(X, K, R, ldx, exps, out, kpad, {});          \
         break;
     switch (s) {
         ALP_SPLIT_CASE(1) ALP_SPLIT_CASE(2) ALP_SPLIT_CASE(3) ALP_SPLIT_CASE(4)
@@ -687,10 +475,9 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     if (kind == ALP_SLICE_INT8) return ALP_ERR_UNSUPPORTED;   // no tcgen05 kind::i8 on sm_103a
     EmulScheme sc;
     if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
+    if (kF32 && sc.crt) return ALP_ERR_UNSUPPORTED;           // the modular scheme is FP64 only
     const int b = sc.b;
-    const int smin = kF32 ? 2 : kMinSlices;
-    const int smax = kF32 ? emul_max_slices_f32(b) : emul_max_slices(b);
-    if (nslices < smin || nslices > smax) return ALP_ERR_INVALID_ARG;
+    if (!emul_slices_ok(sc, nslices, kF32)) return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N || !C) return ALP_ERR_INVALID_ARG;
     const bool reads_ab = alpha != T(0) && K > 0;
@@ -709,7 +496,10 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
             return native_scale(M, N, beta, C, ldc, s);
         }
     }
-    if (K > emul_max_k(b) || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    if (K > emul_scheme_max_k(sc) || M > 0x7fffffffLL || N > 0x7fffffffLL)
+        return ALP_ERR_UNSUPPORTED;
+    const int kcrt = sc.crt ? crt_bits(K, nslices) : 0;
+    if (sc.crt && kcrt < 1) return ALP_ERR_UNSUPPORTED;
     const EmulLayout L = emul_layout(M, N, K, nslices);
     if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
         return ALP_ERR_WORKSPACE;
@@ -724,17 +514,32 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     alp_status st;
     if ((st = emul_exponents(M, K, A, lda, ta, e, s)) != ALP_OK) return st;
     if ((st = emul_exponents(N, K, B, ldb, 1 - tb, f, s)) != ALP_OK) return st;
-    if ((st = emul_split(M, K, A, lda, ta, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
-    if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK) return st;
+    if constexpr (kF32) {
+        if ((st = emul_split(M, K, A, lda, ta, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
+        if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK)
+            return st;
+    } else if (sc.crt) {
+        if ((st = emul_split_crt(M, K, A, lda, ta, e, nslices, da, L.kpad, kcrt, s)) != ALP_OK)
+            return st;
+        if ((st = emul_split_crt(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, kcrt, s)) != ALP_OK)
+            return st;
+    } else {
+        if ((st = emul_split(M, K, A, lda, ta, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
+        if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK)
+            return st;
+    }
     alp_config cfg;
     const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
     if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
                               have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
-                              sc.trim)) != ALP_OK)
+                              sc.trim, sc.crt)) != ALP_OK)
         return st;
     if constexpr (kF32)
         return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e,
                                     f, M, N, alpha, beta, C, ldc);
+    else if (sc.crt)
+        return launch_recombine_crt(nslices, kcrt, recombine_grid(M, N), s, G, M * L.ldg, L.ldg,
+                                    e, f, M, N, alpha, beta, C, ldc);
     else
         return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f,
                                 M, N, alpha, beta, C, ldc);
@@ -749,8 +554,7 @@ extern "C" {
 size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < kMinSlices ||
-        nslices > emul_max_slices(sc.b))
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || !emul_slices_ok(sc, nslices, false))
         return 0;
     return emul_layout(M, N, K, nslices).bytes;
 }
@@ -758,10 +562,11 @@ size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
 alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,
                                int* pieces, int* t_lo, int* t_hi) {
     EmulScheme sc;
-    if (tiles < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 || nslices > emul_max_slices(sc.b) ||
-        sms < 1 || !n_full || !pieces || !t_lo || !t_hi)
+    if (tiles < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+        nslices > (sc.crt ? kCrtMaxModuli : emul_max_slices(sc.b)) || sms < 1 || !n_full ||
+        !pieces || !t_lo || !t_hi)
         return ALP_ERR_INVALID_ARG;
-    const TailSplit ts = tail_split(tiles, nslices, sms, sc.trim);
+    const TailSplit ts = tail_split(tiles, nslices, sms, sc.trim, sc.crt);
     *n_full = ts.n_full;
     *pieces = ts.pieces;
     for (int i = 0; i < 8; ++i) {
@@ -784,13 +589,19 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
                           const int32_t* exps, int nslices, alp_slice_kind kind, void* out_bf16,
                           int64_t kpad, void* stream) {
     EmulScheme sc;
-    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
-        nslices > emul_max_slices(sc.b) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
-        (R > 0 && K > 0 && !X))
+    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) ||
+        (sc.crt ? !emul_slices_ok(sc, nslices, false)
+                : (nslices < 1 || nslices > emul_max_slices(sc.b))) ||
+        kpad < K || kpad % 64 || !exps || !out_bf16 || (R > 0 && K > 0 && !X))
         return ALP_ERR_INVALID_ARG;
     if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
     if (trans && ldx < R) return ALP_ERR_INVALID_ARG;
+    if (sc.crt && (K > kEmulMaxK || crt_bits(K, nslices) < 1)) return ALP_ERR_UNSUPPORTED;
     if (R == 0 || kpad == 0) return ALP_OK;
+    if (sc.crt)
+        return emul_split_crt(R, K, X, ldx, trans, exps, nslices,
+                              reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
+                              crt_bits(K, nslices), reinterpret_cast<cudaStream_t>(stream));
     return emul_split(R, K, X, ldx, trans, exps, nslices,
                       reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
                       reinterpret_cast<cudaStream_t>(stream), sc.b);
@@ -800,22 +611,23 @@ alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind, const void* da_bf16, const void* db_bf16,
                                    int64_t kpad, int32_t* G, int64_t ldg, void* stream) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
-        nslices > emul_max_slices(sc.b) || kpad < K || kpad % kEmulBK || ldg < N ||
-        ldg % 256 || K > emul_max_k(sc.b))
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) ||
+        (sc.crt ? !emul_slices_ok(sc, nslices, false)
+                : (nslices < 1 || nslices > emul_max_slices(sc.b))) ||
+        kpad < K || kpad % kEmulBK || ldg < N || ldg % 256 || K > emul_scheme_max_k(sc))
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0 || K == 0) return ALP_OK;
     if (!da_bf16 || !db_bf16 || !G) return ALP_ERR_INVALID_ARG;
     return emul_slice_gemm(M, N, K, nslices, reinterpret_cast<const __nv_bfloat16*>(da_bf16),
                            reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, G, ldg,
-                           reinterpret_cast<cudaStream_t>(stream), 0, 0, sc.b, sc.trim);
+                           reinterpret_cast<cudaStream_t>(stream), 0, 0, sc.b, sc.trim, sc.crt);
 }
 
 alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
                               const int32_t* G, int64_t ldg, const int32_t* e, const int32_t* f,
                               double alpha, double beta, double* C, int64_t ldc, void* stream) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || sc.crt || nslices < 1 ||
         nslices > emul_max_slices(sc.b) || ldg < N || ldc < N)
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
@@ -823,6 +635,27 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
     return launch_recombine(nslices, sc.b, recombine_grid(M, N),
                             reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M, N,
                             alpha, beta, C, ldc);
+}
+
+int alp_emul_crt_bits(int64_t K, int nmoduli) {
+    if (K < 0 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli || K > kEmulMaxK) return 0;
+    return crt_bits(K, nmoduli);
+}
+
+alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
+                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const int32_t* f, double alpha, double beta, double* C,
+                                  int64_t ldc, void* stream) {
+    if (M < 0 || N < 0 || K < 0 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli ||
+        ldg < N || ldc < N)
+        return ALP_ERR_INVALID_ARG;
+    const int k = alp_emul_crt_bits(K, nmoduli);
+    if (k < 1) return ALP_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
+    return launch_recombine_crt(nmoduli, k, recombine_grid(M, N),
+                                reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M,
+                                N, alpha, beta, C, ldc);
 }
 
 alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -849,8 +682,7 @@ alp_status alp_gemm_f64_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, 
 size_t alp_gemm_f32_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 2 ||
-        nslices > emul_max_slices_f32(sc.b))
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || !emul_slices_ok(sc, nslices, true))
         return 0;
     return emul_layout(M, N, K, nslices).bytes;
 }
@@ -868,7 +700,7 @@ alp_status alp_emul_split_f32(int64_t R, int64_t K, const float* X, int64_t ldx,
                               const int32_t* exps, int nslices, alp_slice_kind kind,
                               void* out_bf16, int64_t kpad, void* stream) {
     EmulScheme sc;
-    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || sc.crt || nslices < 1 ||
         nslices > emul_max_slices_f32(sc.b) || kpad < K || kpad % 64 || !exps || !out_bf16 ||
         (R > 0 && K > 0 && !X))
         return ALP_ERR_INVALID_ARG;
@@ -885,7 +717,7 @@ alp_status alp_emul_recombine_f32(int64_t M, int64_t N, int nslices, alp_slice_k
                                   const int32_t* f, float alpha, float beta, float* C,
                                   int64_t ldc, void* stream) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || nslices < 1 ||
+    if (M < 0 || N < 0 || !emul_scheme_of(kind, &sc) || sc.crt || nslices < 1 ||
         nslices > emul_max_slices_f32(sc.b) || ldg < N || ldc < N)
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;

@@ -24,19 +24,48 @@ inline int64_t emul_max_k(int b) { return b == 8 ? 14336 : 32768; }
 constexpr int64_t kEmulMaxK = 32768;
 inline bool emul_digit_bits_ok(int b) { return b == 7 || b == 8; }
 
-// The digit scheme of a slice kind: b bits per digit, and whether the last
-// group t = s+1 is trimmed to its pairs with a leading digit, (1, s) and (s, 1).
+// The scheme of a slice kind: b bits per digit, whether the last group t =
+// s+1 is trimmed to its pairs with a leading digit, (1, s) and (s, 1), or
+// the modular scheme (residues modulo s pairwise coprime moduli; b = 8 is
+// its residue width for the chunk bounds).
 struct EmulScheme {
     int b;
     bool trim;
+    bool crt;
 };
 inline bool emul_scheme_of(int kind, EmulScheme* sc) {
     switch (kind) {
-        case ALP_SLICE_BF16: *sc = {7, false}; return true;
-        case ALP_SLICE_BF16_B8: *sc = {8, false}; return true;
-        case ALP_SLICE_BF16_B8_TRIM: *sc = {8, true}; return true;
+        case ALP_SLICE_BF16: *sc = {7, false, false}; return true;
+        case ALP_SLICE_BF16_B8: *sc = {8, false, false}; return true;
+        case ALP_SLICE_BF16_B8_TRIM: *sc = {8, true, false}; return true;
+        case ALP_SLICE_BF16_CRT: *sc = {8, false, true}; return true;
         default: return false;
     }
+}
+
+// The modular scheme (emul_crt.cu): 4..16 moduli; k = crt_bits(K, n) bits per
+// scaled operand (0 when no k >= 1 fits).
+constexpr int kCrtMinModuli = 4;
+constexpr int kCrtMaxModuli = 16;
+int crt_bits(int64_t K, int n);
+template <typename T>
+alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int trans,
+                          const int32_t* exps, int n, __nv_bfloat16* out, int64_t kpad, int k,
+                          cudaStream_t st);
+alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const int32_t* G,
+                                int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
+                                int64_t M, int64_t N, double alpha, double beta, double* C,
+                                int64_t ldc);
+// Slice counts a GEMM call accepts: 3..emul_max_slices(b) digits for FP64,
+// 2..32/b for FP32, kCrtMinModuli..kCrtMaxModuli moduli for the modular scheme.
+inline bool emul_slices_ok(const EmulScheme& sc, int s, bool f32) {
+    if (sc.crt) return !f32 && s >= kCrtMinModuli && s <= kCrtMaxModuli;
+    return f32 ? (s >= 2 && s <= emul_max_slices_f32(sc.b))
+               : (s >= kMinSlices && s <= emul_max_slices(sc.b));
+}
+// Largest K of one call: the modular scheme's int32 sums |Q_l| <= K 2^14 allow 32768.
+inline int64_t emul_scheme_max_k(const EmulScheme& sc) {
+    return sc.crt ? kEmulMaxK : emul_max_k(sc.b);
 }
 // Whether digit pair (p, q) of group t = p + q is multiplied.
 __host__ __device__ inline bool emul_pair_kept(int p, int q, int s, bool trim) {
@@ -63,7 +92,7 @@ enum EmulArrangement { kEmulSingle = 1, kEmulShareB = 2, kEmulPair = 3 };
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
                            cudaStream_t stream, int group_m = 0, int cluster = 0,
-                           int digit_bits = kDigitBits, bool trim = false);
+                           int digit_bits = kDigitBits, bool trim = false, bool crt = false);
 
 // Tail split of the slice-product launch (see emul_gemm.cu): whole tiles for
 // blocks [0, n_full), then each remaining tile cut into `pieces` blocks by
@@ -72,7 +101,7 @@ struct TailSplit {
     int n_full, pieces;
     int t_lo[8], t_hi[8];
 };
-TailSplit tail_split(int tiles, int s, int sms, bool trim = false);
+TailSplit tail_split(int tiles, int s, int sms, bool trim = false, bool crt = false);
 
 // Configs of the emulated path: alp_config{128, 256, 64, cluster, 0, group_m}
 // with cluster in {1, 2} (blocks sharing each B tile), or {256, 256, 64, 2,

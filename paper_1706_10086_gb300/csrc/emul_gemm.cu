@@ -89,13 +89,14 @@ constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barrie
 
 struct EmulGemmParams {
     int64_t M, N, K;
-    int s, digit_bits, trim;
+    int s, digit_bits, trim, crt;
     int32_t* G;
     int64_t ldg, gplane;
     int tiles_m, tiles_n, group_m;
     // tail split: blocks [0, n_full) take whole tiles; tiles n_full.. (the last,
     // partial wave) are cut into `pieces` blocks each, piece i taking the
-    // groups t_lo..t_hi packed in byte i of t_ranges (t_lo | t_hi << 4).
+    // groups t_lo..t_hi packed in byte i of t_ranges ((t_lo - 2) | (t_hi - 2) << 4,
+    // so that t up to 17, the last group of 16 moduli, fits).
     // Groups write disjoint planes of G.
     int n_full, pieces;
     uint64_t t_ranges;
@@ -112,14 +113,27 @@ __host__ __device__ __forceinline__ int chunk_of(int p, int q, int b) {
 }
 
 // The fixed job order of one tile (or of one piece of it, groups t_lo..t_hi):
-// groups t ascending, pairs p ascending (q = t - p), K chunks ascending.  One 32-bit word per job: first k-block
-// (bits 0..9), end k-block (10..19), p-1 (20..22), q-1 (23..25), last chunk
-// of its group (26).  Thread 0 writes the table into shared memory; every role
-// walks it.  Returns the number of jobs.
-__device__ int build_jobs(int s, int K, int b, bool trim, int t_lo, int t_hi, uint32_t* jobs) {
+// groups t ascending, pairs p ascending (q = t - p), K chunks ascending.  One
+// 32-bit word per job: first k-block (bits 0..9), end k-block (10..19), p-1
+// (20..23), q-1 (24..27), last chunk of its group (28).  Thread 0 writes the
+// table into shared memory; every role walks it.  Returns the number of jobs.
+__device__ int build_jobs(int s, int K, int b, bool trim, bool crt, int t_lo, int t_hi,
+                          uint32_t* jobs) {
     int n = 0;
     const int kblocks = (K + kTK - 1) / kTK;
     for (int t = t_lo; t <= t_hi; ++t) {
+        if (crt) {
+            // modular scheme: group t is modulus l = t - 1, the pair (l, l);
+            // residues |r| <= 128, so chunks of 1024 keep partial sums <= 2^24
+            const int l = t - 1, cb = 1024 / kTK;
+            for (int kb = 0; kb < kblocks; kb += cb) {
+                const int ke = (kb + cb < kblocks) ? kb + cb : kblocks;
+                const uint32_t last = ke == kblocks ? 1u : 0u;
+                jobs[n++] = (uint32_t)kb | ((uint32_t)ke << 10) | ((uint32_t)(l - 1) << 20) |
+                            ((uint32_t)(l - 1) << 24) | (last << 28);
+            }
+            continue;
+        }
         const int plo = (t - s > 1) ? t - s : 1;
         int phi = (s < t - 1) ? s : t - 1;
         while (phi > plo && !emul_pair_kept(phi, t - phi, s, trim)) --phi;   // last kept pair
@@ -131,7 +145,7 @@ __device__ int build_jobs(int s, int K, int b, bool trim, int t_lo, int t_hi, ui
                 const int ke = (kb + cb < kblocks) ? kb + cb : kblocks;
                 const uint32_t last = (ke == kblocks && p == phi) ? 1u : 0u;
                 jobs[n++] = (uint32_t)kb | ((uint32_t)ke << 10) | ((uint32_t)(p - 1) << 20) |
-                            ((uint32_t)(q - 1) << 23) | (last << 26);
+                            ((uint32_t)(q - 1) << 24) | (last << 28);
             }
         }
     }
@@ -139,9 +153,9 @@ __device__ int build_jobs(int s, int K, int b, bool trim, int t_lo, int t_hi, ui
 }
 __device__ __forceinline__ int job_kb(uint32_t j) { return (int)(j & 1023u); }
 __device__ __forceinline__ int job_ke(uint32_t j) { return (int)((j >> 10) & 1023u); }
-__device__ __forceinline__ int job_p(uint32_t j) { return (int)((j >> 20) & 7u) + 1; }
-__device__ __forceinline__ int job_q(uint32_t j) { return (int)((j >> 23) & 7u) + 1; }
-__device__ __forceinline__ bool job_last(uint32_t j) { return (j >> 26) & 1u; }
+__device__ __forceinline__ int job_p(uint32_t j) { return (int)((j >> 20) & 15u) + 1; }
+__device__ __forceinline__ int job_q(uint32_t j) { return (int)((j >> 24) & 15u) + 1; }
+__device__ __forceinline__ bool job_last(uint32_t j) { return (j >> 28) & 1u; }
 
 // g[0..3] = a[0..3] (if do_store), then a[0..3] = 0.
 __device__ __forceinline__ void store4_and_zero(int32_t* g, uint32_t do_store, uint32_t& a0,
@@ -192,7 +206,8 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
         }
         const uint32_t jd = jobs[job];
         if (job_last(jd)) {
-            t_group = job_p(jd) + job_q(jd);
+            // plane of G: t - 2 for the digit pair (p, q), t = p + q; l - 1 for modulus l
+            t_group = prm.crt ? job_p(jd) + 1 : job_p(jd) + job_q(jd);
             // G rows are padded to whole 256-column tiles, so the strip is in
             // bounds; rows past M are not stored.  Each asm block stores acc
             // and zeroes it in place.
@@ -246,11 +261,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if ((int)blockIdx.x >= prm.n_full) {
             const int pc = ((int)blockIdx.x - prm.n_full) % prm.pieces;
             const uint32_t r = (uint32_t)(prm.t_ranges >> (8 * pc)) & 0xffu;
-            t_lo = (int)(r & 15u);
-            t_hi = (int)(r >> 4);
+            t_lo = (int)(r & 15u) + 2;
+            t_hi = (int)(r >> 4) + 2;
         }
-        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, t_lo, t_hi,
-                                 jobs);
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, prm.crt != 0,
+                                 t_lo, t_hi, jobs);
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -438,11 +453,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (cid >= prm.n_full) {
             const int pc = (cid - prm.n_full) % prm.pieces;
             const uint32_t r = (uint32_t)(prm.t_ranges >> (8 * pc)) & 0xffu;
-            t_lo = (int)(r & 15u);
-            t_hi = (int)(r >> 4);
+            t_lo = (int)(r & 15u) + 2;
+            t_hi = (int)(r >> 4) + 2;
         }
-        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, t_lo, t_hi,
-                                 jobs);
+        *njobs_slot = build_jobs(prm.s, (int)prm.K, prm.digit_bits, prm.trim != 0, prm.crt != 0,
+                                 t_lo, t_hi, jobs);
         fence_barrier_init();
     }
     if (warp == 1) {
@@ -566,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // largest count <= min(sms / r, s, 8) whose best cut of groups t = 2..s+1
 // (group t holds t-1 digit pairs) into contiguous ranges keeps the largest
 // piece smallest.  No split when the last wave is full or pieces < 2.
-TailSplit tail_split(int tiles, int s, int sms, bool trim) {
+TailSplit tail_split(int tiles, int s, int sms, bool trim, bool crt) {
     TailSplit ts;
     ts.n_full = tiles;
     ts.pieces = 1;
@@ -581,7 +596,7 @@ TailSplit tail_split(int tiles, int s, int sms, bool trim) {
     if (k < 2 || r == sms) return ts;
     // smallest threshold whose greedy contiguous cut needs <= k pieces; group t
     // holds t-1 pairs (2 when it is the trimmed last group)
-    auto weight = [&](int t) { return (trim && t == s + 1 && s > 2) ? 2 : t - 1; };
+    auto weight = [&](int t) { return crt ? 1 : (trim && t == s + 1 && s > 2) ? 2 : t - 1; };
     int total = 0, widest = 0;
     for (int t = 2; t <= s + 1; ++t) {
         total += weight(t);
@@ -621,14 +636,17 @@ TailSplit tail_split(int tiles, int s, int sms, bool trim) {
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
                            cudaStream_t stream, int group_m, int cluster, int digit_bits,
-                           bool trim) {
-    if (!emul_digit_bits_ok(digit_bits) || s > emul_max_slices(digit_bits) ||
-        K > emul_max_k(digit_bits))
+                           bool trim, bool crt) {
+    if (crt) {
+        if (s < kCrtMinModuli || s > kCrtMaxModuli || K > kEmulMaxK) return ALP_ERR_UNSUPPORTED;
+    } else if (!emul_digit_bits_ok(digit_bits) || s > emul_max_slices(digit_bits) ||
+               K > emul_max_k(digit_bits)) {
         return ALP_ERR_UNSUPPORTED;
+    }
     {   // the job table of one tile must fit its shared-memory slot
         const int64_t kblocks = (K + kTK - 1) / kTK;
-        int64_t njobs = 0;
-        for (int t = 2; t <= s + 1; ++t)
+        int64_t njobs = crt ? s * ((kblocks + 1024 / kTK - 1) / (1024 / kTK)) : 0;
+        for (int t = 2; t <= s + 1 && !crt; ++t)
             for (int pp = (t - s > 1 ? t - s : 1); pp <= (s < t - 1 ? s : t - 1); ++pp) {
                 const int qq = t - pp;
                 if (!emul_pair_kept(pp, qq, s, trim)) continue;
@@ -653,6 +671,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.s = s;
     p.digit_bits = digit_bits;
     p.trim = trim ? 1 : 0;
+    p.crt = crt ? 1 : 0;
     p.G = G;
     p.ldg = ldg;
     p.gplane = M * ldg;
@@ -666,14 +685,14 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     const int tiles = (int)(tiles_m * tiles_n);
     p.n_full = 0x7fffffff;   // every block a whole tile unless split below
     p.pieces = 1;
-    p.t_ranges = 2u | (uint32_t)(s + 1) << 4;
+    p.t_ranges = (uint64_t)(s - 1) << 4;
     if (cl == 1 && emul_tail_split_on()) {
-        const TailSplit ts = tail_split(tiles, s, device_sm_count(), trim);
+        const TailSplit ts = tail_split(tiles, s, device_sm_count(), trim, crt);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
         p.t_ranges = 0;
         for (int i = 0; i < ts.pieces; ++i)
-            p.t_ranges |= (uint64_t)(ts.t_lo[i] | ts.t_hi[i] << 4) << (8 * i);
+            p.t_ranges |= (uint64_t)((ts.t_lo[i] - 2) | (ts.t_hi[i] - 2) << 4) << (8 * i);
     }
     if (cl == 1) {
         const int64_t grid = p.n_full >= tiles
@@ -690,12 +709,12 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     const int64_t pair_tiles = ((tiles_m + 1) / 2) * tiles_n;
     int64_t clusters = pair_tiles;
     if (pair && emul_tail_split_on()) {   // in units of pairs, half the SMs each
-        const TailSplit ts = tail_split((int)pair_tiles, s, device_sm_count() / 2, trim);
+        const TailSplit ts = tail_split((int)pair_tiles, s, device_sm_count() / 2, trim, crt);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
         p.t_ranges = 0;
         for (int i = 0; i < ts.pieces; ++i)
-            p.t_ranges |= (uint64_t)(ts.t_lo[i] | ts.t_hi[i] << 4) << (8 * i);
+            p.t_ranges |= (uint64_t)((ts.t_lo[i] - 2) | (ts.t_hi[i] - 2) << 4) << (8 * i);
         if (ts.n_full < pair_tiles) clusters = ts.n_full + (pair_tiles - ts.n_full) * ts.pieces;
     }
     cudaError_t e = pair ? cudaFuncSetAttribute(emul_gemm_pair_kernel,

@@ -1,0 +1,241 @@
+// Device helpers of the emulated GEMMs: the exact fixed-point form of a
+// scaled operand, its digits, bf16 packing, the split kernels (rows of a
+// row-major matrix, or its columns through shared memory), which take a
+// splitter object that turns one value into S small integers, and the
+// rounding of a 128-bit integer to double.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "alp_internal.cuh"
+
+namespace alp {
+
+// ---------------------------------------------------------------------------
+// 2. split
+// ---------------------------------------------------------------------------
+// Digits of a * 2^-e.  r0 = a * 2^-e is held as a 64-bit fixed-point number
+// with 62 fraction bits, rounded to odd (truncate, then set the last bit if
+// anything was cut off): every later rounding happens at least 2 bits above
+// that last bit, so the digits equal those of the exact value ((s-1) b + 2 <=
+// 62 - b).  Each step is d = round-half-even(X / 2^(62-b)), X = (X - d 2^(62-b))
+// * 2^b, which is x = r * 2^b, d = nearest integer (ties to even), r = x - d in
+// fixed point.
+__device__ __forceinline__ uint64_t fixed_point_r0(double a, int e) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(a);
+    const bool neg = (bits >> 63) != 0;
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    uint64_t m = bits & ((1ull << 52) - 1);
+    int E;
+    if (ex == 0x7FF) {
+        m = 0;
+        E = 0;   // Inf/NaN: reported by the scan; digits 0
+    } else if (ex == 0) {
+        E = -1074;
+    } else {
+        m |= 1ull << 52;
+        E = ex - 1075;
+    }
+    const int sh = E - e + 62;
+    uint64_t Y;
+    if (m == 0) Y = 0;
+    else if (sh >= 0) Y = m << (sh > 63 ? 63 : sh);
+    else if (sh > -64) {
+        const int r = -sh;
+        Y = (m >> r) | ((m & ((1ull << r) - 1)) != 0 ? 1ull : 0ull);
+    } else Y = 1;   // nonzero but below 2^-62: sticky bit only
+    return neg ? (0ull - Y) : Y;   // two's complement of the signed value
+}
+
+template <int S, int B>
+__device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
+    constexpr int SH = 62 - B;   // the digit's unit in the fixed point
+    uint64_t X = fixed_point_r0(a, e);
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+        // round half to even of X / 2^SH: floor((X + 2^(SH-1) - 1 + odd) / 2^SH),
+        // odd = the parity of floor(X / 2^SH)
+        const uint64_t odd = (X >> SH) & 1;
+        const int64_t dd = (int64_t)(X + ((1ull << (SH - 1)) - 1) + odd) >> SH;
+        d[p] = (int)dd;
+        // (X - dd 2^SH) 2^B, |.| <= 2^61; SH + B = 62
+        X = (X << B) - ((uint64_t)dd << 62);
+    }
+}
+
+// The splitter of the digit schemes: s digits of B bits (split_digits).  The
+// split kernels below take a splitter object, so that other integer
+// representations of the operands (the residues of the modular scheme) reuse
+// them.
+template <int B>
+struct DigitSplit {
+    template <int S>
+    __device__ __forceinline__ void split(double a, int e, int (&d)[S]) const {
+        split_digits<S, B>(a, e, d);
+    }
+};
+
+// Two digits (|v| <= 256) as packed bf16: the float 1.5*2^23 + v - 1.5*2^23
+// is exactly v, and its upper 16 bits are its bf16 encoding (at most 9
+// significant bits), so no conversion instruction is needed.
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
+    const float fl = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+    const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+    return __byte_perm((uint32_t)__float_as_int(fl), (uint32_t)__float_as_int(fh), 0x7632);
+}
+
+// A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
+// thread handles two consecutive k.
+template <typename T, int S, typename Sp>
+__global__ void split_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K,
+                                  int64_t ldx, const int32_t* __restrict__ e,
+                                  __nv_bfloat16* __restrict__ out, int64_t kpad, const Sp sp) {
+    const int64_t half = kpad >> 1;
+    const int64_t total = R * half;
+    const int64_t plane = R * kpad;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / half;
+        const int64_t k = (idx - r * half) * 2;
+        const int er = e[r];
+        int d0[S], d1[S];
+        sp.template split<S>(k < K ? (double)__ldg(X + r * ldx + k) : 0.0, er, d0);
+        sp.template split<S>(k + 1 < K ? (double)__ldg(X + r * ldx + k + 1) : 0.0, er, d1);
+        uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
+#pragma unroll
+        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+    }
+}
+
+// As split_rows_kernel with four consecutive k per thread: rows from
+// blockIdx.y (grid stride, no division per element), two 16-byte loads of A
+// when its row is 16-byte aligned, one 8-byte store per digit plane.  Needs
+// out 8-byte aligned (the launch checks).
+template <typename T, int S, typename Sp>
+__global__ void __launch_bounds__(256) split_rows4_kernel(const T* __restrict__ X, int64_t R,
+                                                          int64_t K, int64_t ldx,
+                                                          const int32_t* __restrict__ e,
+                                                          __nv_bfloat16* __restrict__ out,
+                                                          int64_t kpad, const Sp sp) {
+    const int64_t plane = R * kpad;
+    for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
+        const int er = e[r];
+        const T* xr = X + r * ldx;
+        const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
+        for (int64_t k = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); k < kpad;
+             k += 4 * (int64_t)gridDim.x * blockDim.x) {
+            double a[4];
+            if (xvec && k + 3 < K) {
+                if constexpr (sizeof(T) == 8) {
+                    const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
+                    const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
+                    a[0] = p0.x;
+                    a[1] = p0.y;
+                    a[2] = p1.x;
+                    a[3] = p1.y;
+                } else {
+                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(xr + k));
+                    a[0] = p0.x;
+                    a[1] = p0.y;
+                    a[2] = p0.z;
+                    a[3] = p0.w;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? (double)__ldg(xr + k + u) : 0.0;
+            }
+            int d0[S], d1[S], d2[S], d3[S];
+            sp.template split<S>(a[0], er, d0);
+            sp.template split<S>(a[1], er, d1);
+            sp.template split<S>(a[2], er, d2);
+            sp.template split<S>(a[3], er, d3);
+            uint2* o = reinterpret_cast<uint2*>(out + r * kpad + k);
+#pragma unroll
+            for (int p = 0; p < S; ++p)
+                o[(p * plane) >> 2] = make_uint2(pack_bf16x2(d0[p], d1[p]), pack_bf16x2(d2[p], d3[p]));
+        }
+    }
+}
+
+// B (K x N, row-major) -> out[p][j][k] (row stride kpad): 64 x 32 tiles through
+// shared memory so that reads run along j and writes along k.
+template <typename T, int S, typename Sp>
+__global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
+                                  int64_t ldx, const int32_t* __restrict__ f,
+                                  __nv_bfloat16* __restrict__ out, int64_t kpad, const Sp sp) {
+    __shared__ double t[32][65];
+    const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 warps
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int64_t k = k0 + ty + 8 * r, j = j0 + tx;
+        t[tx][ty + 8 * r] = (k < K && j < N) ? (double)__ldg(X + k * ldx + j) : 0.0;
+    }
+    __syncthreads();
+    const int64_t plane = N * kpad;
+#pragma unroll
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int64_t j = j0 + jj;
+        if (j >= N) continue;
+        const int fj = f[j];
+        int d0[S], d1[S];
+        sp.template split<S>(t[jj][2 * tx], fj, d0);
+        sp.template split<S>(t[jj][2 * tx + 1], fj, d1);
+        const int64_t k = k0 + 2 * tx;
+        if (k >= kpad) continue;
+        uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
+#pragma unroll
+        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+    }
+}
+
+// Nearest double (ties to even) of the 128-bit two's-complement integer
+// hi:lo, multiplied by 2^E: built from 64-bit integer operations on the IEEE
+// encoding (FP64 arithmetic is slow on this GPU).  When the scaled result
+// would leave the normal range it falls back to ldexp of the rounded value
+// (which rounds a subnormal result a second time, as the definition does).
+__device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_t lo, int E) {
+    const bool neg = hi_s < 0;
+    uint64_t hi = (uint64_t)hi_s;
+    if (neg) {   // magnitude: two's complement negation
+        lo = ~lo + 1;
+        hi = ~hi + (lo == 0 ? 1 : 0);
+    }
+    if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
+    // top: the 64 bits below and including the leading one; sticky: any bit below
+    uint64_t top;
+    bool sticky;
+    int msb;
+    if (hi) {
+        const int n = __clzll((long long)hi);
+        top = n ? (hi << n) | (lo >> (64 - n)) : hi;
+        sticky = (n ? lo << n : lo) != 0;
+        msb = 127 - n;
+    } else {
+        const int n = __clzll((long long)lo);
+        top = lo << n;
+        sticky = false;
+        msb = 63 - n;
+    }
+    uint64_t m = top >> 11;                      // 53 bits, leading one at bit 52
+    const uint64_t low = top & 0x7FF;            // 11 bits below them
+    if (low > 0x400 || (low == 0x400 && (sticky || (m & 1)))) {
+        ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++msb;
+        }
+    }
+    // m in [2^52, 2^53): value = m * 2^(msb - 52) * 2^E
+    const int be = msb + E + 1023;
+    if (be >= 1 && be <= 2046) {
+        const uint64_t bits =
+            ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
+        return __longlong_as_double((long long)bits);
+    }
+    const double v = __longlong_as_double(
+        (long long)(((uint64_t)neg << 63) | ((uint64_t)(msb + 1023) << 52) | (m & ((1ull << 52) - 1))));
+    return ldexp(v, E);
+}
+
+}  // namespace alp

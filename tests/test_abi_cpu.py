@@ -204,3 +204,45 @@ def test_emul_tail_split(alp):
         alp.alp_emul_tail_split(10, 9, B7, 152)
     with pytest.raises(alp.AlpError):
         alp.alp_emul_tail_split(10, 8, B8T, 152)
+
+
+def test_emul_tail_split_modular_scheme(alp):
+    """With the modular kind every group is one product, so the best cut of s
+    moduli into at most k pieces has ceil(s / k) in its largest piece."""
+    CRT = alp.ALP_SLICE_BF16_CRT
+    for s in range(4, 17):
+        for tiles in (5, 38, 151, 153, 300):
+            n_full, pieces = alp.alp_emul_tail_split(tiles, s, CRT, 152)
+            r = tiles % 152 or 152
+            k = min(152 // r, s, 8)
+            if k < 2:
+                assert pieces == [(2, s + 1)]
+                continue
+            assert n_full == tiles - r and pieces[0][0] == 2 and pieces[-1][1] == s + 1
+            assert max(b - a + 1 for a, b in pieces) == -(-s // k)
+    with pytest.raises(alp.AlpError):
+        alp.alp_emul_tail_split(10, 17, CRT, 152)
+
+
+# the moduli of the modular scheme, in the order the ABI documents them
+CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193]
+
+
+def test_crt_moduli_and_bits_rule(alp):
+    """The documented moduli are pairwise coprime, and alp_emul_crt_bits is the
+    largest k <= 60 with K 2^(2k+2) <= their product (so |P| <= K 2^(2k)
+    stays within a quarter of the product)."""
+    import math
+    for i, a in enumerate(CRT_MODULI):
+        for b in CRT_MODULI[i + 1:]:
+            assert math.gcd(a, b) == 1
+    for n in range(4, 17):
+        Mn = math.prod(CRT_MODULI[:n])
+        for K in (1, 2, 63, 1000, 1024, 8192, 8193, 32768):
+            k = alp.alp_emul_crt_bits(K, n)
+            assert 1 <= k <= 60
+            assert K * 2 ** (2 * k + 2) <= Mn
+            assert k == 60 or K * 2 ** (2 * k + 4) > Mn, (K, n, k)
+    assert alp.alp_emul_crt_bits(32769, 16) == 0
+    assert alp.alp_emul_crt_bits(100, 3) == 0 and alp.alp_emul_crt_bits(100, 17) == 0
+    assert alp.alp_emul_crt_bits(8192, 15) == 51 and alp.alp_emul_crt_bits(8192, 14) == 47

@@ -1,0 +1,286 @@
+"""Parity of the modular emulated FP64 GEMM (alp_slice_kind ALP_SLICE_BF16_CRT,
+through the C-ABI) with the oracle's plain definition of it: operands rounded
+to k-bit integers per row and column, their exact product, one rounding.  The
+GPU reaches that product through residues and the Chinese remainder theorem,
+which the oracle never uses, so agreement bit for bit checks the residues, the
+tensor-core sums and the reconstruction together.  Stage tests check each of
+those against integer arithmetic done here in Python."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1706_10086_gb300 import inputs
+
+from .gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+CRT = 4                                  # ALP_SLICE_BF16_CRT
+# the moduli in the order the ABI documents them
+MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193]
+
+
+def crt_k(K, n):
+    """Largest k <= 60 with K 2^(2k+2) <= m_1 ... m_n."""
+    Mn = 1
+    for m in MODULI[:n]:
+        Mn *= m
+    for k in range(60, 0, -1):
+        if max(K, 1) * 2 ** (2 * k + 2) <= Mn:
+            return k
+    return 0
+
+
+def run_crt(alp, A, B, C, alpha, beta, n, lda=None, ldc=None, raise_on_error=True):
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    dA, lda = dev(A, lda)
+    dB, ldb = dev(B)
+    dC, ldc = dev(C if C is not None else np.full((M, N), np.nan), ldc)
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, n, CRT)
+    work = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
+    st = alp.alp_gemm_f64_emul(M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc, n, CRT, work, ws,
+                               raise_on_error=raise_on_error)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy()[:M, :N], st, alp.alp_get_device_error()
+
+
+SHAPES = [(128, 256, 64), (200, 300, 130), (1, 1, 1), (257, 513, 1000), (64, 40, 2049)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("n,phi", [(4, 0), (8, 4), (14, 0), (15, 8), (16, 0), (16, 32)])
+def test_crt_bit_exact_vs_oracle(alp, orc, shape, n, phi):
+    M, N, K = shape
+    A, B, C = inputs.gemm_operands(5100 + M + N + K + n + phi, M, N, K, kind="scaled", phi=phi)
+    got, st, err = run_crt(alp, A, B, C, 1.5, 0.5, n)
+    assert st == alp.ALP_OK and err == alp.ALP_OK
+    ref, rc = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, n))
+    assert rc == 0
+    assert np.array_equal(got, ref)
+
+
+EDGE_ROWS = np.array([0, 1, 63, 127, 128, 129])
+
+
+@pytest.mark.parametrize("K", [63, 64, 65, 1023, 1024, 1025, 2049, 8193])
+def test_crt_chunk_boundaries(alp, orc, K):
+    """K around the 1024-wide drain chunks and the 64-wide k-blocks."""
+    M, N = 130, 260
+    A, B, _ = inputs.gemm_operands(5200 + K, M, N, K, kind="scaled", phi=4, with_c=False)
+    got, _, err = run_crt(alp, A, B, None, 1.0, 0.0, 15)
+    assert err == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, 15), rows=EDGE_ROWS)
+    assert np.array_equal(got[EDGE_ROWS], ref)
+
+
+@pytest.mark.parametrize("n", [4, 15])
+def test_crt_partial_sums_at_the_chunk_bound(alp, orc, n):
+    """Entries x = 1/2 + 2^(7-k): x 2^k = 2^(k-1) + 128, whose residue modulo
+    256 is -128 for either sign, so every product of the first modulus is 2^14
+    and each 1024-wide chunk's f32 partial sum is exactly 2^24, the largest the
+    chunking allows; two chunks make the int32 sum 2^25."""
+    K = 2048
+    k = crt_k(K, n)
+    x = 0.5 + 2.0 ** (7 - k)
+    M, N = 130, 260
+    A = np.full((M, K), x)
+    A[1::2] *= -1
+    B = np.full((K, N), x)
+    B[:, 1::4] *= -1
+    got, _, err = run_crt(alp, A, B, None, 1.0, 0.0, n)
+    assert err == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, k, rows=EDGE_ROWS)
+    assert np.array_equal(got[EDGE_ROWS], ref)
+
+
+def test_crt_largest_k_and_modulus_count(alp, orc):
+    """K = 32768 with 16 moduli (k = 54, |P| up to 2^123) and with 4 (k = 7)."""
+    M, N, K = 130, 260, 32768
+    A, B, _ = inputs.gemm_operands(5300, M, N, K, kind="scaled", phi=2, with_c=False)
+    for n in (16, 4):
+        got, st, err = run_crt(alp, A, B, None, 1.0, 0.0, n)
+        assert st == alp.ALP_OK and err == alp.ALP_OK
+        ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, n), rows=EDGE_ROWS)
+        assert np.array_equal(got[EDGE_ROWS], ref)
+    # opposite-sign operands at their largest: |A'| = |B'| = 2^54 - 2, |P| near
+    # K 2^108 = 2^123, just under Mn / 4
+    A = np.ones((M, K)) * (1.0 - 2.0 ** -53)
+    B = -np.ones((K, N)) * (1.0 - 2.0 ** -53)
+    got, _, err = run_crt(alp, A, B, None, 1.0, 0.0, 16)
+    assert err == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, 16), rows=EDGE_ROWS)
+    assert np.array_equal(got[EDGE_ROWS], ref) and abs(ref[0, 0] + K) <= K * 2.0 ** -50
+
+
+def test_crt_alpha_beta_padding_special_cases_and_limits(alp, orc):
+    import torch
+    M, N, K = 100, 70, 90
+    A, B, C = inputs.gemm_operands(5400, M, N, K)
+    A[5] = 0.0                                       # a zero row
+    B[:, 7] = 0.0                                    # a zero column
+    A[6, :3] = [2.0 ** 900, -2.0 ** 850, 2.0 ** -900]
+    B[:2, 8] = [2.0 ** -1000, 3.0 * 2.0 ** -1040]    # a column of tiny values
+    k = crt_k(K, 15)
+    got, _, err = run_crt(alp, A, B, C, -2.0, 0.25, 15, lda=K + 3, ldc=N + 5)
+    assert err == alp.ALP_OK
+    ref, _ = orc.crt_gemm(-2.0, A, B, 0.25, C, k)
+    assert np.array_equal(got, ref)
+    got, _, _ = run_crt(alp, A, B, None, 1.0, 0.0, 15)
+    ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, k)
+    assert np.array_equal(got, ref)
+    got, _, _ = run_crt(alp, np.full_like(A, np.nan), B, C, 0.0, 0.5, 15)
+    assert np.array_equal(got, 0.5 * C)
+    A[3, 4] = np.inf
+    _, st, err = run_crt(alp, A, B, C, 1.0, 0.0, 15)
+    assert st == alp.ALP_OK and err == alp.ALP_ERR_UNSUPPORTED
+    call = lambda M_, K_, n, kind=CRT: alp.alp_gemm_f64_emul(  # noqa: E731
+        M_, 4, K_, 1.0, 8, K_, 8, 4, 0.0, 8, 4, n, kind, 256, 1 << 40, stream=0,
+        raise_on_error=False)
+    assert call(4, 4, 3) == alp.ALP_ERR_INVALID_ARG
+    assert call(4, 4, 17) == alp.ALP_ERR_INVALID_ARG
+    assert call(4, 32769, 16) == alp.ALP_ERR_UNSUPPORTED
+    assert alp.alp_gemm_f64_emul_workspace(4, 4, 4, 3, CRT) == 0
+    assert alp.alp_gemm_f64_emul_workspace(4, 4, 4, 16, CRT) > 0
+    assert alp.alp_gemm_f32_emul_workspace(4, 4, 4, 4, CRT) == 0
+    assert alp.alp_gemm_f32_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 4, CRT, 256, 1 << 40,
+                                 stream=0, raise_on_error=False) == alp.ALP_ERR_UNSUPPORTED
+    G = torch.zeros((15, 4, 256), dtype=torch.int32, device="cuda")
+    e = torch.zeros(4, dtype=torch.int32, device="cuda")
+    C4 = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    assert alp.alp_emul_recombine(4, 4, 15, CRT, G, 256, e, e, 1.0, 0.0, C4, 4,
+                                  raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+def test_crt_transposed_operands_bit_exact(alp, orc, ta, tb):
+    import torch
+    M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
+    A, B, C = inputs.gemm_operands(5500 + 2 * ta + tb, M, N, K, kind="scaled", phi=8)
+    As = np.ascontiguousarray(A.T) if ta else A
+    Bs = np.ascontiguousarray(B.T) if tb else B
+    lda, ldb = As.shape[1] + 3, Bs.shape[1] + 5
+    dA = torch.full((As.shape[0], lda), float("nan"), dtype=torch.float64, device="cuda")
+    dA[:, :As.shape[1]] = torch.from_numpy(As)
+    dB = torch.full((Bs.shape[0], ldb), float("nan"), dtype=torch.float64, device="cuda")
+    dB[:, :Bs.shape[1]] = torch.from_numpy(Bs)
+    dC = torch.from_numpy(C).cuda()
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, 15, CRT)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f64_emul_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N, 15, CRT, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, 15))
+    assert np.array_equal(dC.cpu().numpy(), ref)
+
+
+def scaled_ints(orc, X, k, by_rows=True):
+    """X' = nearest integer (ties to even) to X 2^(k - e) per row (or column)."""
+    if by_rows:
+        e, _ = orc.row_exponents(X)
+        return np.rint(np.ldexp(X, (k - e[:, None]).astype(np.int32))).astype(np.int64), e
+    f, _ = orc.col_exponents(X)
+    return np.rint(np.ldexp(X, (k - f[None, :]).astype(np.int32))).astype(np.int64), f
+
+
+def residue(x, m):
+    """x mod m moved to [-m/2, m/2): the representative the split writes."""
+    r = np.mod(x, m)
+    return np.where(2 * r >= m + (m & 1), r - m, r)
+
+
+@pytest.mark.parametrize("n,phi", [(15, 0), (16, 8), (4, 32)])
+def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
+    """alp_emul_split with the modular kind writes the residues of the scaled
+    integers (rows of A; columns of B via trans = 1); alp_emul_slice_products
+    writes Q_l = sum_k a_l b_l exactly; alp_emul_recombine_crt turns them into
+    the oracle's result."""
+    import torch
+    M, N, K = 200, 300, 1100
+    kpad = (K + 63) // 64 * 64
+    A, B, C = inputs.gemm_operands(5600 + n + phi, M, N, K, kind="scaled", phi=phi)
+    A[0, :6] = [0.5, -0.5, 0.75, 2.0 ** -60, -(1.0 - 2.0 ** -53), 0.0]
+    k = crt_k(K, n)
+    Ai, e = scaled_ints(orc, A, k)
+    Bi, f = scaled_ints(orc, B, k, by_rows=False)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    de = torch.from_numpy(e).cuda()
+    df = torch.from_numpy(f).cuda()
+    da = torch.full((n, M, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
+    db = torch.full((n, N, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(M, K, dA, K, 0, de, n, CRT, da, kpad)
+    alp.alp_emul_split(N, K, dB, N, 1, df, n, CRT, db, kpad)
+    torch.cuda.synchronize()
+    ra = da.float().cpu().numpy().astype(np.int64)
+    rb = db.float().cpu().numpy().astype(np.int64)
+    for l in range(n):
+        assert np.array_equal(ra[l, :, :K], residue(Ai, MODULI[l])), l
+        assert np.array_equal(rb[l, :, :K], residue(Bi.T, MODULI[l])), l
+    assert np.all(ra[:, :, K:] == 0) and np.all(rb[:, :, K:] == 0)
+    ldg = (N + 255) // 256 * 256
+    G = torch.full((n, M, ldg), 12345, dtype=torch.int32, device="cuda")
+    alp.alp_emul_slice_products(M, N, K, n, CRT, da, db, kpad, G, ldg)
+    torch.cuda.synchronize()
+    g = G.cpu().numpy()
+    for l in range(n):
+        assert np.array_equal(g[l, :, :N], ra[l, :, :K] @ rb[l, :, :K].T), l
+    dC = torch.from_numpy(C.copy()).cuda()
+    alp.alp_emul_recombine_crt(M, N, K, n, G, ldg, de, df, 1.5, 0.5, dC, N)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, k)
+    assert np.array_equal(dC.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("n", [4, 9, 15, 16])
+def test_crt_recombine_rounding(alp, n):
+    """alp_emul_recombine_crt on crafted residue sums: P anywhere in
+    [-Mn/4, Mn/4] (the ends included), given as Q_l = P mod m_l plus random
+    multiples of m_l with |Q_l| < 2^30 (the documented range), with tails that are exact ties, just off a
+    tie, or carry one sticky bit; each result must be the correctly rounded
+    alpha-free value P 2^(e_i + f_j - 2k) (Python's exact rational rounding)."""
+    import random
+
+    import torch
+    K = 8192
+    k = crt_k(K, n)
+    Mn = 1
+    for m in MODULI[:n]:
+        Mn *= m
+    rnd = random.Random(33 + n)
+    vals = [0, 1, -1, Mn // 4, -(Mn // 4), Mn // 4 - 1, 2 ** 53 + 1, -(2 ** 54 + 2)]
+    vals = [v for v in vals if abs(v) <= Mn // 4]
+    top = (Mn // 4).bit_length()
+    while len(vals) < 500:
+        nbits = rnd.randrange(1, top)
+        X = rnd.getrandbits(nbits) | (1 << (nbits - 1))
+        form = rnd.randrange(5)
+        if nbits > 54 and form < 4:
+            r = nbits - 54 if form < 3 else rnd.randrange(0, nbits - 54)
+            X = (X >> (r + 1)) << (r + 1)
+            X += [1 << r, (1 << r) - 1, (1 << r) + 1, 1 << r][form]
+        if X <= Mn // 4:
+            vals.append(-X if rnd.random() < 0.5 else X)
+    N = len(vals)
+    ldg = (N + 255) // 256 * 256
+    rows = 3
+    G = np.zeros((n, rows, ldg), dtype=np.int32)
+    for j, P in enumerate(vals):
+        for l, m in enumerate(MODULI[:n]):
+            for r in range(rows):
+                G[l, r, j] = P % m + m * rnd.randrange(-(2 ** 30) // m + 1, 2 ** 30 // m - 1)
+    e = np.array([0, 5, -40], dtype=np.int32)
+    f = np.array([rnd.randrange(-8, 9) for _ in range(N)], dtype=np.int32)
+    dC = torch.full((rows, N), float("nan"), dtype=torch.float64, device="cuda")
+    alp.alp_emul_recombine_crt(rows, N, K, n, torch.from_numpy(G).cuda(), ldg,
+                               torch.from_numpy(e).cuda(), torch.from_numpy(f).cuda(), 1.0, 0.0,
+                               dC, N)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()
+    for r in range(rows):
+        for j, P in enumerate(vals):
+            E = int(e[r]) + int(f[j]) - 2 * k
+            want = float(Fraction(P) * Fraction(2) ** E)
+            assert got[r, j] == want, (r, j, P, E)

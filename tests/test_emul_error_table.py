@@ -1,6 +1,7 @@
 """Error table of the emulated FP64 GEMM at M = N = K = 8192: for phi in
 {0, 8, 32} (entries u * 2^e, e uniform in [-phi, phi]) and 3..8 slices of
-7-bit digits (3..7 of 8-bit digits, full and with the trimmed last group),
+7-bit digits (3..7 of 8-bit digits, full and with the trimmed last group;
+12..16 moduli of the modular scheme),
 the largest componentwise error |dC| / (|A||B|) in units of 2^-53 and the
 normwise error ||dC||_F / ||C||_F against the long-double oracle on sampled
 rows, next to the native DMMA kernel on the same inputs.  Set
@@ -46,6 +47,7 @@ def test_error_table_8192(alp, orc):
         runs = [("", alp.ALP_SLICE_BF16, s) for s in range(3, 9)]
         runs += [("b8", alp.ALP_SLICE_BF16_B8, s) for s in range(3, 8)]
         runs += [("b8trim", alp.ALP_SLICE_BF16_B8_TRIM, s) for s in range(3, 8)]
+        runs += [("crt", alp.ALP_SLICE_BF16_CRT, s) for s in range(12, 17)]
         for name, kind, s in runs:
             ws = alp.alp_gemm_f64_emul_workspace(n, n, n, s, kind)
             work = torch.empty(ws, dtype=torch.uint8, device="cuda")
@@ -65,6 +67,9 @@ def test_error_table_8192(alp, orc):
     # no worse than the native kernel; wider exponent ranges are reported, not
     # asserted (row/column scaling spends digits on the spread)
     assert table["phi0"]["s8"][0] <= table["phi0"]["native"][0]
+    # the modular scheme with 15 moduli (k = 51 bits per operand at K = 8192)
+    assert table["phi0"]["crts15"][0] <= table["phi0"]["native"][0]
+    assert table["phi0"]["crts15"][1] <= table["phi0"]["native"][1]
     for phi in (0, 8, 32):
         comps = [table[f"phi{phi}"][f"s{s}"][0] for s in range(3, 9)]
         assert comps[-1] < comps[0], comps
@@ -76,12 +81,15 @@ def test_error_table_8192(alp, orc):
         # are of one magnitude, phi = 0; with a spread of exponents the leading
         # digits are often small and it gains little over s-1, so the noisier
         # largest componentwise error is not ordered)
+        # each modulus adds about 4 bits to k, so the error falls with n
+        comps = [table[f"phi{phi}"][f"crts{s}"][1] for s in range(12, 17)]
+        assert all(a > b for a, b in zip(comps, comps[1:])), comps
         for s in range(4, 8):
             t = table[f"phi{phi}"]
             assert t[f"b8s{s}"][1] <= t[f"b8trims{s}"][1] <= t[f"b8s{s - 1}"][1], (phi, s)
 
 
-@pytest.mark.parametrize("kind,s", [("bf16", 7), ("bf16_b8_trim", 7)])
+@pytest.mark.parametrize("kind,s", [("bf16", 7), ("bf16_b8_trim", 7), ("bf16_crt", 15)])
 def test_full_matrix_slice_count_for_uniform_inputs(alp, kind, s):
     """Whole 8192 x 8192 result, phi = 0: the largest componentwise error of
     the native kernel and of the emulated scheme, each measured against 8
@@ -95,7 +103,8 @@ def test_full_matrix_slice_count_for_uniform_inputs(alp, kind, s):
     g.manual_seed(inputs.workload_seed("emul_8192"))
     A = torch.rand(n, n, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
     B = torch.rand(n, n, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
-    kinds = {"bf16": alp.ALP_SLICE_BF16, "bf16_b8_trim": alp.ALP_SLICE_BF16_B8_TRIM}
+    kinds = {"bf16": alp.ALP_SLICE_BF16, "bf16_b8_trim": alp.ALP_SLICE_BF16_B8_TRIM,
+             "bf16_crt": alp.ALP_SLICE_BF16_CRT}
 
     def emul(s, k):
         C = torch.empty(n, n, dtype=torch.float64, device="cuda")

@@ -309,15 +309,15 @@ def test_emul_inf_nan_and_unsupported(alp, orc):
                                  None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_WORKSPACE
     assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_BF16_B8,
                                  None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
-    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 7, 4, None, 0, stream=0,
-                                 raise_on_error=False) == alp.ALP_ERR_INVALID_ARG   # no kind 4
+    assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 7, 5, None, 0, stream=0,
+                                 raise_on_error=False) == alp.ALP_ERR_INVALID_ARG   # no kind 5
     assert alp.alp_gemm_f64_emul(4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, 8, alp.ALP_SLICE_BF16_B8_TRIM,
                                  None, 0, stream=0, raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 8, alp.ALP_SLICE_BF16_B8) == 0
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, alp.ALP_SLICE_BF16_B8) > 0
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 8, alp.ALP_SLICE_BF16_B8_TRIM) == 0
     assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, alp.ALP_SLICE_BF16_B8_TRIM) > 0
-    assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, 4) == 0
+    assert alp.alp_gemm_f64_emul_workspace(64, 64, 64, 7, 5) == 0
 
 
 def componentwise_ratio(got, ref, absAB, alpha, beta, C):
