@@ -268,7 +268,9 @@ def run_alp(args):
     ldg = (N + 255) // 256 * 256
     da = torch.empty(s * M * kpad, dtype=torch.bfloat16, device=dev)
     db = torch.empty(s * N * kpad, dtype=torch.bfloat16, device=dev)
-    G = torch.empty(s * M * ldg, dtype=torch.int32, device=dev)
+    # int32 group sums, or one byte per residue for the modular scheme
+    G = torch.empty(s * M * ldg * (1 if kind == alp.ALP_SLICE_BF16_CRT else 4),
+                    dtype=torch.uint8, device=dev)
     e = torch.empty(M, dtype=torch.int32, device=dev)
     f = torch.empty(N, dtype=torch.int32, device=dev)
     launches_per_step = 7   # scan rows, scan cols (2), split A, split B, slice products, recombine

@@ -176,10 +176,12 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
  * the last group sums only its two leading-digit pairs); kpad a multiple of
  * 64, K <= 32768 (b = 7) or 14336 (b = 8).
  * alp_emul_recombine: C = alpha * round(sum_t S^t 2^(b(nslices+1-t))) *
- * 2^(e_i + f_j - b(nslices+1)) (+ fma(beta, C, .)) from those sums. */
+ * 2^(e_i + f_j - b(nslices+1)) (+ fma(beta, C, .)) from those sums.
+ * G is 16-byte aligned.  For the modular kind (below) G holds bytes, not
+ * int32: plane l (stride M*ldg bytes) holds x_l = (P y_l) mod m_{l+1}. */
 alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind, const void* da_bf16, const void* db_bf16,
-                                   int64_t kpad, int32_t* G, int64_t ldg, void* stream);
+                                   int64_t kpad, void* G, int64_t ldg, void* stream);
 alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind kind,
                               const int32_t* G, int64_t ldg, const int32_t* e, const int32_t* f,
                               double alpha, double beta, double* C, int64_t ldc, void* stream);
@@ -195,10 +197,12 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  *   P = A' B' exact (|P| <= K 2^(2k) <= Mn / 4),
  *   C = alpha * RN(P 2^(e_i + f_j - 2k))  (+ fma(beta, C, .) when beta != 0).
  * P is reached through its residues: the split writes out[l][r][k] = A'_rk mod
- * m_{l+1}, moved to [-128, 127] (exact in bf16); the tensor-core stage writes
- * Q_l = sum_k a_l b_l (int32, Q_l = P mod m_l) into G[l-1]; the recombination
- * takes the Chinese remainder reconstruction in 128-bit integers and rounds
- * once.  n products of K digits instead of the digit scheme's s(s+1)/2.
+ * m_{l+1}, moved to [-m/2, m/2) (exact in bf16); the tensor-core stage sums
+ * Q_l = sum_k a_l b_l exactly (|Q_l| <= K 2^14, Q_l = P mod m_l) and writes
+ * the byte x_l = (Q_l y_l) mod m_l, y_l = (Mn/m_l)^-1 mod m_l, into plane
+ * l-1 of G; the recombination forms sum_l x_l (Mn/m_l) = P mod Mn in 128-bit
+ * integers (the Chinese remainder theorem) and rounds once.  n products of
+ * K digits instead of the digit scheme's s(s+1)/2.
  * n in 4..16, K <= 32768; FP64 only (the FP32 calls return
  * ALP_ERR_UNSUPPORTED for this kind).  The error is about
  * K 2^(-k) max|A_i.| max|B_.j| per element, from the two operand roundings:
@@ -206,12 +210,13 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  * FP64's error.  alp_gemm_f64_emul, alp_gemm_f64_emul_ex, the workspace
  * query, alp_emul_split and alp_emul_slice_products accept the kind;
  * alp_emul_recombine does not (it has no K): use alp_emul_recombine_crt,
- * whose G holds n planes of sums with |Q_l| < 2^30 (the slice-product stage
- * writes |Q_l| <= K 2^14 <= 2^29).
+ * which reads the n byte planes R[l][i][j] = (P_ij y_{l+1}) mod m_{l+1}
+ * (row stride ldr bytes, plane stride M*ldr) that the slice-product stage
+ * writes.  Bytes not below their modulus give unspecified results.
  */
 int alp_emul_crt_bits(int64_t K, int nmoduli);   /* k above; 0 if invalid */
 alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
-                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const uint8_t* R, int64_t ldr, const int32_t* e,
                                   const int32_t* f, double alpha, double beta, double* C,
                                   int64_t ldc, void* stream);
 

@@ -42,66 +42,178 @@ __device__ __forceinline__ int frexp_exponent_of_bits(uint64_t mb) {
     return ex - 1022;
 }
 
-// |x| as the bits of a double (FP32 operands convert exactly, so frexp and
-// the digits are the same as for the double of equal value).
-__device__ __forceinline__ uint64_t abs_bits(double x) {
-    return (uint64_t)__double_as_longlong(x) & kAbsMask;
-}
-__device__ __forceinline__ uint64_t abs_bits(float x) { return abs_bits((double)x); }
 
-// One warp per row of a row-major R x K matrix (T = double or float).
+// |x| as ordered integer keys (larger key, larger |x|): the bits of a double
+// without its sign, or of a float.  A key at or above the infinity's is Inf
+// or NaN.  The float key converts to the double bits of the same value for
+// the exponent (FP32 operands convert exactly, so frexp and the digits are
+// the same as for the double of equal value).
+template <typename T> struct ScanKey;
+template <> struct ScanKey<double> {
+    using type = uint64_t;
+    static constexpr uint64_t kInf = 0x7FF0000000000000ull;
+    __device__ static uint64_t of(uint64_t bits) { return bits & kAbsMask; }
+    __device__ static uint64_t to_double_bits(uint64_t k) { return k; }
+};
+template <> struct ScanKey<float> {
+    using type = uint32_t;
+    static constexpr uint32_t kInf = 0x7F800000u;
+    __device__ static uint32_t of(uint32_t bits) { return bits & 0x7FFFFFFFu; }
+    __device__ static uint64_t to_double_bits(uint32_t k) {
+        return (uint64_t)__double_as_longlong((double)__int_as_float((int)k));
+    }
+};
+
+// Largest key of the V = 16 / sizeof(T) elements of a 16-byte vector.
+template <typename T>
+__device__ __forceinline__ typename ScanKey<T>::type vec_key(uint4 v) {
+    using SK = ScanKey<T>;
+    if constexpr (sizeof(T) == 8) {
+        const uint64_t a = SK::of(((uint64_t)v.y << 32) | v.x);
+        const uint64_t b = SK::of(((uint64_t)v.w << 32) | v.z);
+        return a > b ? a : b;
+    } else {
+        const uint32_t a = max(SK::of(v.x), SK::of(v.y)), b = max(SK::of(v.z), SK::of(v.w));
+        return max(a, b);
+    }
+}
+template <typename T>
+__device__ __forceinline__ typename ScanKey<T>::type elem_key(const T* p) {
+    using SK = ScanKey<T>;
+    if constexpr (sizeof(T) == 8) return SK::of((uint64_t)__double_as_longlong(__ldg(p)));
+    else return SK::of((uint32_t)__float_as_int(__ldg(p)));
+}
+
+// One warp per row of a row-major R x K matrix (T = double or float): the
+// 16-byte aligned body as vectors, four in flight per lane; the ragged ends
+// element by element.
 template <typename T>
 __global__ void scan_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K, int64_t ldx,
                                  int32_t* __restrict__ e, int* err) {
+    using SK = ScanKey<T>;
+    using Key = typename SK::type;
+    constexpr int V = 16 / (int)sizeof(T);
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= R) return;
     const T* p = X + row * ldx;
-    uint64_t mx = 0;
-    bool bad = false;
-    for (int64_t k = lane; k < K; k += 32) {
-        const uint64_t v = abs_bits(__ldg(p + k));
-        if ((v >> 52) == 0x7FF) bad = true;
-        else mx = v > mx ? v : mx;
+    int64_t head = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15) / sizeof(T));
+    if (head > K) head = K;
+    const int64_t nvec = (K - head) / V;
+    Key mx = 0;
+    if (lane < head) mx = elem_key(p + lane);
+    const uint4* pv = reinterpret_cast<const uint4*>(p + head);
+    int64_t v = lane;
+    for (; v + 96 < nvec; v += 128) {
+        const uint4 a = __ldg(pv + v), b = __ldg(pv + v + 32), c = __ldg(pv + v + 64),
+                    d = __ldg(pv + v + 96);
+        const Key ka = vec_key<T>(a), kb = vec_key<T>(b), kc = vec_key<T>(c), kd = vec_key<T>(d);
+        const Key k1 = ka > kb ? ka : kb, k2 = kc > kd ? kc : kd;
+        const Key k3 = k1 > k2 ? k1 : k2;
+        mx = k3 > mx ? k3 : mx;
+    }
+    for (; v < nvec; v += 32) {
+        const Key k1 = vec_key<T>(__ldg(pv + v));
+        mx = k1 > mx ? k1 : mx;
+    }
+    for (int64_t k = head + nvec * V + lane; k < K; k += 32) {
+        const Key k1 = elem_key(p + k);
+        mx = k1 > mx ? k1 : mx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+        const Key y = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = y > mx ? y : mx;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) set_device_error(err, ALP_ERR_UNSUPPORTED);
-    if (lane == 0) e[row] = frexp_exponent_of_bits(mx);
+    if (lane == 0) {
+        if (mx >= SK::kInf) set_device_error(err, ALP_ERR_UNSUPPORTED);
+        e[row] = frexp_exponent_of_bits(SK::to_double_bits(mx));
+    }
 }
 
-// Columns of a row-major K x N matrix: blocks of 32 columns x (8 threads x
-// kColChunk rows).  The frexp exponent grows with |x|, so the column exponent
-// is the atomic max of the blocks' exponents; f starts at kNoExp (memset to
-// 0x80 bytes) and all-zero columns are set to 0 afterwards.
+// Columns of a row-major K x N matrix: blocks of 32 x V columns (one 16-byte
+// vector per thread; element by element where a vector would leave the row
+// or is unaligned) x (8 threads x kColChunk rows), four rows in flight per
+// thread.  The frexp exponent grows with |x|, so the column exponent is the
+// atomic max of the blocks' exponents; f starts at kNoExp (memset to 0x80
+// bytes) and all-zero columns are set to 0 afterwards.
 constexpr int kColChunk = 256;
 constexpr int32_t kNoExp = (int32_t)0x80808080;
 
 template <typename T>
 __global__ void scan_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N, int64_t ldx,
                                  int32_t* __restrict__ f, int* err) {
-    __shared__ uint64_t red[8][32];
-    const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    using SK = ScanKey<T>;
+    using Key = typename SK::type;
+    constexpr int V = 16 / (int)sizeof(T);
+    __shared__ Key red[8][32 * V];
+    const int64_t j = ((int64_t)blockIdx.x * 32 + threadIdx.x) * V;
     const int64_t k0 = (int64_t)blockIdx.y * kColChunk;
     const int64_t k1 = (k0 + kColChunk < K) ? k0 + kColChunk : K;
-    uint64_t mx = 0;
-    bool bad = false;
-    if (j < N) {
-        for (int64_t k = k0 + threadIdx.y; k < k1; k += 8) {
-            const uint64_t v = abs_bits(__ldg(X + k * ldx + j));
-            if ((v >> 52) == 0x7FF) bad = true;
-            else mx = v > mx ? v : mx;
+    Key mx[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) mx[c] = 0;
+    const bool vec = j + V <= N && (reinterpret_cast<uintptr_t>(X + j) & 15) == 0 &&
+                     ((ldx * (int64_t)sizeof(T)) & 15) == 0;
+    if (vec) {
+        int64_t k = k0 + threadIdx.y;
+        for (; k + 24 < k1; k += 32) {
+            uint4 w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                w[q] = __ldg(reinterpret_cast<const uint4*>(X + (k + 8 * q) * ldx + j));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t* u = reinterpret_cast<const uint32_t*>(&w[q]);
+#pragma unroll
+                for (int c = 0; c < V; ++c) {
+                    Key kk;
+                    if constexpr (sizeof(T) == 8)
+                        kk = SK::of(((uint64_t)u[2 * c + 1] << 32) | u[2 * c]);
+                    else
+                        kk = SK::of(u[c]);
+                    mx[c] = kk > mx[c] ? kk : mx[c];
+                }
+            }
         }
+        for (; k < k1; k += 8) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(X + k * ldx + j));
+            const uint32_t* u = reinterpret_cast<const uint32_t*>(&w);
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                Key kk;
+                if constexpr (sizeof(T) == 8) kk = SK::of(((uint64_t)u[2 * c + 1] << 32) | u[2 * c]);
+                else kk = SK::of(u[c]);
+                mx[c] = kk > mx[c] ? kk : mx[c];
+            }
+        }
+    } else {
+        for (int64_t k = k0 + threadIdx.y; k < k1; k += 8)
+#pragma unroll
+            for (int c = 0; c < V; ++c)
+                if (j + c < N) {
+                    const Key kk = elem_key(X + k * ldx + j + c);
+                    mx[c] = kk > mx[c] ? kk : mx[c];
+                }
     }
-    red[threadIdx.y][threadIdx.x] = mx;
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        red[threadIdx.y][threadIdx.x * V + c] = mx[c];
+        bad |= mx[c] >= SK::kInf;
+    }
     if (bad) set_device_error(err, ALP_ERR_UNSUPPORTED);
     __syncthreads();
-    if (threadIdx.y == 0 && j < N) {
-        for (int r = 1; r < 8; ++r) mx = red[r][threadIdx.x] > mx ? red[r][threadIdx.x] : mx;
-        if (mx) atomicMax(f + j, frexp_exponent_of_bits(mx));
+    // the block's 32 V columns, 8 partial maxima each: thread tid finishes
+    // column tid (threads beyond 32 V have none)
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int col = tid; col < 32 * V; col += 256) {
+        const int64_t jc = (int64_t)blockIdx.x * 32 * V + col;
+        if (jc >= N) continue;
+        Key m = red[0][col];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) m = red[r][col] > m ? red[r][col] : m;
+        if (m && m < SK::kInf) atomicMax(f + jc, frexp_exponent_of_bits(SK::to_double_bits(m)));
     }
 }
 
@@ -272,7 +384,7 @@ static dim3 recombine_grid(int64_t M, int64_t N) {
 // ---------------------------------------------------------------------------
 static inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s) {
+EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s, int gbytes) {
     EmulLayout L;
     L.kpad = (K + kEmulBK - 1) / kEmulBK * kEmulBK;
     if (L.kpad == 0) L.kpad = kEmulBK;
@@ -280,7 +392,7 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s) {
     size_t off = 0;
     L.off_da = off; off += up256((size_t)s * M * L.kpad * 2);
     L.off_db = off; off += up256((size_t)s * N * L.kpad * 2);
-    L.off_g = off;  off += up256((size_t)s * M * L.ldg * 4);
+    L.off_g = off;  off += up256((size_t)s * M * L.ldg * gbytes);
     L.off_e = off; off += up256((size_t)M * 4);
     L.off_f = off; off += up256((size_t)N * 4);
     L.bytes = off;
@@ -307,7 +419,8 @@ alp_status emul_exponents(int64_t rows, int64_t cols, const T* X, int64_t ldx, i
     // trans: X is cols x rows row-major (K x N); exponents per column (rows = N)
     const int64_t N = rows, K = cols;
     if (cudaMemsetAsync(exps, 0x80, (size_t)N * 4, st) != cudaSuccess) return ALP_ERR_CUDA;
-    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + kColChunk - 1) / kColChunk));
+    constexpr int V = 16 / (int)sizeof(T);
+    dim3 grid((unsigned)((N + 32 * V - 1) / (32 * V)), (unsigned)((K + kColChunk - 1) / kColChunk));
     if (K > 0) scan_cols_kernel<T><<<grid, dim3(32, 8), 0, st>>>(X, K, N, ldx, exps, err);
     zero_empty_columns_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, exps);
     return cuda_status(cudaGetLastError());
@@ -500,7 +613,7 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
         return ALP_ERR_UNSUPPORTED;
     const int kcrt = sc.crt ? crt_bits(K, nslices) : 0;
     if (sc.crt && kcrt < 1) return ALP_ERR_UNSUPPORTED;
-    const EmulLayout L = emul_layout(M, N, K, nslices);
+    const EmulLayout L = emul_layout(M, N, K, nslices, sc.crt ? 1 : 4);
     if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
         return ALP_ERR_WORKSPACE;
     char* ws = static_cast<char*>(workspace);
@@ -538,8 +651,9 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
         return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e,
                                     f, M, N, alpha, beta, C, ldc);
     else if (sc.crt)
-        return launch_recombine_crt(nslices, kcrt, recombine_grid(M, N), s, G, M * L.ldg, L.ldg,
-                                    e, f, M, N, alpha, beta, C, ldc);
+        return launch_recombine_crt(nslices, kcrt, recombine_grid(M, N), s,
+                                    reinterpret_cast<const uint8_t*>(G), M * L.ldg, L.ldg, e, f,
+                                    M, N, alpha, beta, C, ldc);
     else
         return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f,
                                 M, N, alpha, beta, C, ldc);
@@ -556,7 +670,7 @@ size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
     EmulScheme sc;
     if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || !emul_slices_ok(sc, nslices, false))
         return 0;
-    return emul_layout(M, N, K, nslices).bytes;
+    return emul_layout(M, N, K, nslices, sc.crt ? 1 : 4).bytes;
 }
 
 alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,
@@ -609,7 +723,7 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
 
 alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind, const void* da_bf16, const void* db_bf16,
-                                   int64_t kpad, int32_t* G, int64_t ldg, void* stream) {
+                                   int64_t kpad, void* G, int64_t ldg, void* stream) {
     EmulScheme sc;
     if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) ||
         (sc.crt ? !emul_slices_ok(sc, nslices, false)
@@ -617,9 +731,10 @@ alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,
         kpad < K || kpad % kEmulBK || ldg < N || ldg % 256 || K > emul_scheme_max_k(sc))
         return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0 || K == 0) return ALP_OK;
-    if (!da_bf16 || !db_bf16 || !G) return ALP_ERR_INVALID_ARG;
+    if (!da_bf16 || !db_bf16 || !G || ((uintptr_t)G & 15)) return ALP_ERR_INVALID_ARG;
     return emul_slice_gemm(M, N, K, nslices, reinterpret_cast<const __nv_bfloat16*>(da_bf16),
-                           reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, G, ldg,
+                           reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad,
+                           static_cast<int32_t*>(G), ldg,
                            reinterpret_cast<cudaStream_t>(stream), 0, 0, sc.b, sc.trim, sc.crt);
 }
 
@@ -643,18 +758,18 @@ int alp_emul_crt_bits(int64_t K, int nmoduli) {
 }
 
 alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
-                                  const int32_t* G, int64_t ldg, const int32_t* e,
+                                  const uint8_t* R, int64_t ldr, const int32_t* e,
                                   const int32_t* f, double alpha, double beta, double* C,
                                   int64_t ldc, void* stream) {
     if (M < 0 || N < 0 || K < 0 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli ||
-        ldg < N || ldc < N)
+        ldr < N || ldc < N)
         return ALP_ERR_INVALID_ARG;
     const int k = alp_emul_crt_bits(K, nmoduli);
     if (k < 1) return ALP_ERR_UNSUPPORTED;
     if (M == 0 || N == 0) return ALP_OK;
-    if (!G || !e || !f || !C) return ALP_ERR_INVALID_ARG;
+    if (!R || !e || !f || !C) return ALP_ERR_INVALID_ARG;
     return launch_recombine_crt(nmoduli, k, recombine_grid(M, N),
-                                reinterpret_cast<cudaStream_t>(stream), G, M * ldg, ldg, e, f, M,
+                                reinterpret_cast<cudaStream_t>(stream), R, M * ldr, ldr, e, f, M,
                                 N, alpha, beta, C, ldc);
 }
 

@@ -48,12 +48,14 @@ inline bool emul_scheme_of(int kind, EmulScheme* sc) {
 constexpr int kCrtMinModuli = 4;
 constexpr int kCrtMaxModuli = 16;
 int crt_bits(int64_t K, int n);
+// y_l = (Mn / m_l)^-1 mod m_l for the first n moduli (host).
+uint32_t crt_weight(int n, int l);
 template <typename T>
 alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int trans,
                           const int32_t* exps, int n, __nv_bfloat16* out, int64_t kpad, int k,
                           cudaStream_t st);
-alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const int32_t* G,
-                                int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
+alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const uint8_t* R,
+                                int64_t rplane, int64_t ldr, const int32_t* e, const int32_t* f,
                                 int64_t M, int64_t N, double alpha, double beta, double* C,
                                 int64_t ldc);
 // Slice counts a GEMM call accepts: 3..emul_max_slices(b) digits for FP64,
@@ -78,7 +80,9 @@ struct EmulLayout {
     size_t off_da, off_db, off_g, off_e, off_f, bytes;
 };
 
-EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s);
+// gbytes: bytes per element of G (4: int32 group sums; 1: the modular
+// scheme's residues).
+EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s, int gbytes = 4);
 
 // Block arrangement of the slice-product kernel: one block per 128 x 256
 // tile, two blocks (a cluster) sharing each B tile by multicast, or a CTA pair

@@ -5,52 +5,17 @@
 // pairwise coprime moduli m_l <= 256: the residues of A' and B' (in
 // [-128, 127], exact in bf16) are multiplied on the tensor cores by the
 // slice-product kernel (one product per modulus instead of one per digit
-// pair), and P follows by the Chinese remainder theorem, exactly, because
+// pair; the epilogue reduces each sum to P mod m_l, one byte), and P follows
+// by the Chinese remainder theorem, exactly, because
 // |P| <= K 2^(2k) <= M / 4 with M = m_1 ... m_n.  C = alpha RN(P 2^(e_i + f_j
 // - 2k)) (+ fma(beta, C, .)).
 #include <cstdint>
 
+#include "crt.cuh"
 #include "emul.cuh"
 #include "emul_split.cuh"
 
 namespace alp {
-
-// The moduli, largest first (pairwise coprime; 256 = 2^8 first).
-__host__ __device__ __forceinline__ constexpr uint32_t crt_modulus(int l) {
-    switch (l) {
-        case 0: return 256u;
-        case 1: return 255u;
-        case 2: return 253u;
-        case 3: return 251u;
-        case 4: return 247u;
-        case 5: return 241u;
-        case 6: return 239u;
-        case 7: return 233u;
-        case 8: return 229u;
-        case 9: return 227u;
-        case 10: return 223u;
-        case 11: return 217u;
-        case 12: return 211u;
-        case 13: return 199u;
-        case 14: return 197u;
-        case 15: return 193u;
-        default: return 1u;
-    }
-}
-// 2^bits mod m.
-__host__ __device__ __forceinline__ constexpr uint32_t crt_pow2_mod(int bits, uint32_t m) {
-    uint32_t r = 1u % m;
-    for (int i = 0; i < bits; ++i) r = (r * 2u) % m;
-    return r;
-}
-// x mod m for x < 2^30: q = floor(x ceil(2^38 / m) / 2^38) is exact for m <= 255
-// (the product over-estimates x / m by less than 2^-8, and x mod m <= m - 1
-// keeps the fraction below 1 - 1/m); m = 256 is a mask.
-__device__ __forceinline__ uint32_t crt_mod(uint32_t x, uint32_t m) {
-    if (m == 256u) return x & 255u;
-    const uint32_t magic = (uint32_t)(((1ull << 38) + m - 1) / m);
-    return x - (__umulhi(x, magic) >> 6) * m;
-}
 
 // P must satisfy K 2^(2k + 2) <= M (so |P| <= M / 4); the largest such k <= 60.
 int crt_bits(int64_t K, int n) {
@@ -65,6 +30,17 @@ int crt_bits(int64_t K, int n) {
         if (sh + kbits > 127) continue;                      // K 2^sh > 2^126 > M
         if (((unsigned __int128)Kc << sh) <= M) return k;
     }
+    return 0;
+}
+
+uint32_t crt_weight(int n, int l) {
+    if (n < 1 || n > kCrtMaxModuli || l < 0 || l >= n) return 0;
+    const uint32_t m = crt_modulus(l);
+    uint32_t r = 1;   // Mn / m_l mod m_l = prod_{i != l} m_i mod m_l
+    for (int i = 0; i < n; ++i)
+        if (i != l) r = (r * (crt_modulus(i) % m)) % m;
+    for (uint32_t y = 1; y < m; ++y)
+        if ((r * y) % m == 1u) return y;
     return 0;
 }
 
@@ -137,13 +113,12 @@ template alp_status emul_split_crt<double>(int64_t, int64_t, const double*, int6
                                            const int32_t*, int, __nv_bfloat16*, int64_t, int,
                                            cudaStream_t);
 
-// Chinese remainder reconstruction constants for n moduli: M = prod m_l,
-// M_l = M / m_l (two 64-bit limbs), y_l = (M_l mod m_l)^-1 mod m_l, 1 / m_l.
+// Chinese remainder reconstruction constants for n moduli: Mn = prod m_l and
+// M_l = Mn / m_l as four 32-bit limbs, and F_l = round(2^32 / m_l).
 struct CrtRecConsts {
-    uint64_t ml_lo[kCrtMaxModuli], ml_hi[kCrtMaxModuli];
-    uint64_t mm_lo, mm_hi;
-    uint32_t y[kCrtMaxModuli];
-    float inv[kCrtMaxModuli];
+    uint32_t ml[kCrtMaxModuli][4];
+    uint32_t mn[4];
+    uint32_t F[kCrtMaxModuli];
     int k;
 };
 
@@ -151,107 +126,109 @@ static CrtRecConsts crt_consts(int n, int k) {
     CrtRecConsts c{};
     unsigned __int128 M = 1;
     for (int l = 0; l < n; ++l) M *= crt_modulus(l);
-    c.mm_lo = (uint64_t)M;
-    c.mm_hi = (uint64_t)(M >> 64);
+    for (int i = 0; i < 4; ++i) c.mn[i] = (uint32_t)(M >> (32 * i));
     for (int l = 0; l < n; ++l) {
         const uint32_t m = crt_modulus(l);
         const unsigned __int128 Ml = M / m;
-        c.ml_lo[l] = (uint64_t)Ml;
-        c.ml_hi[l] = (uint64_t)(Ml >> 64);
-        const uint32_t r = (uint32_t)(Ml % m);
-        uint32_t y = 0;
-        for (uint32_t t = 1; t < m; ++t)
-            if ((r * t) % m == 1u) { y = t; break; }
-        c.y[l] = y;
-        c.inv[l] = 1.0f / (float)m;
+        for (int i = 0; i < 4; ++i) c.ml[l][i] = (uint32_t)(Ml >> (32 * i));
+        c.F[l] = (uint32_t)(((1ull << 32) + m / 2) / m);
     }
     c.k = k;
     return c;
 }
 
-// acc += x * (hi:lo) for a small x, modulo 2^128.
-__device__ __forceinline__ void mad_u128(uint64_t& acc_lo, uint64_t& acc_hi, uint32_t x,
-                                         uint64_t lo, uint64_t hi) {
-    const uint64_t p_lo = lo * x, p_mid = __umul64hi(lo, x), p_hi = hi * x + p_mid;
-    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;"
-        : "+l"(acc_lo), "+l"(acc_hi)
-        : "l"(p_lo), "l"(p_hi));
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
 }
 
-// Four columns per thread as the digit-scheme recombination: the n group
-// sums Q_l (int32, Q_l = P mod m_l up to multiples of m_l) of four adjacent
-// columns arrive as one 16-byte load per plane.
+// Four columns per thread: the n bytes x_l = (P y_l) mod m_l (four adjacent
+// columns in one 32-bit load per plane) give sum_l x_l M_l = P + c Mn for the
+// integer c = round(sum_l x_l / m_l)
+// (|P| / Mn <= 1/4).  The sum is kept as four 64-bit column sums of 32-bit
+// limbs (each below 16 * 2^8 * 2^32), c from a 32.32 fixed-point sum whose
+// error is below 2^-21, and P = sum - c Mn follows by one carry pass, exact
+// modulo 2^128, which holds it.
 template <int S>
 __global__ void __launch_bounds__(256) recombine_crt_kernel(
-    const int32_t* __restrict__ G, int64_t gplane, int64_t ldg, const int32_t* __restrict__ e,
+    const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
     const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
-    double* __restrict__ C, int64_t ldc, bool gvec, const CrtRecConsts cc) {
+    double* __restrict__ C, int64_t ldc, bool rvec, const CrtRecConsts cc) {
     for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
         const int ei = e[i] - 2 * cc.k;
-        const int32_t* gi = G + i * ldg;
+        const uint8_t* ri = R + i * ldr;
         double* ci = C + i * ldc;
         const bool cvec = (reinterpret_cast<uintptr_t>(ci) & 15) == 0;
         for (int64_t j = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N;
              j += 4 * (int64_t)gridDim.x * blockDim.x) {
-            int4 v[S];
+            uint32_t v[S];
 #pragma unroll
             for (int t = 0; t < S; ++t) {
-                const int32_t* g = gi + (int64_t)t * gplane + j;
-                if (gvec) v[t] = __ldg(reinterpret_cast<const int4*>(g));
-                else v[t] = make_int4(__ldg(g), __ldg(g + 1), __ldg(g + 2), __ldg(g + 3));
+                const uint8_t* g = ri + (int64_t)t * rplane + j;
+                if (rvec) v[t] = __ldg(reinterpret_cast<const uint32_t*>(g));
+                else
+                    v[t] = (uint32_t)__ldg(g) | (uint32_t)__ldg(g + 1) << 8 |
+                           (uint32_t)__ldg(g + 2) << 16 | (uint32_t)__ldg(g + 3) << 24;
             }
-            double out[4];
-#pragma unroll
+            double o0 = 0.0, o1 = 0.0, o2 = 0.0, o3 = 0.0;   // not an array: u is a runtime index
+#pragma unroll 1
             for (int u = 0; u < 4; ++u) {
                 if (j + u >= N) break;
-                uint64_t lo = 0, hi = 0;
-                float q = 0.0f;
+                uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, qa = 0;
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    const int32_t Q = u == 0 ? v[t].x : u == 1 ? v[t].y : u == 2 ? v[t].z : v[t].w;
-                    const uint32_t m = crt_modulus(t);
-                    uint32_t r = crt_mod(Q < 0 ? (uint32_t)(-(int64_t)Q) : (uint32_t)Q, m);
-                    if (Q < 0 && r) r = m - r;
-                    const uint32_t x = crt_mod(r * cc.y[t], m);
-                    mad_u128(lo, hi, x, cc.ml_lo[t], cc.ml_hi[t]);
-                    q = __fmaf_rn((float)x, cc.inv[t], q);
+                    const uint32_t x = (v[t] >> (8 * u)) & 255u;
+                    a0 = mad_wide(x, cc.ml[t][0], a0);
+                    a1 = mad_wide(x, cc.ml[t][1], a1);
+                    a2 = mad_wide(x, cc.ml[t][2], a2);
+                    a3 = mad_wide(x, cc.ml[t][3], a3);
+                    qa = mad_wide(x, cc.F[t], qa);
                 }
-                // sum x_l M_l = M (q_int + P / M) with |P| / M <= 1/4: subtract M rint(q)
-                const uint32_t qi = (uint32_t)__float2int_rn(q);
-                uint64_t s_lo = 0, s_hi = 0;
-                mad_u128(s_lo, s_hi, qi, cc.mm_lo, cc.mm_hi);
-                asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;"
-                    : "+l"(lo), "+l"(hi)
-                    : "l"(s_lo), "l"(s_hi));
-                const double w = i128_scaled_to_double_rn((int64_t)hi, lo, ei + __ldg(f + j + u));
+                const uint32_t qi = (uint32_t)((qa + 0x80000000ull) >> 32);
+                int64_t c = (int64_t)a0 - (int64_t)((uint64_t)qi * cc.mn[0]);
+                const uint32_t w0 = (uint32_t)c;
+                c = (c >> 32) + (int64_t)a1 - (int64_t)((uint64_t)qi * cc.mn[1]);
+                const uint32_t w1 = (uint32_t)c;
+                c = (c >> 32) + (int64_t)a2 - (int64_t)((uint64_t)qi * cc.mn[2]);
+                const uint32_t w2 = (uint32_t)c;
+                c = (c >> 32) + (int64_t)a3 - (int64_t)((uint64_t)qi * cc.mn[3]);
+                const uint32_t w3 = (uint32_t)c;
+                const int64_t hi = (int64_t)(((uint64_t)w3 << 32) | w2);
+                const uint64_t lo = ((uint64_t)w1 << 32) | w0;
+                const double w = i128_scaled_to_double_rn(hi, lo, ei + __ldg(f + j + u));
                 double o = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
                 if (beta != 0.0) o = __fma_rn(beta, ci[j + u], o);
-                out[u] = o;
+                o0 = u == 0 ? o : o0;
+                o1 = u == 1 ? o : o1;
+                o2 = u == 2 ? o : o2;
+                o3 = u == 3 ? o : o3;
             }
             if (cvec && j + 3 < N) {
-                reinterpret_cast<double2*>(ci + j)[0] = make_double2(out[0], out[1]);
-                reinterpret_cast<double2*>(ci + j)[1] = make_double2(out[2], out[3]);
+                reinterpret_cast<double2*>(ci + j)[0] = make_double2(o0, o1);
+                reinterpret_cast<double2*>(ci + j)[1] = make_double2(o2, o3);
             } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (j + u < N) ci[j + u] = out[u];
+                ci[j] = o0;
+                if (j + 1 < N) ci[j + 1] = o1;
+                if (j + 2 < N) ci[j + 2] = o2;
+                if (j + 3 < N) ci[j + 3] = o3;
             }
         }
     }
 }
 
-alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const int32_t* G,
-                                int64_t gplane, int64_t ldg, const int32_t* e, const int32_t* f,
+alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const uint8_t* R,
+                                int64_t rplane, int64_t ldr, const int32_t* e, const int32_t* f,
                                 int64_t M, int64_t N, double alpha, double beta, double* C,
                                 int64_t ldc) {
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtRecConsts cc = crt_consts(n, k);
-    const bool gvec = (reinterpret_cast<uintptr_t>(G) & 15) == 0 && gplane % 4 == 0 && ldg % 4 == 0;
+    const bool rvec = (reinterpret_cast<uintptr_t>(R) & 3) == 0 && rplane % 4 == 0 && ldr % 4 == 0;
     grid.x = (unsigned)((grid.x + 1) / 2);   // four columns per thread
 #define ALP_CRT_REC_CASE(x)                                                                       \
     case x:                                                                                      \
-        recombine_crt_kernel<x><<<grid, 256, 0, st>>>(G, gplane, ldg, e, f, M, N, alpha, beta, C, \
-                                                      ldc, gvec, cc);                            \
+        recombine_crt_kernel<x><<<grid, 256, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
+                                                      ldc, rvec, cc);                            \
         break;
     switch (n) {
         ALP_CRT_REC_CASE(4) ALP_CRT_REC_CASE(5) ALP_CRT_REC_CASE(6) ALP_CRT_REC_CASE(7)

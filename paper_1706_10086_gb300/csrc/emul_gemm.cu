@@ -25,6 +25,7 @@
 // group the block writes S^t to G[t-2] (int32).
 #include <cstdlib>
 
+#include "crt.cuh"
 #include "emul.cuh"
 #include "tc.cuh"
 
@@ -102,6 +103,8 @@ struct EmulGemmParams {
     uint64_t t_ranges;
     uint64_t timeout_ns;
     int* err;
+    // modular scheme: y_l = (Mn / m_l)^-1 mod m_l, the weight of residue l
+    uint8_t crt_y[kCrtMaxModuli];
 };
 
 // K chunk of pair (p, q): the largest multiple of 64 with |partial sums| <= 2^24,
@@ -205,9 +208,33 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
             else mbar_arrive(&acce[b]);
         }
         const uint32_t jd = jobs[job];
-        if (job_last(jd)) {
-            // plane of G: t - 2 for the digit pair (p, q), t = p + q; l - 1 for modulus l
-            t_group = prm.crt ? job_p(jd) + 1 : job_p(jd) + job_q(jd);
+        if (job_last(jd) && prm.crt) {
+            // modular scheme: plane l of modulus m_l receives x = (Q y_l) mod
+            // m_l = (P y_l) mod m_l, one byte per column (rows padded as below)
+            const int l = job_p(jd) - 1;
+            const uint32_t m = crt_modulus(l), magic = crt_magic(m), y = prm.crt_y[l];
+            uint8_t* g = reinterpret_cast<uint8_t*>(prm.G) + (int64_t)l * prm.gplane +
+                         (int64_t)gm * prm.ldg + n0 + half * 128;
+            const uint32_t do_store = gm < prm.M ? 1u : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = 16 * i + 4 * q;
+                    w[q] = crt_mod(crt_residue((int32_t)acc[c], m, magic) * y, m, magic) |
+                           crt_mod(crt_residue((int32_t)acc[c + 1], m, magic) * y, m, magic) << 8 |
+                           crt_mod(crt_residue((int32_t)acc[c + 2], m, magic) * y, m, magic) << 16 |
+                           crt_mod(crt_residue((int32_t)acc[c + 3], m, magic) * y, m, magic) << 24;
+                }
+                store4_and_zero(reinterpret_cast<int32_t*>(g + 16 * i), do_store, w[0], w[1],
+                                w[2], w[3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 128; ++i) acc[i] = 0;
+        } else if (job_last(jd)) {
+            // plane of G: t - 2 for the digit pair (p, q), t = p + q
+            t_group = job_p(jd) + job_q(jd);
             // G rows are padded to whole 256-column tiles, so the strip is in
             // bounds; rows past M are not stored.  Each asm block stores acc
             // and zeroes it in place.
@@ -672,6 +699,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.digit_bits = digit_bits;
     p.trim = trim ? 1 : 0;
     p.crt = crt ? 1 : 0;
+    for (int l = 0; l < kCrtMaxModuli; ++l) p.crt_y[l] = crt && l < s ? crt_weight(s, l) : 0;
     p.G = G;
     p.ldg = ldg;
     p.gplane = M * ldg;

@@ -32,6 +32,14 @@ def crt_k(K, n):
     return 0
 
 
+def crt_weights(n):
+    """y_l = (Mn / m_l)^-1 mod m_l, the weight of residue l."""
+    Mn = 1
+    for m in MODULI[:n]:
+        Mn *= m
+    return [pow(Mn // m % m, -1, m) for m in MODULI[:n]]
+
+
 def run_crt(alp, A, B, C, alpha, beta, n, lda=None, ldc=None, raise_on_error=True):
     import torch
     M, K = A.shape
@@ -195,8 +203,8 @@ def residue(x, m):
 def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
     """alp_emul_split with the modular kind writes the residues of the scaled
     integers (rows of A; columns of B via trans = 1); alp_emul_slice_products
-    writes Q_l = sum_k a_l b_l exactly; alp_emul_recombine_crt turns them into
-    the oracle's result."""
+    writes the byte ((sum_k a_l b_l) y_l) mod m_l = (P y_l) mod m_l;
+    alp_emul_recombine_crt turns those into the oracle's result."""
     import torch
     M, N, K = 200, 300, 1100
     kpad = (K + 63) // 64 * 64
@@ -220,12 +228,15 @@ def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
         assert np.array_equal(rb[l, :, :K], residue(Bi.T, MODULI[l])), l
     assert np.all(ra[:, :, K:] == 0) and np.all(rb[:, :, K:] == 0)
     ldg = (N + 255) // 256 * 256
-    G = torch.full((n, M, ldg), 12345, dtype=torch.int32, device="cuda")
+    G = torch.full((n, M, ldg), 255, dtype=torch.uint8, device="cuda")
     alp.alp_emul_slice_products(M, N, K, n, CRT, da, db, kpad, G, ldg)
     torch.cuda.synchronize()
     g = G.cpu().numpy()
+    y = crt_weights(n)
     for l in range(n):
-        assert np.array_equal(g[l, :, :N], ra[l, :, :K] @ rb[l, :, :K].T), l
+        Q = ra[l, :, :K] @ rb[l, :, :K].T
+        assert np.abs(Q).max() <= K * 2 ** 14
+        assert np.array_equal(g[l, :, :N], np.mod(np.mod(Q, MODULI[l]) * y[l], MODULI[l])), l
     dC = torch.from_numpy(C.copy()).cuda()
     alp.alp_emul_recombine_crt(M, N, K, n, G, ldg, de, df, 1.5, 0.5, dC, N)
     torch.cuda.synchronize()
@@ -236,9 +247,8 @@ def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
 
 @pytest.mark.parametrize("n", [4, 9, 15, 16])
 def test_crt_recombine_rounding(alp, n):
-    """alp_emul_recombine_crt on crafted residue sums: P anywhere in
-    [-Mn/4, Mn/4] (the ends included), given as Q_l = P mod m_l plus random
-    multiples of m_l with |Q_l| < 2^30 (the documented range), with tails that are exact ties, just off a
+    """alp_emul_recombine_crt on crafted residues: P anywhere in [-Mn/4, Mn/4]
+    (the ends included), given as the bytes (P y_l) mod m_l, with tails that are exact ties, just off a
     tie, or carry one sticky bit; each result must be the correctly rounded
     alpha-free value P 2^(e_i + f_j - 2k) (Python's exact rational rounding)."""
     import random
@@ -266,11 +276,11 @@ def test_crt_recombine_rounding(alp, n):
     N = len(vals)
     ldg = (N + 255) // 256 * 256
     rows = 3
-    G = np.zeros((n, rows, ldg), dtype=np.int32)
+    G = np.zeros((n, rows, ldg), dtype=np.uint8)
+    y = crt_weights(n)
     for j, P in enumerate(vals):
         for l, m in enumerate(MODULI[:n]):
-            for r in range(rows):
-                G[l, r, j] = P % m + m * rnd.randrange(-(2 ** 30) // m + 1, 2 ** 30 // m - 1)
+            G[l, :, j] = P * y[l] % m
     e = np.array([0, 5, -40], dtype=np.int32)
     f = np.array([rnd.randrange(-8, 9) for _ in range(N)], dtype=np.int32)
     dC = torch.full((rows, N), float("nan"), dtype=torch.float64, device="cuda")

@@ -64,6 +64,57 @@ def test_exponents_match_oracle(alp, orc):
     assert alp.alp_get_device_error() == alp.ALP_OK
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("off,ld_pad,R,K", [(0, 0, 37, 1000), (1, 3, 37, 1001), (3, 0, 5, 7),
+                                            (0, 1, 9, 2), (2, 2, 300, 515)])
+def test_exponents_vector_and_ragged_paths(alp, orc, dtype, off, ld_pad, R, K):
+    """Row and column scans on views whose base is off elements past a 16-byte
+    boundary and whose leading dimension is padded: the aligned vector body,
+    the unaligned head, the ragged tail and the element-by-element column
+    path; one Inf and one NaN are reported and do not affect other rows."""
+    import torch
+    X = inputs.scaled(3003 + off + K, 0, (R, K), phi=40)
+    X[1] = 0.0
+    X[2, K - 1] = 2.0 ** 600 if dtype == "f64" else 2.0 ** 100
+    X[3, 0] = -(2.0 ** -1060) if dtype == "f64" else -(2.0 ** -140)
+    X[3, 1:] = 0.0
+    npdt = np.float64 if dtype == "f64" else np.float32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Xc = X.astype(npdt)
+    ld = K + ld_pad
+    buf = torch.zeros(off + R * ld + 8, dtype=tdt, device="cuda")
+    view = buf[off:off + R * ld].view(R, ld)
+    view[:, :K] = torch.from_numpy(Xc)
+    scan = alp.alp_emul_exponents if dtype == "f64" else alp.alp_emul_exponents_f32
+    e = torch.empty(R, dtype=torch.int32, device="cuda")
+    scan(R, K, view, ld, 0, e)
+    torch.cuda.synchronize()
+    ref, _ = orc.row_exponents(Xc.astype(np.float64))
+    assert np.array_equal(e.cpu().numpy(), ref)
+    # the same values stored K x R (columns), leading dimension ld2
+    XT = np.ascontiguousarray(Xc.T)
+    ld2 = R + ld_pad
+    buf2 = torch.zeros(off + K * ld2 + 8, dtype=tdt, device="cuda")
+    view2 = buf2[off:off + K * ld2].view(K, ld2)
+    view2[:, :R] = torch.from_numpy(XT)
+    f = torch.empty(R, dtype=torch.int32, device="cuda")
+    scan(R, K, view2, ld2, 1, f)
+    torch.cuda.synchronize()
+    assert np.array_equal(f.cpu().numpy(), ref)
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    view[4, K // 2] = float("inf")
+    view2[K // 2, 4] = float("nan")
+    scan(R, K, view, ld, 0, e)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_ERR_UNSUPPORTED
+    got = e.cpu().numpy()
+    assert np.array_equal(np.delete(got, 4), np.delete(ref, 4))
+    scan(R, K, view2, ld2, 1, f)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_ERR_UNSUPPORTED
+    assert np.array_equal(np.delete(f.cpu().numpy(), 4), np.delete(ref, 4))
+
+
 @pytest.mark.parametrize("phi", [0, 8, 32])
 @pytest.mark.parametrize("s,kind", [(8, "b7"), (7, "b8"), (3, "b8"), (7, "b8t")])
 def test_split_matches_oracle(alp, orc, phi, s, kind):
