@@ -41,8 +41,8 @@ if ROOT not in sys.path:
 METRIC = "FP64-accurate GEMM TFLOP/s (native vs emulated) and % of peak at N=8192"
 UNIT = "TFLOP/s"
 KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_gb300/csrc/tc.cuh",
-                  "paper_1706_10086_gb300/csrc/emul.cuh")
-TRAFFIC_PROFILE = "profiles/emul_gemm_kernel_8192.md"
+                  "paper_1706_10086_gb300/csrc/emul.cuh", "paper_1706_10086_gb300/csrc/crt.cuh")
+TRAFFIC_PROFILES = "profiles/emul_gemm_kernel_8192_*.md"
 # slice kinds of alp_gemm_f64_emul: name -> (enum value, digit pairs for s slices)
 KINDS = {"bf16": (1, lambda s: s * (s + 1) // 2), "bf16_b8": (2, lambda s: s * (s + 1) // 2),
          "bf16_b8_trim": (3, lambda s: s * (s - 1) // 2 + 2), "bf16_crt": (4, lambda s: s)}
@@ -56,12 +56,10 @@ def parse_args():
     ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--nslices", type=int, default=None,
-                    help="digit slices (moduli for bf16_crt); default 7, or 15 for bf16_crt. "
-                         "With the default kind 7 is no less accurate than native FP64 for "
-                         "the default uniform inputs (checked live against 8 slices of 7-bit "
-                         "digits); wide exponent ranges need --kind bf16 with 8 or --kind "
-                         "bf16_b8 with 7")
-    ap.add_argument("--kind", choices=tuple(KINDS), default="bf16_b8_trim",
+                    help="moduli for bf16_crt (default 15: more accurate than native FP64 "
+                         "for the default uniform inputs, checked live against 8 slices of "
+                         "7-bit digits), digit slices for the other kinds (default 7)")
+    ap.add_argument("--kind", choices=tuple(KINDS), default="bf16_crt",
                     help="scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
                          "up to 7), bf16_b8_trim (8-bit, last group keeps only its two "
                          "leading-digit pairs), bf16_crt (residues modulo 4..16 moduli, one "
@@ -131,25 +129,22 @@ def kernel_source_hash():
 
 
 def profiled_traffic(workload):
-    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
-    summary, if it was taken on the current kernel source and this workload;
-    else None."""
-    path = os.path.join(ROOT, TRAFFIC_PROFILE)
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_hash") != kernel_source_hash() or vals.get("workload") != workload:
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
+    """DRAM bytes per launch of the tensor-core kernel from a committed ncu
+    summary taken on the current kernel source and this workload; else None."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, TRAFFIC_PROFILES))):
+        vals = {}
+        for line in open(path).read().splitlines():
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+        if (vals.get("kernel_source_hash") == kernel_source_hash()
+                and vals.get("workload") == workload):
+            try:
+                return float(vals["dram_bytes_per_launch_full_size"])
+            except (KeyError, ValueError):
+                return None
+    return None
 
 
 class ClockSampler:
