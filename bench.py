@@ -40,6 +40,7 @@ if ROOT not in sys.path:
 
 METRIC = "FP64-accurate GEMM TFLOP/s (native vs emulated) and % of peak at N=8192"
 UNIT = "TFLOP/s"
+NOMINAL_BF16_TFLOPS = 2250.0   # dense bf16 tensor rate of one GB300 (nominal)
 KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_gb300/csrc/tc.cuh",
                   "paper_1706_10086_gb300/csrc/emul.cuh", "paper_1706_10086_gb300/csrc/crt.cuh")
 TRAFFIC_PROFILES = "profiles/emul_gemm_kernel_8192_*.md"
@@ -128,9 +129,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the tensor-core kernel from a committed ncu
-    summary taken on the current kernel source and this workload; else None."""
+def profiled_values(workload):
+    """The `- key: value` lines of the committed ncu summary taken on the
+    current kernel source and this workload ({} if there is none)."""
     import glob
     for path in sorted(glob.glob(os.path.join(ROOT, TRAFFIC_PROFILES))):
         vals = {}
@@ -140,11 +141,26 @@ def profiled_traffic(workload):
                 vals[k.strip()] = v.strip().strip("`")
         if (vals.get("kernel_source_hash") == kernel_source_hash()
                 and vals.get("workload") == workload):
-            try:
-                return float(vals["dram_bytes_per_launch_full_size"])
-            except (KeyError, ValueError):
-                return None
-    return None
+            return vals
+    return {}
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the tensor-core kernel from a committed ncu
+    summary taken on the current kernel source and this workload; else None."""
+    try:
+        return float(profiled_values(workload)["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def profiled_tensor_active(workload):
+    """sm__pipe_tensor_cycles_active (% of the hardware peak) from the same
+    summary, or None."""
+    try:
+        return float(profiled_values(workload)["sm__pipe_tensor_cycles_active"].split()[0])
+    except (KeyError, ValueError, IndexError):
+        return None
 
 
 class ClockSampler:
@@ -335,7 +351,12 @@ def run_alp(args):
                 "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
                 "algorithmic_flops_per_launch": pairs * 2.0 * M * N * K,
                 "kernel_ms": round(kern_avg, 3),
-                "traffic": profiled_traffic(workload_name(n, s, args.kind, phi))}
+                "traffic": profiled_traffic(workload_name(n, s, args.kind, phi)),
+                # the measured peak is the library GEMM's; against the nominal
+                # dense bf16 rate and the tensor pipe's own activity counter
+                "nominal_peak": NOMINAL_BF16_TFLOPS,
+                "frac_of_nominal": round(achieved / NOMINAL_BF16_TFLOPS, 4),
+                "tensor_active_pct_ncu": profiled_tensor_active(workload_name(n, s, args.kind, phi))}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": max(3, args.warmup),

@@ -79,8 +79,10 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtSplit sp{k};
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
-    const int64_t bx = (kpad + 1023) / 1024;
-    int64_t by = (int64_t)device_sm_count() * 8 / bx;
+    // 128-thread blocks (4 k per thread): small enough to run beside the
+    // tensor-core kernel's blocks when the two overlap on different streams
+    const int64_t bx = (kpad + 511) / 512;
+    int64_t by = (int64_t)device_sm_count() * 16 / bx;
     by = by < 1 ? 1 : by > R ? R : by > 65535 ? 65535 : by;
     const dim3 grid4((unsigned)bx, (unsigned)by);
     int64_t blocks = (R * (kpad / 2) + 255) / 256;
@@ -89,7 +91,7 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
 #define ALP_CRT_SPLIT_CASE(x)                                                                    \
     case x:                                                                                      \
         if (!trans && vec)                                                                       \
-            split_rows4_kernel<T, x, CrtSplit><<<grid4, 256, 0, st>>>(X, R, K, ldx, exps, out,    \
+            split_rows4_kernel<T, x, CrtSplit><<<grid4, 128, 0, st>>>(X, R, K, ldx, exps, out,    \
                                                                       kpad, sp);                  \
         else if (!trans)                                                                         \
             split_rows_kernel<T, x, CrtSplit><<<(unsigned)blocks, 256, 0, st>>>(                  \
@@ -151,7 +153,7 @@ __device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
 // error is below 2^-21, and P = sum - c Mn follows by one carry pass, exact
 // modulo 2^128, which holds it.
 template <int S>
-__global__ void __launch_bounds__(256) recombine_crt_kernel(
+__global__ void __launch_bounds__(128) recombine_crt_kernel(
     const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
     const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
     double* __restrict__ C, int64_t ldc, bool rvec, const CrtRecConsts cc) {
@@ -224,10 +226,12 @@ alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const 
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtRecConsts cc = crt_consts(n, k);
     const bool rvec = (reinterpret_cast<uintptr_t>(R) & 3) == 0 && rplane % 4 == 0 && ldr % 4 == 0;
-    grid.x = (unsigned)((grid.x + 1) / 2);   // four columns per thread
+    // four columns per thread, 128-thread blocks: 512 columns per block, as
+    // the grid was sized; small enough to run beside the tensor-core kernel's
+    // blocks when the two overlap on different streams
 #define ALP_CRT_REC_CASE(x)                                                                       \
     case x:                                                                                      \
-        recombine_crt_kernel<x><<<grid, 256, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
+        recombine_crt_kernel<x><<<grid, 128, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
                                                       ldc, rvec, cc);                            \
         break;
     switch (n) {
