@@ -254,6 +254,41 @@ alp_status alp_gemm_f32_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, 
                                 int64_t ldb, float beta, float* C, int64_t ldc, int nslices,
                                 alp_slice_kind kind, void* workspace, size_t workspace_bytes,
                                 void* stream);
+/*
+ * Column-major (BLAS) entry points: C = alpha op(A) op(B) + beta C with every
+ * matrix column-major: op(A) is M x K with A stored M x K (lda >= M) for
+ * trans_a = 0 or K x M (lda >= K) for trans_a = 1; op(B) is K x N with B
+ * stored K x N (ldb >= K) or N x K (ldb >= N); C is M x N (ldc >= M).  A
+ * column-major matrix is the row-major storage of its transpose, so each call
+ * is the row-major call for C^T = op(B)^T op(A)^T: operands, M and N, and the
+ * two trans flags swapped (no data is moved for that; the native GEMM packs a
+ * row-major-transposed operand as alp_gemm_f64_ex does).  The emulated
+ * results equal, bit for bit, those of the row-major calls on the same
+ * matrices (each element's scaling exponents and exact product are the same);
+ * the native result has the same error bound.  Workspace: the row-major
+ * query with swapped arguments, which the *_cm_workspace calls return.
+ */
+alp_status alp_gemm_f64_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                           double alpha, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double beta, double* C, int64_t ldc,
+                           const alp_config* cfg, void* workspace, size_t workspace_bytes,
+                           void* stream);
+size_t alp_gemm_f64_cm_workspace(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K);
+alp_status alp_gemm_f64_emul_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                double alpha, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double beta, double* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream);
+size_t alp_gemm_f64_emul_cm_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                      alp_slice_kind kind);
+alp_status alp_gemm_f32_emul_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                float alpha, const float* A, int64_t lda, const float* B,
+                                int64_t ldb, float beta, float* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream);
+size_t alp_gemm_f32_emul_cm_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                      alp_slice_kind kind);
+
 /* Its stages: the exponent scan and split of alp_emul_exponents and
  * alp_emul_split for float operands (values converted exactly to double), and
  * the FP32 recombination of alp_emul_slice_products' group sums. */

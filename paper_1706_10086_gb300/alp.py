@@ -89,6 +89,15 @@ _SIGS = {
                               _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_ex": ([_int, _int, _i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp,
                               _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f64_cm": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
+                         _i64, ctypes.POINTER(alp_config), _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f64_cm_workspace": ([_int, _int, _i64, _i64, _i64], ctypes.c_size_t),
+    "alp_gemm_f64_emul_cm": ([_int, _int, _i64, _i64, _i64, _f64, _vp, _i64, _vp, _i64, _f64, _vp,
+                              _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f64_emul_cm_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
+    "alp_gemm_f32_emul_cm": ([_int, _int, _i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp,
+                              _i64, _int, _int, _vp, ctypes.c_size_t, _vp], _int),
+    "alp_gemm_f32_emul_cm_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
     "alp_emul_exponents_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
     "alp_emul_split_f32": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _i64, _vp], _int),
     "alp_emul_recombine_f32": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f32, _f32, _vp, _i64,
@@ -300,6 +309,48 @@ def alp_gemm_f32_emul_ex(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta,
                                     _p(B), ldb, float(beta), _p(C), ldc, int(nslices), int(kind),
                                     _p(workspace), int(workspace_bytes), _s(stream))
     return _check(st, "alp_gemm_f32_emul_ex", raise_on_error)
+
+
+def alp_gemm_f64_cm(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cfg=None,
+                    workspace=None, workspace_bytes=0, stream=None, raise_on_error=True):
+    c = None
+    if cfg is not None:
+        c = cfg if isinstance(cfg, alp_config) else alp_config(*cfg)
+    st = lib().alp_gemm_f64_cm(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                               _p(B), ldb, float(beta), _p(C), ldc,
+                               ctypes.byref(c) if c is not None else None, _p(workspace),
+                               int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f64_cm", raise_on_error)
+
+
+def alp_gemm_f64_cm_workspace(trans_a, trans_b, M, N, K):
+    return int(lib().alp_gemm_f64_cm_workspace(int(trans_a), int(trans_b), M, N, K))
+
+
+def alp_gemm_f64_emul_cm(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                         nslices, kind=ALP_SLICE_BF16_CRT, workspace=None, workspace_bytes=0,
+                         stream=None, raise_on_error=True):
+    st = lib().alp_gemm_f64_emul_cm(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                                    _p(B), ldb, float(beta), _p(C), ldc, int(nslices), int(kind),
+                                    _p(workspace), int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f64_emul_cm", raise_on_error)
+
+
+def alp_gemm_f64_emul_cm_workspace(M, N, K, nslices, kind):
+    return int(lib().alp_gemm_f64_emul_cm_workspace(M, N, K, int(nslices), int(kind)))
+
+
+def alp_gemm_f32_emul_cm(trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                         nslices, kind=ALP_SLICE_BF16_B8, workspace=None, workspace_bytes=0,
+                         stream=None, raise_on_error=True):
+    st = lib().alp_gemm_f32_emul_cm(int(trans_a), int(trans_b), M, N, K, float(alpha), _p(A), lda,
+                                    _p(B), ldb, float(beta), _p(C), ldc, int(nslices), int(kind),
+                                    _p(workspace), int(workspace_bytes), _s(stream))
+    return _check(st, "alp_gemm_f32_emul_cm", raise_on_error)
+
+
+def alp_gemm_f32_emul_cm_workspace(M, N, K, nslices, kind):
+    return int(lib().alp_gemm_f32_emul_cm_workspace(M, N, K, int(nslices), int(kind)))
 
 
 def alp_emul_exponents_f32(rows, cols, X, ldx, trans, exps, stream=None, raise_on_error=True):

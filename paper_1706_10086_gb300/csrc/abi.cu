@@ -226,6 +226,20 @@ static size_t ex_bytes_b(int tb, int64_t K, int64_t N) {
     return tb ? (((size_t)K * (size_t)N * 8 + 255) & ~(size_t)255) : 0;
 }
 
+// Column-major calls: C^T = op(B)^T op(A)^T in row-major terms.
+size_t alp_gemm_f64_cm_workspace(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K) {
+    return alp_gemm_f64_ex_workspace(trans_b, trans_a, N, M, K);
+}
+
+alp_status alp_gemm_f64_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                           double alpha, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double beta, double* C, int64_t ldc,
+                           const alp_config* cfg, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+    return alp_gemm_f64_ex(trans_b, trans_a, N, M, K, alpha, B, ldb, A, lda, beta, C, ldc, cfg,
+                           workspace, workspace_bytes, stream);
+}
+
 size_t alp_gemm_f64_ex_workspace(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K) {
     if (M < 0 || N < 0 || K < 0 || (trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1))
         return 0;

@@ -861,4 +861,36 @@ alp_status alp_gemm_f32_emul_ex(int trans_a, int trans_b, int64_t M, int64_t N, 
                                  reinterpret_cast<cudaStream_t>(stream));
 }
 
+// ---- column-major calls: C^T = op(B)^T op(A)^T in row-major terms ----
+
+size_t alp_gemm_f64_emul_cm_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                      alp_slice_kind kind) {
+    return alp_gemm_f64_emul_workspace(N, M, K, nslices, kind);
+}
+
+alp_status alp_gemm_f64_emul_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                double alpha, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double beta, double* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    return emul_gemm_impl<double>(trans_b, trans_a, N, M, K, alpha, B, ldb, A, lda, beta, C, ldc,
+                                  nslices, kind, workspace, workspace_bytes,
+                                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t alp_gemm_f32_emul_cm_workspace(int64_t M, int64_t N, int64_t K, int nslices,
+                                      alp_slice_kind kind) {
+    return alp_gemm_f32_emul_workspace(N, M, K, nslices, kind);
+}
+
+alp_status alp_gemm_f32_emul_cm(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                                float alpha, const float* A, int64_t lda, const float* B,
+                                int64_t ldb, float beta, float* C, int64_t ldc, int nslices,
+                                alp_slice_kind kind, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    return emul_gemm_impl<float>(trans_b, trans_a, N, M, K, alpha, B, ldb, A, lda, beta, C, ldc,
+                                 nslices, kind, workspace, workspace_bytes,
+                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
