@@ -191,10 +191,11 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  * Uchino and Imamura's scheme II, 2024).  With n = nslices moduli m_1..m_n,
  * the first n of 256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217,
  * 211, 199, 197, 193 (pairwise coprime, product Mn), and
- * k = alp_emul_crt_bits(K, n), the largest k <= 60 with K 2^(2k+2) <= Mn:
+ * k = alp_emul_crt_bits(K, n), the largest k <= 60 with
+ * K 2^(2k+1) <= Mn (1 - 2^-18):
  *   A'_ik = RN(A_ik 2^(k - e_i)), B'_kj = RN(B_kj 2^(k - f_j)) (integers,
  *   |.| <= 2^k, e_i and f_j the exponents above),
- *   P = A' B' exact (|P| <= K 2^(2k) <= Mn / 4),
+ *   P = A' B' exact (|P| <= K 2^(2k) < Mn / 2),
  *   C = alpha * RN(P 2^(e_i + f_j - 2k))  (+ fma(beta, C, .) when beta != 0).
  * P is reached through its residues: the split writes out[l][r][k] = A'_rk mod
  * m_{l+1}, moved to [-m/2, m/2) (exact in bf16); the tensor-core stage sums

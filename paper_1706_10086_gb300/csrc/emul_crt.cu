@@ -5,9 +5,9 @@
 // pairwise coprime moduli m_l <= 256: the residues of A' and B' (in
 // [-128, 127], exact in bf16) are multiplied on the tensor cores by the
 // slice-product kernel (one product per modulus instead of one per digit
-// pair; the epilogue reduces each sum to P mod m_l, one byte), and P follows
-// by the Chinese remainder theorem, exactly, because
-// |P| <= K 2^(2k) <= M / 4 with M = m_1 ... m_n.  C = alpha RN(P 2^(e_i + f_j
+// pair; the epilogue reduces each sum to a weighted residue byte), and P
+// follows by the Chinese remainder theorem, exactly, because
+// |P| <= K 2^(2k) < M / 2 with M = m_1 ... m_n.  C = alpha RN(P 2^(e_i + f_j
 // - 2k)) (+ fma(beta, C, .)).
 #include <cstdint>
 
@@ -17,18 +17,22 @@
 
 namespace alp {
 
-// P must satisfy K 2^(2k + 2) <= M (so |P| <= M / 4); the largest such k <= 60.
+// The largest k <= 60 with K 2^(2k+1) <= M (1 - 2^-18): then |P| <= K 2^(2k)
+// stays below M / 2 by at least M 2^-19, more than the error of the
+// reconstruction's fixed-point quotient (below 2^-21 in units of M), so that
+// quotient rounds to the right multiple of M.
 int crt_bits(int64_t K, int n) {
     if (n < 1 || n > kCrtMaxModuli) return 0;
     unsigned __int128 M = 1;
     for (int l = 0; l < n; ++l) M *= crt_modulus(l);
+    const unsigned __int128 lim = M - (M >> 18);
     const uint64_t Kc = K > 0 ? (uint64_t)K : 1;
     int kbits = 0;
     while ((Kc >> kbits) != 0) ++kbits;
     for (int k = 60; k >= 1; --k) {
-        const int sh = 2 * k + 2;
+        const int sh = 2 * k + 1;
         if (sh + kbits > 127) continue;                      // K 2^sh > 2^126 > M
-        if (((unsigned __int128)Kc << sh) <= M) return k;
+        if (((unsigned __int128)Kc << sh) <= lim) return k;
     }
     return 0;
 }
@@ -148,7 +152,7 @@ __device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
 // Four columns per thread: the n bytes x_l = (P y_l) mod m_l (four adjacent
 // columns in one 32-bit load per plane) give sum_l x_l M_l = P + c Mn for the
 // integer c = round(sum_l x_l / m_l)
-// (|P| / Mn <= 1/4).  The sum is kept as four 64-bit column sums of 32-bit
+// (|P| / Mn <= 1/2 - 2^-19).  The sum is kept as four 64-bit column sums of 32-bit
 // limbs (each below 16 * 2^8 * 2^32), c from a 32.32 fixed-point sum whose
 // error is below 2^-21, and P = sum - c Mn follows by one carry pass, exact
 // modulo 2^128, which holds it.

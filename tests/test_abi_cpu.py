@@ -230,8 +230,8 @@ CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 1
 
 def test_crt_moduli_and_bits_rule(alp):
     """The documented moduli are pairwise coprime, and alp_emul_crt_bits is the
-    largest k <= 60 with K 2^(2k+2) <= their product (so |P| <= K 2^(2k)
-    stays within a quarter of the product)."""
+    largest k <= 60 with K 2^(2k+1) <= Mn (1 - 2^-18), Mn their product (so
+    |P| <= K 2^(2k) stays below Mn / 2 by at least Mn 2^-19)."""
     import math
     for i, a in enumerate(CRT_MODULI):
         for b in CRT_MODULI[i + 1:]:
@@ -241,8 +241,9 @@ def test_crt_moduli_and_bits_rule(alp):
         for K in (1, 2, 63, 1000, 1024, 8192, 8193, 32768):
             k = alp.alp_emul_crt_bits(K, n)
             assert 1 <= k <= 60
-            assert K * 2 ** (2 * k + 2) <= Mn
-            assert k == 60 or K * 2 ** (2 * k + 4) > Mn, (K, n, k)
+            lim = Mn - (Mn >> 18)
+            assert K * 2 ** (2 * k + 1) <= lim
+            assert k == 60 or K * 2 ** (2 * k + 3) > lim, (K, n, k)
     assert alp.alp_emul_crt_bits(32769, 16) == 0
     assert alp.alp_emul_crt_bits(100, 3) == 0 and alp.alp_emul_crt_bits(100, 17) == 0
-    assert alp.alp_emul_crt_bits(8192, 15) == 51 and alp.alp_emul_crt_bits(8192, 14) == 47
+    assert alp.alp_emul_crt_bits(8192, 15) == 51 and alp.alp_emul_crt_bits(8192, 14) == 48

@@ -20,7 +20,7 @@ def crt_k(K, n):
     Mn = 1
     for m in CRT_MODULI[:n]:
         Mn *= m
-    return next(k for k in range(60, 0, -1) if K * 2 ** (2 * k + 2) <= Mn)
+    return next(k for k in range(60, 0, -1) if K * 2 ** (2 * k + 1) <= Mn - (Mn >> 18))
 
 
 def colmajor(X, pad, dtype):

@@ -22,12 +22,12 @@ MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 
 
 
 def crt_k(K, n):
-    """Largest k <= 60 with K 2^(2k+2) <= m_1 ... m_n."""
+    """Largest k <= 60 with K 2^(2k+1) <= Mn (1 - 2^-18), Mn = m_1 ... m_n."""
     Mn = 1
     for m in MODULI[:n]:
         Mn *= m
     for k in range(60, 0, -1):
-        if max(K, 1) * 2 ** (2 * k + 2) <= Mn:
+        if max(K, 1) * 2 ** (2 * k + 1) <= Mn - (Mn >> 18):
             return k
     return 0
 
@@ -114,7 +114,7 @@ def test_crt_largest_k_and_modulus_count(alp, orc):
         ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, n), rows=EDGE_ROWS)
         assert np.array_equal(got[EDGE_ROWS], ref)
     # opposite-sign operands at their largest: |A'| = |B'| = 2^54 - 2, |P| near
-    # K 2^108 = 2^123, just under Mn / 4
+    # K 2^108 = 2^123, a fifth of Mn
     A = np.ones((M, K)) * (1.0 - 2.0 ** -53)
     B = -np.ones((K, N)) * (1.0 - 2.0 ** -53)
     got, _, err = run_crt(alp, A, B, None, 1.0, 0.0, 16)
@@ -247,8 +247,9 @@ def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
 
 @pytest.mark.parametrize("n", [4, 9, 15, 16])
 def test_crt_recombine_rounding(alp, n):
-    """alp_emul_recombine_crt on crafted residues: P anywhere in [-Mn/4, Mn/4]
-    (the ends included), given as the bytes (P y_l) mod m_l, with tails that are exact ties, just off a
+    """alp_emul_recombine_crt on crafted residues: P anywhere in [-L, L],
+    L = floor((Mn - Mn/2^18) / 2) the largest |P| the k rule admits (the
+    ends included), given as the bytes (P y_l) mod m_l, with tails that are exact ties, just off a
     tie, or carry one sticky bit; each result must be the correctly rounded
     alpha-free value P 2^(e_i + f_j - 2k) (Python's exact rational rounding)."""
     import random
@@ -260,9 +261,11 @@ def test_crt_recombine_rounding(alp, n):
     for m in MODULI[:n]:
         Mn *= m
     rnd = random.Random(33 + n)
-    vals = [0, 1, -1, Mn // 4, -(Mn // 4), Mn // 4 - 1, 2 ** 53 + 1, -(2 ** 54 + 2)]
-    vals = [v for v in vals if abs(v) <= Mn // 4]
-    top = (Mn // 4).bit_length()
+    L = (Mn - (Mn >> 18)) // 2
+    assert K * 2 ** (2 * k) <= L          # every product the k rule admits
+    vals = [0, 1, -1, L, -L, L - 1, 2 ** 53 + 1, -(2 ** 54 + 2)]
+    vals = [v for v in vals if abs(v) <= L]
+    top = L.bit_length()
     while len(vals) < 500:
         nbits = rnd.randrange(1, top)
         X = rnd.getrandbits(nbits) | (1 << (nbits - 1))
@@ -271,7 +274,7 @@ def test_crt_recombine_rounding(alp, n):
             r = nbits - 54 if form < 3 else rnd.randrange(0, nbits - 54)
             X = (X >> (r + 1)) << (r + 1)
             X += [1 << r, (1 << r) - 1, (1 << r) + 1, 1 << r][form]
-        if X <= Mn // 4:
+        if X <= L:
             vals.append(-X if rnd.random() < 0.5 else X)
     N = len(vals)
     ldg = (N + 255) // 256 * 256
