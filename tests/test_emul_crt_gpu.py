@@ -297,3 +297,25 @@ def test_crt_recombine_rounding(alp, n):
             E = int(e[r]) + int(f[j]) - 2 * k
             want = float(Fraction(P) * Fraction(2) ** E)
             assert got[r, j] == want, (r, j, P, E)
+
+
+def test_crt_host_resident_operands(alp, orc):
+    """A, B and C in pageable host memory on a device that reads it through
+    the host's page tables (alp_host_access): the residue splits read A and B
+    there and the reconstruction writes C there; skipped elsewhere."""
+    import torch
+    pageable, _ = alp.alp_host_access()
+    if not pageable:
+        pytest.skip("this device does not access pageable host memory")
+    M, N, K = 3 * 128 + 5, 2 * 256 + 9, 700
+    A, B, C = inputs.gemm_operands(5700, M, N, K, kind="scaled", phi=8)
+    A, B = np.ascontiguousarray(A), np.ascontiguousarray(B)
+    hC = np.ascontiguousarray(C.copy())
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, 15, CRT)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    alp.alp_gemm_f64_emul(M, N, K, 1.5, A.ctypes.data, K, B.ctypes.data, N, 0.5, hC.ctypes.data,
+                          N, 15, CRT, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, 15))
+    assert np.array_equal(hC, ref)
