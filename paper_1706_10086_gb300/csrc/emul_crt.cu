@@ -83,8 +83,7 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtSplit sp{k};
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
-    // 128-thread blocks (4 k per thread): small enough to run beside the
-    // tensor-core kernel's blocks when the two overlap on different streams
+    // 128-thread blocks (4 k per thread; measured slightly faster than 256)
     const int64_t bx = (kpad + 511) / 512;
     int64_t by = (int64_t)device_sm_count() * 16 / bx;
     by = by < 1 ? 1 : by > R ? R : by > 65535 ? 65535 : by;
@@ -231,8 +230,7 @@ alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const 
     const CrtRecConsts cc = crt_consts(n, k);
     const bool rvec = (reinterpret_cast<uintptr_t>(R) & 3) == 0 && rplane % 4 == 0 && ldr % 4 == 0;
     // four columns per thread, 128-thread blocks: 512 columns per block, as
-    // the grid was sized; small enough to run beside the tensor-core kernel's
-    // blocks when the two overlap on different streams
+    // the grid was sized
 #define ALP_CRT_REC_CASE(x)                                                                       \
     case x:                                                                                      \
         recombine_crt_kernel<x><<<grid, 128, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
