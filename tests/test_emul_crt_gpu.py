@@ -278,13 +278,15 @@ def test_crt_recombine_rounding(alp, n):
             vals.append(-X if rnd.random() < 0.5 else X)
     N = len(vals)
     ldg = (N + 255) // 256 * 256
-    rows = 3
+    rows = 5
     G = np.zeros((n, rows, ldg), dtype=np.uint8)
     y = crt_weights(n)
     for j, P in enumerate(vals):
         for l, m in enumerate(MODULI[:n]):
             G[l, :, j] = P * y[l] % m
-    e = np.array([0, 5, -40], dtype=np.int32)
+    # the last two rows scale mid-sized P into the subnormal range and past the
+    # largest double
+    e = np.array([0, 5, -40, 2 * k - 1074 - top // 2, 2 * k + 1024 - top // 2], dtype=np.int32)
     f = np.array([rnd.randrange(-8, 9) for _ in range(N)], dtype=np.int32)
     dC = torch.full((rows, N), float("nan"), dtype=torch.float64, device="cuda")
     alp.alp_emul_recombine_crt(rows, N, K, n, torch.from_numpy(G).cuda(), ldg,
@@ -295,8 +297,16 @@ def test_crt_recombine_rounding(alp, n):
     for r in range(rows):
         for j, P in enumerate(vals):
             E = int(e[r]) + int(f[j]) - 2 * k
-            want = float(Fraction(P) * Fraction(2) ** E)
+            if r < 3:
+                want = float(Fraction(P) * Fraction(2) ** E)      # one rounding
+            else:
+                # the definition: P rounded to double, then scaled (a second
+                # rounding below the normal range, infinity above it)
+                with np.errstate(over="ignore"):
+                    want = float(np.ldexp(np.float64(float(P)), E))
             assert got[r, j] == want, (r, j, P, E)
+    assert np.isinf(got[4]).any() and np.isfinite(got[4]).any()
+    assert ((got[3] != 0) & (np.abs(got[3]) < 2.0 ** -1022)).any()
 
 
 def test_crt_host_resident_operands(alp, orc):
