@@ -90,9 +90,11 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s, int gbytes = 4);
 enum EmulArrangement { kEmulSingle = 1, kEmulShareB = 2, kEmulPair = 3 };
 
 // S^t for t = 2..s+1 into G[(t-2)][M][ldg] (int32), from the digit slices
-// da[s][M][kpad] and db[s][N][kpad] (bf16, K-major).  group_m: tile-rows per
-// raster group (0 = default, the tunable of the emulated path).
-// cluster: the EmulArrangement (0 = default, one block per tile).
+// da[s][M][kpad] and db[s][N][kpad] (bf16, K-major); with crt, s moduli and
+// the residue slices instead, and G holds s byte planes [l][M][ldg] of
+// (Q_l y_l) mod m_l.  group_m: tile-rows per raster group (0 = default, the
+// tunable of the emulated path).  cluster: the EmulArrangement (0 = default,
+// emul_cluster()).
 alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bfloat16* da,
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
                            cudaStream_t stream, int group_m = 0, int cluster = 0,

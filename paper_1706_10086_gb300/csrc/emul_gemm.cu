@@ -1,28 +1,37 @@
 // Slice products of the emulated FP64 GEMM on tcgen05 tensor cores.
 //
-// One thread block per 128 x 256 tile of C, except in the last, partial wave
-// of blocks, whose tiles are each cut into up to 8 blocks by ranges of groups
-// t (tail_split below) so that wave ends sooner.  For every digit pair (p, q) with
-// p + q = t <= s + 1 (groups t ascending, p ascending) the block multiplies the
-// bf16 digit slices D_A^p (128 x K) and D_B^q (256 x K, K-major) in K chunks:
+// Arrangements (emul_arrangement_of): by default a CTA pair (2-block cluster)
+// per 256 x 256 tile of C, its tcgen05 MMAs (.cta_group::2, M = 256) spanning
+// both SMs; otherwise one block per 128 x 256 tile, or two such blocks sharing
+// each B tile by multicast.  In the last, partial wave each tile is cut into
+// up to 8 blocks (or pairs) by ranges of groups t (tail_split below) so that
+// the wave ends sooner.  Per block:
 //
-//   warp 0      TMA producer: 128x64 A and 256x64 B tiles (128-byte swizzle)
-//               into a 4-stage shared-memory ring ("full"/"empty" mbarriers);
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 f32 accumulators)
-//               and issues tcgen05.mma kind::f16 (M=128, N=256, K=16) from one
+//   warp 0      TMA producer: 128x64 A and 256x64 (pair: 128x64) B tiles
+//               (128-byte swizzle) into a shared-memory ring of stages
+//               ("full"/"empty" mbarriers);
+//   warp 1      allocates 512 TMEM columns (two f32 accumulators of 256
+//               columns) and issues tcgen05.mma kind::f16 (K = 16) from one
 //               thread, committing each stage back to the producer and each
 //               finished chunk to the epilogue;
 //   warps 2-9   drain a finished chunk from TMEM (tcgen05.ld) while the other
 //               accumulator fills, and add it exactly into int32 registers.
 //
+// Jobs (build_jobs): the digit schemes multiply the digit pairs (p, q) of
+// each group t = p + q <= s + 1 (groups ascending, p ascending); the modular
+// scheme multiplies residue slice l of A by residue slice l of B, one group
+// per modulus.  Each job is one K chunk of one product.
+//
 // Exactness: digits satisfy |d_1| <= 2^b, |d_p| <= 2^(b-1) (p >= 2), so a
 // chunk of 2^(24-2b) (pair 1,1), 2^(25-2b) (one first digit) or 2^(26-2b) (no
 // first digit) products -- 1024 / 2048 / 4096 for b = 7, 256 / 512 / 1024 for
-// b = 8 -- has |partial sum| <= 2^24: every value the f32 accumulator takes
-// is an integer f32 holds exactly, so no MMA rounds.  The drain converts each
-// chunk's integer exactly (cvt) and adds it into a 32-bit running sum, the
-// exact group sum S^t (|S^t| < 2^31 for the K limits).  At the end of each
-// group the block writes S^t to G[t-2] (int32).
+// b = 8 -- has |partial sum| <= 2^24; residues satisfy |r| <= 128, so chunks
+// of 1024 do.  Every value the f32 accumulator takes is then an integer f32
+// holds exactly, so no MMA rounds.  The drain converts each chunk's integer
+// exactly (cvt) and adds it into a 32-bit running sum, the exact group sum
+// (|S^t| < 2^31, |Q_l| <= K 2^14 for the K limits).  At the end of a group
+// the block writes S^t to G[t-2] (int32), or, for the modular scheme, the byte
+// (Q_l y_l) mod m_l to plane l-1 of G.
 #include <cstdlib>
 
 #include "crt.cuh"
