@@ -48,30 +48,51 @@ uint32_t crt_weight(int n, int l) {
     return 0;
 }
 
-// The splitter: A' = RN(a 2^(k - e)) from the rounded-to-odd fixed point (the
-// rounding sits at least 2 bits above its sticky bit, so it is exact), then
-// |A'| = hi 2^40 + mid 2^20 + lo, and per modulus x = hi (2^40 mod m) + mid
-// (2^20 mod m) + lo < 2^30, r = x mod m, negated for A' < 0, and moved to
-// [-m/2, m/2).
+// The splitter.  A' = RN(a 2^(k - e)) straight from the IEEE fields: a =
+// +-mant 2^E, shifted left when sh = E + k - e >= 0 (exact; |A'| < 2^k since
+// |a| < 2^e), else rounded half to even at bit -sh (0 below 2^-54 of mant).
+// Then the signed A' = hi 2^40 + mid 2^20 + lo (hi signed, |hi| <= 2^20; mid,
+// lo in [0, 2^20)) and per modulus x = hi (2^40 mod m) + mid (2^20 mod m) + lo
+// + b_m with b_m = m ceil(2^28 / m) + floor(m / 2), so that 0 < x < 2^30 and
+// x = A' + floor(m / 2) (mod m); the residue moved to [-floor(m/2),
+// ceil(m/2)) is (x mod m) - floor(m / 2), whose subtraction folds into the
+// bf16 packing.
+__host__ __device__ constexpr uint32_t crt_split_bias(uint32_t m) {
+    return m * (((1u << 28) + m - 1) / m) + m / 2;
+}
 struct CrtSplit {
     int k;
     template <int S>
     __device__ __forceinline__ void split(double a, int e, int (&d)[S]) const {
-        const uint64_t X = fixed_point_r0(a, e);
-        const int SH = 62 - k;
-        const uint64_t odd = (X >> SH) & 1;
-        const int64_t v = (int64_t)(X + ((1ull << (SH - 1)) - 1) + odd) >> SH;
-        const bool neg = v < 0;
-        const uint64_t u = neg ? (uint64_t)(-v) : (uint64_t)v;
-        const uint32_t lo = (uint32_t)(u & 0xFFFFFu), mid = (uint32_t)((u >> 20) & 0xFFFFFu);
-        const uint32_t hi = (uint32_t)(u >> 40);
+        const uint64_t bits = (uint64_t)__double_as_longlong(a);
+        const int ex = (int)((bits >> 52) & 0x7FF);
+        uint64_t mant = bits & ((1ull << 52) - 1);
+        int E = -1074;
+        if (ex == 0x7FF) mant = 0;   // Inf/NaN: reported by the scan; residues 0
+        else if (ex) {
+            mant |= 1ull << 52;
+            E = ex - 1075;
+        }
+        const int sh = E + k - e;
+        uint64_t u;
+        if (sh >= 0) {
+            u = mant << (sh > 63 ? 63 : sh);
+        } else if (sh < -54) {
+            u = 0;
+        } else {
+            const int r = -sh;
+            const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1), half = 1ull << (r - 1);
+            u = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+        }
+        const int64_t v = (int64_t)bits < 0 ? -(int64_t)u : (int64_t)u;
+        const int32_t hi = (int32_t)(v >> 40);
+        const uint32_t mid = (uint32_t)(v >> 20) & 0xFFFFFu, lo = (uint32_t)v & 0xFFFFFu;
 #pragma unroll
         for (int l = 0; l < S; ++l) {
             const uint32_t m = crt_modulus(l);
-            const uint32_t x = hi * crt_pow2_mod(40, m) + mid * crt_pow2_mod(20, m) + lo;
-            uint32_t r = crt_mod(x, m);
-            if (neg && r) r = m - r;
-            d[l] = (2u * r >= m + (m & 1u)) ? (int)r - (int)m : (int)r;
+            const int32_t x = hi * (int32_t)crt_pow2_mod(40, m) +
+                              (int32_t)(mid * crt_pow2_mod(20, m) + (lo + crt_split_bias(m)));
+            d[l] = (int)crt_mod((uint32_t)x, m) - (int)(m / 2);
         }
     }
 };
@@ -180,10 +201,11 @@ __global__ void __launch_bounds__(128) recombine_crt_kernel(
 #pragma unroll 1
             for (int u = 0; u < 4; ++u) {
                 if (j + u >= N) break;
+                const uint32_t sel = 0x4440u + (uint32_t)u;   // byte u, zeros above
                 uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, qa = 0;
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    const uint32_t x = (v[t] >> (8 * u)) & 255u;
+                    const uint32_t x = __byte_perm(v[t], 0u, sel);
                     a0 = mad_wide(x, cc.ml[t][0], a0);
                     a1 = mad_wide(x, cc.ml[t][1], a1);
                     a2 = mad_wide(x, cc.ml[t][2], a2);
