@@ -104,7 +104,9 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtSplit sp{k};
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
-    // 128-thread blocks (4 k per thread; measured slightly faster than 256)
+    // 128-thread blocks (4 k per thread), registers capped for 6 blocks per
+    // SM (measured faster than 256 threads, and than the uncapped 100
+    // registers)
     const int64_t bx = (kpad + 511) / 512;
     int64_t by = (int64_t)device_sm_count() * 16 / bx;
     by = by < 1 ? 1 : by > R ? R : by > 65535 ? 65535 : by;
@@ -115,8 +117,8 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
 #define ALP_CRT_SPLIT_CASE(x)                                                                    \
     case x:                                                                                      \
         if (!trans && vec)                                                                       \
-            split_rows4_kernel<T, x, CrtSplit><<<grid4, 128, 0, st>>>(X, R, K, ldx, exps, out,    \
-                                                                      kpad, sp);                  \
+            split_rows4_kernel<T, x, CrtSplit, 128, 6><<<grid4, 128, 0, st>>>(X, R, K, ldx, exps, \
+                                                                              out, kpad, sp);     \
         else if (!trans)                                                                         \
             split_rows_kernel<T, x, CrtSplit><<<(unsigned)blocks, 256, 0, st>>>(                  \
                 X, R, K, ldx, exps, out, kpad, sp);                                              \
@@ -192,53 +194,67 @@ __global__ void __launch_bounds__(128) recombine_crt_kernel(
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 const uint8_t* g = ri + (int64_t)t * rplane + j;
-                if (rvec) v[t] = __ldg(reinterpret_cast<const uint32_t*>(g));
-                else
-                    v[t] = (uint32_t)__ldg(g) | (uint32_t)__ldg(g + 1) << 8 |
-                           (uint32_t)__ldg(g + 2) << 16 | (uint32_t)__ldg(g + 3) << 24;
+                if (rvec) {   // ldr and j are multiples of 4: the word stays in the row
+                    v[t] = __ldg(reinterpret_cast<const uint32_t*>(g));
+                } else {
+                    v[t] = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (j + b < N) v[t] |= (uint32_t)__ldg(g + b) << (8 * b);
+                }
             }
-            double o0 = 0.0, o1 = 0.0, o2 = 0.0, o3 = 0.0;   // not an array: u is a runtime index
+            // two columns at a time (two independent chains), byte u of each
+            // plane word by one byte permute
+            double o[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 1
-            for (int u = 0; u < 4; ++u) {
-                if (j + u >= N) break;
-                const uint32_t sel = 0x4440u + (uint32_t)u;   // byte u, zeros above
-                uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, qa = 0;
+            for (int up = 0; up < 2; ++up) {
+                if (j + 2 * up >= N) break;
+                const uint32_t s0 = 0x4440u + 2u * (uint32_t)up, s1 = s0 + 1u;
+                uint64_t a[2][4] = {}, qa[2] = {};
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    const uint32_t x = __byte_perm(v[t], 0u, sel);
-                    a0 = mad_wide(x, cc.ml[t][0], a0);
-                    a1 = mad_wide(x, cc.ml[t][1], a1);
-                    a2 = mad_wide(x, cc.ml[t][2], a2);
-                    a3 = mad_wide(x, cc.ml[t][3], a3);
-                    qa = mad_wide(x, cc.F[t], qa);
+                    const uint32_t x0 = __byte_perm(v[t], 0u, s0), x1 = __byte_perm(v[t], 0u, s1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        a[0][q] = mad_wide(x0, cc.ml[t][q], a[0][q]);
+                        a[1][q] = mad_wide(x1, cc.ml[t][q], a[1][q]);
+                    }
+                    qa[0] = mad_wide(x0, cc.F[t], qa[0]);
+                    qa[1] = mad_wide(x1, cc.F[t], qa[1]);
                 }
-                const uint32_t qi = (uint32_t)((qa + 0x80000000ull) >> 32);
-                int64_t c = (int64_t)a0 - (int64_t)((uint64_t)qi * cc.mn[0]);
-                const uint32_t w0 = (uint32_t)c;
-                c = (c >> 32) + (int64_t)a1 - (int64_t)((uint64_t)qi * cc.mn[1]);
-                const uint32_t w1 = (uint32_t)c;
-                c = (c >> 32) + (int64_t)a2 - (int64_t)((uint64_t)qi * cc.mn[2]);
-                const uint32_t w2 = (uint32_t)c;
-                c = (c >> 32) + (int64_t)a3 - (int64_t)((uint64_t)qi * cc.mn[3]);
-                const uint32_t w3 = (uint32_t)c;
-                const int64_t hi = (int64_t)(((uint64_t)w3 << 32) | w2);
-                const uint64_t lo = ((uint64_t)w1 << 32) | w0;
-                const double w = i128_scaled_to_double_rn(hi, lo, ei + __ldg(f + j + u));
-                double o = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
-                if (beta != 0.0) o = __fma_rn(beta, ci[j + u], o);
-                o0 = u == 0 ? o : o0;
-                o1 = u == 1 ? o : o1;
-                o2 = u == 2 ? o : o2;
-                o3 = u == 3 ? o : o3;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t jj = j + 2 * up + h;
+                    const uint32_t qi = (uint32_t)((qa[h] + 0x80000000ull) >> 32);
+                    int64_t c = (int64_t)a[h][0] - (int64_t)((uint64_t)qi * cc.mn[0]);
+                    const uint32_t w0 = (uint32_t)c;
+                    c = (c >> 32) + (int64_t)a[h][1] - (int64_t)((uint64_t)qi * cc.mn[1]);
+                    const uint32_t w1 = (uint32_t)c;
+                    c = (c >> 32) + (int64_t)a[h][2] - (int64_t)((uint64_t)qi * cc.mn[2]);
+                    const uint32_t w2 = (uint32_t)c;
+                    c = (c >> 32) + (int64_t)a[h][3] - (int64_t)((uint64_t)qi * cc.mn[3]);
+                    const uint32_t w3 = (uint32_t)c;
+                    const int64_t hi = (int64_t)(((uint64_t)w3 << 32) | w2);
+                    const uint64_t lo = ((uint64_t)w1 << 32) | w0;
+                    // columns past N read the row's zero padding; their value is not stored
+                    const double w = i128_scaled_to_double_rn(hi, lo, ei + (jj < N ? __ldg(f + jj) : 0));
+                    double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
+                    if (beta != 0.0 && jj < N) out = __fma_rn(beta, ci[jj], out);
+                    if (up == 0) {
+                        if (h == 0) o[0] = out; else o[1] = out;
+                    } else {
+                        if (h == 0) o[2] = out; else o[3] = out;
+                    }
+                }
             }
             if (cvec && j + 3 < N) {
-                reinterpret_cast<double2*>(ci + j)[0] = make_double2(o0, o1);
-                reinterpret_cast<double2*>(ci + j)[1] = make_double2(o2, o3);
+                reinterpret_cast<double2*>(ci + j)[0] = make_double2(o[0], o[1]);
+                reinterpret_cast<double2*>(ci + j)[1] = make_double2(o[2], o[3]);
             } else {
-                ci[j] = o0;
-                if (j + 1 < N) ci[j + 1] = o1;
-                if (j + 2 < N) ci[j + 2] = o2;
-                if (j + 3 < N) ci[j + 3] = o3;
+                ci[j] = o[0];
+                if (j + 1 < N) ci[j + 1] = o[1];
+                if (j + 2 < N) ci[j + 2] = o[2];
+                if (j + 3 < N) ci[j + 3] = o[3];
             }
         }
     }

@@ -110,9 +110,10 @@ __global__ void split_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K,
 // As split_rows_kernel with four consecutive k per thread: rows from
 // blockIdx.y (grid stride, no division per element), two 16-byte loads of A
 // when its row is 16-byte aligned, one 8-byte store per digit plane.  Needs
-// out 8-byte aligned (the launch checks).
-template <typename T, int S, typename Sp>
-__global__ void __launch_bounds__(256) split_rows4_kernel(const T* __restrict__ X, int64_t R,
+// out 8-byte aligned (the launch checks).  THREADS and MINB are the launch's
+// block size and the blocks per SM its register budget must allow.
+template <typename T, int S, typename Sp, int THREADS = 256, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB) split_rows4_kernel(const T* __restrict__ X, int64_t R,
                                                           int64_t K, int64_t ldx,
                                                           const int32_t* __restrict__ e,
                                                           __nv_bfloat16* __restrict__ out,

@@ -329,3 +329,49 @@ def test_crt_host_resident_operands(alp, orc):
     assert alp.alp_get_device_error() == alp.ALP_OK
     ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, 15))
     assert np.array_equal(hC, ref)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 37, 517])
+def test_crt_recombine_tight_rows(alp, N):
+    """alp_emul_recombine_crt on byte planes whose rows are exactly N bytes
+    (not a multiple of 4: the byte-by-byte path), the buffer ending with the
+    last row, beta != 0: the same results as the same residues in padded
+    rows (the word-load path)."""
+    import random
+
+    import torch
+    n, K, M = 15, 8192, 3
+    k = crt_k(K, n)
+    Mn = 1
+    for m in MODULI[:n]:
+        Mn *= m
+    L = (Mn - (Mn >> 18)) // 2
+    rnd = random.Random(91 + N)
+    y = crt_weights(n)
+    P = [rnd.randrange(-L, L + 1) for _ in range(M * N)]
+    tight = np.zeros((n, M, N), dtype=np.uint8)
+    for idx, p in enumerate(P):
+        for l, m in enumerate(MODULI[:n]):
+            tight[l, idx // N, idx % N] = p * y[l] % m
+    ldp = (N + 255) // 256 * 256
+    padded = np.zeros((n, M, ldp), dtype=np.uint8)
+    padded[:, :, :N] = tight
+    e = torch.tensor([3, -7, 0], dtype=torch.int32, device="cuda")
+    f = torch.from_numpy(np.arange(N, dtype=np.int32) % 5 - 2).cuda()
+    C0 = torch.from_numpy(inputs.uniform(93, 0, (M, N))).cuda()
+    out = []
+    for R, ld in ((tight, N), (padded, ldp)):
+        C = C0.clone()
+        alp.alp_emul_recombine_crt(M, N, K, n, torch.from_numpy(np.ascontiguousarray(R)).cuda(),
+                                   ld, e, f, 1.5, 0.5, C, N)
+        torch.cuda.synchronize()
+        out.append(C.cpu().numpy())
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    assert np.array_equal(out[0], out[1])
+    for idx in (0, M * N - 1):
+        i, j = divmod(idx, N)
+        E = int(e[i]) + int(f[j]) - 2 * k
+        w = float(Fraction(P[idx]) * Fraction(2) ** E)
+        # alpha w rounded, then fma(beta, C, .) rounded once
+        want = float(Fraction(0.5) * Fraction(C0[i, j].item()) + Fraction(1.5 * w))
+        assert out[0][i, j] == want
