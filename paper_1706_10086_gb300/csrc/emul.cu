@@ -500,8 +500,12 @@ __global__ void __launch_bounds__(256) recombine_f32_kernel(
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 const int32_t* g = gi + (int64_t)t * gplane + j;
-                if (gvec) v[t] = __ldg(reinterpret_cast<const int4*>(g));
-                else v[t] = make_int4(__ldg(g), __ldg(g + 1), __ldg(g + 2), __ldg(g + 3));
+                if (gvec) {   // ldg and j are multiples of 4: the vector stays in the row
+                    v[t] = __ldg(reinterpret_cast<const int4*>(g));
+                } else {      // element by element, nothing read past column N - 1
+                    v[t] = make_int4(__ldg(g), j + 1 < N ? __ldg(g + 1) : 0,
+                                     j + 2 < N ? __ldg(g + 2) : 0, j + 3 < N ? __ldg(g + 3) : 0);
+                }
             }
             float out[4];
 #pragma unroll

@@ -180,3 +180,29 @@ def test_emul_f32_transposed_operands_bit_exact(alp, orc, ta, tb):
     assert alp.alp_get_device_error() == alp.ALP_OK
     ref, _ = model(orc, 1.5, A, B, 0.5, C, 3, "b8")
     assert np.array_equal(dC.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("N", [1, 3, 37])
+def test_recombine_f32_tight_rows(alp, N):
+    """alp_emul_recombine_f32 on group sums whose rows are exactly N int32
+    (the element-by-element path; the buffer ends with the last row): the
+    same results as the same sums in rows padded to 256 columns."""
+    import torch
+    s, M = 3, 5
+    kind = alp.ALP_SLICE_BF16_B8
+    rng = np.random.default_rng(17 + N)
+    tight = rng.integers(-2 ** 20, 2 ** 20, size=(s, M, N), dtype=np.int32)
+    padded = np.zeros((s, M, 256), dtype=np.int32)
+    padded[:, :, :N] = tight
+    e = torch.tensor([0, 3, -5, 7, 1], dtype=torch.int32, device="cuda")
+    f = torch.from_numpy(np.arange(N, dtype=np.int32) % 3 - 1).cuda()
+    C0 = torch.from_numpy(rng.standard_normal((M, N)).astype(np.float32)).cuda()
+    out = []
+    for G, ld in ((tight, N), (padded, 256)):
+        C = C0.clone()
+        alp.alp_emul_recombine_f32(M, N, s, kind, torch.from_numpy(np.ascontiguousarray(G)).cuda(),
+                                   ld, e, f, 1.5, 0.5, C, N)
+        torch.cuda.synchronize()
+        out.append(C.cpu().numpy())
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    assert np.array_equal(out[0], out[1]) and np.all(np.isfinite(out[0]))
