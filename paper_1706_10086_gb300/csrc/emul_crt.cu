@@ -173,11 +173,10 @@ __device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
 
 // Four columns per thread: the n bytes x_l = (P y_l) mod m_l (four adjacent
 // columns in one 32-bit load per plane) give sum_l x_l M_l = P + c Mn for the
-// integer c = round(sum_l x_l / m_l)
-// (|P| / Mn <= 1/2 - 2^-19).  The sum is kept as four 64-bit column sums of 32-bit
-// limbs (each below 16 * 2^8 * 2^32), c from a 32.32 fixed-point sum whose
-// error is below 2^-21, and P = sum - c Mn follows by one carry pass, exact
-// modulo 2^128, which holds it.
+// integer c = round(sum_l x_l / m_l) (|P| / Mn <= 1/2 - 2^-19).  The sum is
+// kept as four 64-bit column sums of 32-bit limbs (each below 16 * 2^8 *
+// 2^32), c from a 32.32 fixed-point sum whose error is below 2^-21, and P =
+// sum - c Mn follows by one carry pass, exact modulo 2^128, which holds it.
 template <int S>
 __global__ void __launch_bounds__(128) recombine_crt_kernel(
     const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(128) recombine_crt_kernel(
                     const uint32_t w3 = (uint32_t)c;
                     const int64_t hi = (int64_t)(((uint64_t)w3 << 32) | w2);
                     const uint64_t lo = ((uint64_t)w1 << 32) | w0;
-                    // columns past N read the row's zero padding; their value is not stored
+                    // a column past N computes from the row's padding and is not stored
                     const double w = i128_scaled_to_double_rn(hi, lo, ei + (jj < N ? __ldg(f + jj) : 0));
                     double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
                     if (beta != 0.0 && jj < N) out = __fma_rn(beta, ci[jj], out);
