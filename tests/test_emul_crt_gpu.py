@@ -375,3 +375,19 @@ def test_crt_recombine_tight_rows(alp, N):
         # alpha w rounded, then fma(beta, C, .) rounded once
         want = float(Fraction(0.5) * Fraction(C0[i, j].item()) + Fraction(1.5 * w))
         assert out[0][i, j] == want
+
+
+def test_crt_full_size_sampled_rows(alp, orc):
+    """M = N = K = 8192 in the bench's launch configuration (CTA pairs, the
+    last partial wave split by moduli): sampled rows bit-exact against the
+    oracle's definition for 15 moduli (phi = 0, the bench's inputs' range) and
+    16 (phi = 8), with alpha = 1.5 and beta = 0.5."""
+    M = N = K = 8192
+    rows = np.array([0, 1, 4097, 8190, 8191])
+    for n, phi in ((15, 0), (16, 8)):
+        A, B, C = inputs.gemm_operands(inputs.workload_seed("emul_8192") + phi, M, N, K,
+                                       kind="scaled", phi=phi)
+        got, st, err = run_crt(alp, A, B, C, 1.5, 0.5, n)
+        assert st == alp.ALP_OK and err == alp.ALP_OK
+        ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, n), rows=rows)
+        assert np.array_equal(got[rows], ref), n
