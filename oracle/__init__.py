@@ -7,9 +7,13 @@ never does, and this package imports nothing from it: the two share no code.
 Contents
 --------
 * ``alp_oracle.c`` (built here with gcc): the GEMM of Eq. 1 of Matthes et al.
-  2017 as a long-double triple loop, ``|A||B|`` for the error bound, and the
-  emulated FP64 GEMM (exponent scan, digit split in FP64 steps, exact integer
-  slice products, exact recombination rounded once to FP64).
+  2017 as a long-double triple loop, ``|A||B|`` for the error bound, the
+  emulated FP64 GEMM of the digit schemes (exponent scan, digit split in FP64
+  steps, exact integer slice products, exact recombination rounded once to
+  FP64) and its FP32 counterpart, and the modular scheme's definition (k-bit
+  scaled integers, their exact product in 128-bit integers, one rounding; no
+  residues or moduli).  Each is pinned in ``tests/test_oracle_pins.py``
+  against exact rationals, derived bounds and integer cases.
 * ``mlp.py``: the tile-config cost model (forward, backward, masked MSE, Adam)
   in float64 numpy.
 """
