@@ -174,7 +174,7 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
  * M*ldg), from digit slices da[p][m][k] (M x kpad) and db[p][n][k] (N x kpad)
  * as written by alp_emul_split with the same kind (ALP_SLICE_BF16_B8_TRIM:
  * the last group sums only its two leading-digit pairs); kpad a multiple of
- * 64, K <= 32768 (b = 7) or 14336 (b = 8).
+ * 64, K <= 32768 (b = 7) or 14336 (b = 8) (65472 for the modular kind).
  * alp_emul_recombine: C = alpha * round(sum_t S^t 2^(b(nslices+1-t))) *
  * 2^(e_i + f_j - b(nslices+1)) (+ fma(beta, C, .)) from those sums.
  * G is 16-byte aligned.  For the modular kind (below) G holds bytes, not
@@ -204,7 +204,7 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  * l-1 of G; the recombination forms sum_l x_l (Mn/m_l) = P mod Mn in 128-bit
  * integers (the Chinese remainder theorem) and rounds once.  n products of
  * K digits instead of the digit scheme's s(s+1)/2.
- * n in 4..16, K <= 32768; FP64 only (the FP32 calls return
+ * n in 4..16, K <= 65472 (1023 blocks of 64; |Q_l| <= K 2^14 < 2^30); FP64 only (the FP32 calls return
  * ALP_ERR_UNSUPPORTED for this kind).  The error is about
  * K 2^(-k) max|A_i.| max|B_.j| per element, from the two operand roundings:
  * for K = 8192 and similar magnitudes, 15 moduli (k = 51) stay below native

@@ -714,7 +714,7 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
         return ALP_ERR_INVALID_ARG;
     if (!trans && ldx < K) return ALP_ERR_INVALID_ARG;
     if (trans && ldx < R) return ALP_ERR_INVALID_ARG;
-    if (sc.crt && (K > kEmulMaxK || crt_bits(K, nslices) < 1)) return ALP_ERR_UNSUPPORTED;
+    if (sc.crt && (K > kCrtMaxK || crt_bits(K, nslices) < 1)) return ALP_ERR_UNSUPPORTED;
     if (R == 0 || kpad == 0) return ALP_OK;
     if (sc.crt)
         return emul_split_crt(R, K, X, ldx, trans, exps, nslices,
@@ -757,7 +757,7 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
 }
 
 int alp_emul_crt_bits(int64_t K, int nmoduli) {
-    if (K < 0 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli || K > kEmulMaxK) return 0;
+    if (K < 0 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli || K > kCrtMaxK) return 0;
     return crt_bits(K, nmoduli);
 }
 

@@ -47,6 +47,10 @@ inline bool emul_scheme_of(int kind, EmulScheme* sc) {
 // scaled operand (0 when no k >= 1 fits).
 constexpr int kCrtMinModuli = 4;
 constexpr int kCrtMaxModuli = 16;
+// Largest K of the modular scheme: 1023 k-blocks of 64 (the job encoding),
+// where the exact sums |Q_l| <= K 2^14 < 2^30 stay within the residue
+// reduction's range.
+constexpr int64_t kCrtMaxK = 1023 * 64;
 int crt_bits(int64_t K, int n);
 // y_l = (Mn / m_l)^-1 mod m_l for the first n moduli (host).
 uint32_t crt_weight(int n, int l);
@@ -65,9 +69,9 @@ inline bool emul_slices_ok(const EmulScheme& sc, int s, bool f32) {
     return f32 ? (s >= 2 && s <= emul_max_slices_f32(sc.b))
                : (s >= kMinSlices && s <= emul_max_slices(sc.b));
 }
-// Largest K of one call: the modular scheme's int32 sums |Q_l| <= K 2^14 allow 32768.
+// Largest K of one call.
 inline int64_t emul_scheme_max_k(const EmulScheme& sc) {
-    return sc.crt ? kEmulMaxK : emul_max_k(sc.b);
+    return sc.crt ? kCrtMaxK : emul_max_k(sc.b);
 }
 // Whether digit pair (p, q) of group t = p + q is multiplied.
 __host__ __device__ inline bool emul_pair_kept(int p, int q, int s, bool trim) {

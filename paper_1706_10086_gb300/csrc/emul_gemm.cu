@@ -674,7 +674,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
                            cudaStream_t stream, int group_m, int cluster, int digit_bits,
                            bool trim, bool crt) {
     if (crt) {
-        if (s < kCrtMinModuli || s > kCrtMaxModuli || K > kEmulMaxK) return ALP_ERR_UNSUPPORTED;
+        if (s < kCrtMinModuli || s > kCrtMaxModuli || K > kCrtMaxK) return ALP_ERR_UNSUPPORTED;
     } else if (!emul_digit_bits_ok(digit_bits) || s > emul_max_slices(digit_bits) ||
                K > emul_max_k(digit_bits)) {
         return ALP_ERR_UNSUPPORTED;

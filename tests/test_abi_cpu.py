@@ -238,12 +238,12 @@ def test_crt_moduli_and_bits_rule(alp):
             assert math.gcd(a, b) == 1
     for n in range(4, 17):
         Mn = math.prod(CRT_MODULI[:n])
-        for K in (1, 2, 63, 1000, 1024, 8192, 8193, 32768):
+        for K in (1, 2, 63, 1000, 1024, 8192, 8193, 32768, 65472):
             k = alp.alp_emul_crt_bits(K, n)
             assert 1 <= k <= 60
             lim = Mn - (Mn >> 18)
             assert K * 2 ** (2 * k + 1) <= lim
             assert k == 60 or K * 2 ** (2 * k + 3) > lim, (K, n, k)
-    assert alp.alp_emul_crt_bits(32769, 16) == 0
+    assert alp.alp_emul_crt_bits(65473, 16) == 0 and alp.alp_emul_crt_bits(65472, 16) == 54
     assert alp.alp_emul_crt_bits(100, 3) == 0 and alp.alp_emul_crt_bits(100, 17) == 0
     assert alp.alp_emul_crt_bits(8192, 15) == 51 and alp.alp_emul_crt_bits(8192, 14) == 48

@@ -105,8 +105,9 @@ def test_crt_partial_sums_at_the_chunk_bound(alp, orc, n):
 
 
 def test_crt_largest_k_and_modulus_count(alp, orc):
-    """K = 32768 with 16 moduli (k = 54, |P| up to 2^123) and with 4 (k = 7)."""
-    M, N, K = 130, 260, 32768
+    """The largest K, 65472 (1023 k-blocks), with 16 moduli (k = 54, |P| up
+    to 2^124, 1024 jobs per tile) and with 4 (k = 7)."""
+    M, N, K = 130, 260, 65472
     A, B, _ = inputs.gemm_operands(5300, M, N, K, kind="scaled", phi=2, with_c=False)
     for n in (16, 4):
         got, st, err = run_crt(alp, A, B, None, 1.0, 0.0, n)
@@ -114,7 +115,7 @@ def test_crt_largest_k_and_modulus_count(alp, orc):
         ref, _ = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, n), rows=EDGE_ROWS)
         assert np.array_equal(got[EDGE_ROWS], ref)
     # opposite-sign operands at their largest: |A'| = |B'| = 2^54 - 2, |P| near
-    # K 2^108 = 2^123, a fifth of Mn
+    # K 2^108 = 2^124, just under Mn / 2
     A = np.ones((M, K)) * (1.0 - 2.0 ** -53)
     B = -np.ones((K, N)) * (1.0 - 2.0 ** -53)
     got, _, err = run_crt(alp, A, B, None, 1.0, 0.0, 16)
@@ -149,7 +150,7 @@ def test_crt_alpha_beta_padding_special_cases_and_limits(alp, orc):
         raise_on_error=False)
     assert call(4, 4, 3) == alp.ALP_ERR_INVALID_ARG
     assert call(4, 4, 17) == alp.ALP_ERR_INVALID_ARG
-    assert call(4, 32769, 16) == alp.ALP_ERR_UNSUPPORTED
+    assert call(4, 65473, 16) == alp.ALP_ERR_UNSUPPORTED
     assert alp.alp_gemm_f64_emul_workspace(4, 4, 4, 3, CRT) == 0
     assert alp.alp_gemm_f64_emul_workspace(4, 4, 4, 16, CRT) > 0
     assert alp.alp_gemm_f32_emul_workspace(4, 4, 4, 4, CRT) == 0
