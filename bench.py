@@ -393,14 +393,16 @@ def run_alp(args):
     if not args.no_e2e:
         # end to end through the public call with host buffers: every step copies
         # A and B from pinned host memory, runs alp_gemm_f64_emul and copies C
-        # back, all inside the timed region.  Copies run on their own stream with
-        # two sets of device operands, so step i+1's upload and step i's
+        # back, all inside the timed region.  Uploads and downloads run on two
+        # streams of their own (the link carries both directions at once) with
+        # two sets of device operands, so step i+1's upload and step i-1's
         # download overlap step i's GEMM.
         hA = A.cpu().pin_memory()
         hB = B.cpu().pin_memory()
         hC = torch.empty(n, n, dtype=torch.float64).pin_memory()
         sets = [(torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)) for _ in range(2)]
-        copy = torch.cuda.Stream(dev)
+        up = torch.cuda.Stream(dev)
+        down = torch.cuda.Stream(dev)
         ksteps = max(2, args.steps)
 
         def run_e2e(k):
@@ -409,16 +411,16 @@ def run_alp(args):
             comp = [ev() for _ in range(k)]
             d2h = [ev() for _ in range(k)]
             t0, t1 = ev(), ev()
-            t0.record(copy)
+            t0.record(up)
 
             def upload(i):
                 dA, dB, _ = sets[i % 2]
                 if i >= 2:
-                    copy.wait_event(comp[i - 2])
-                with torch.cuda.stream(copy):
+                    up.wait_event(comp[i - 2])       # the set's previous GEMM has read it
+                with torch.cuda.stream(up):
                     dA.copy_(hA, non_blocking=True)
                     dB.copy_(hB, non_blocking=True)
-                h2d[i].record(copy)
+                h2d[i].record(up)
             upload(0)
             for i in range(k):
                 if i + 1 < k:
@@ -426,15 +428,15 @@ def run_alp(args):
                 dA, dB, dC = sets[i % 2]
                 stream.wait_event(h2d[i])
                 if i >= 2:
-                    stream.wait_event(d2h[i - 2])
+                    stream.wait_event(d2h[i - 2])    # the set's previous C is downloaded
                 alp.alp_gemm_f64_emul(M, N, K, alpha, dA, K, dB, N, beta, dC, N, s, kind, work,
                                       wsb, stream)
                 comp[i].record(stream)
-                copy.wait_event(comp[i])
-                with torch.cuda.stream(copy):
+                down.wait_event(comp[i])
+                with torch.cuda.stream(down):
                     hC.copy_(dC, non_blocking=True)
-                d2h[i].record(copy)
-            t1.record(copy)
+                d2h[i].record(down)
+            t1.record(down)                          # after the last download
             torch.cuda.synchronize()
             return t0.elapsed_time(t1) / k
         run_e2e(2)                       # warm-up
@@ -444,7 +446,8 @@ def run_alp(args):
                       "ms_per_step": round(e2e_ms, 3), "steps": ksteps,
                       "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
                       "d2h_bytes_per_step": int(hC.numel() * 8),
-                      "overlap": "copies on a second stream, two operand sets"}
+                      "overlap": "uploads and downloads on two streams of their own, two "
+                                 "operand sets"}
         del sets
 
     if not args.no_e2e and alp.alp_host_access()[0]:
