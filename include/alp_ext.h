@@ -21,8 +21,7 @@ extern "C" {
  * (bm/(8 tm)) * (bn/(4 tn)) compute warps within the per-(tm,tn) thread cap
  * that keeps the register tile resident; at least 2 stages of
  * (bm+bn)*bk*8 bytes within 227 KiB of shared memory.  Emulated path:
- * {128, 256, 64, cluster, 0, group} with cluster in {1, 2} (one block per
- * 128 x 256 tile, or two blocks sharing each B tile through multicast), or
+ * {128, 256, 64, 1, 0, group} (one block per 128 x 256 tile), or
  * {256, 256, 64, 2, 0, group} (CTA pairs whose tcgen05 MMAs span both SMs on
  * a 256 x 256 tile; the default), and group in {1, 2, 4, 8, 16, 32}
  * (tile-rows per raster group). */
@@ -162,8 +161,8 @@ alp_status alp_gemm_batched_varsize_noalloc(int64_t count, const int64_t* dM, co
 /* ---- emulated path: launch shape -------------------------------------------- */
 
 /* Host-only query (no GPU needed): how alp_emul_slice_products cuts a launch
- * of `tiles` 128 x 256 tiles with `nslices` slices on `sms` SMs when blocks do
- * not share B tiles.  Blocks [0, *n_full) take whole tiles; each remaining
+ * of `tiles` tiles with `nslices` slices on `sms` SMs (for CTA pairs: pair
+ * tiles on sms / 2 pairs).  Blocks [0, *n_full) take whole tiles; each remaining
  * tile (the last, partial wave) is taken by *pieces blocks, piece i computing
  * the group sums S^t for t = t_lo[i]..t_hi[i] (arrays of 8).  The cut is the
  * contiguous one whose largest piece (in digit pairs of the kind's scheme:

@@ -89,9 +89,9 @@ struct EmulLayout {
 EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s, int gbytes = 4);
 
 // Block arrangement of the slice-product kernel: one block per 128 x 256
-// tile, two blocks (a cluster) sharing each B tile by multicast, or a CTA pair
-// whose MMAs span both SMs (tcgen05 .cta_group::2, 256 x 256 per pair).
-enum EmulArrangement { kEmulSingle = 1, kEmulShareB = 2, kEmulPair = 3 };
+// tile, or a CTA pair whose MMAs span both SMs (tcgen05 .cta_group::2,
+// 256 x 256 per pair).
+enum EmulArrangement { kEmulSingle = 1, kEmulPair = 3 };
 
 // S^t for t = 2..s+1 into G[(t-2)][M][ldg] (int32), from the digit slices
 // da[s][M][kpad] and db[s][N][kpad] (bf16, K-major); with crt, s moduli and
@@ -113,20 +113,19 @@ struct TailSplit {
 };
 TailSplit tail_split(int tiles, int s, int sms, bool trim = false, bool crt = false);
 
-// Configs of the emulated path: alp_config{128, 256, 64, cluster, 0, group_m}
-// with cluster in {1, 2} (blocks sharing each B tile), or {256, 256, 64, 2,
-// 0, group_m} (CTA pairs sharing each MMA), and group_m in {1, 2, 4, 8, 16,
-// 32} (tile-rows per raster group).
+// Configs of the emulated path: alp_config{128, 256, 64, 1, 0, group_m} (one
+// block per tile) or {256, 256, 64, 2, 0, group_m} (CTA pairs sharing each
+// MMA), and group_m in {1, 2, 4, 8, 16, 32} (tile-rows per raster group).
 inline bool emul_config_valid(const alp_config& c) {
     const bool group = c.stages == 1 || c.stages == 2 || c.stages == 4 || c.stages == 8 ||
                        c.stages == 16 || c.stages == 32;
-    const bool single_or_shared = c.bm == 128 && (c.tm == 1 || c.tm == 2);
+    const bool single = c.bm == 128 && c.tm == 1;
     const bool pair = c.bm == 256 && c.tm == 2;
-    return (single_or_shared || pair) && c.bn == 256 && c.bk == 64 && c.tn == 0 && group;
+    return (single || pair) && c.bn == 256 && c.bk == 64 && c.tn == 0 && group;
 }
 // The EmulArrangement of a valid config.
 inline int emul_arrangement_of(const alp_config& c) {
-    return c.bm == 256 ? kEmulPair : c.tm == 2 ? kEmulShareB : kEmulSingle;
+    return c.bm == 256 ? kEmulPair : kEmulSingle;
 }
 
 }  // namespace alp

@@ -2,10 +2,9 @@
 //
 // Arrangements (emul_arrangement_of): by default a CTA pair (2-block cluster)
 // per 256 x 256 tile of C, its tcgen05 MMAs (.cta_group::2, M = 256) spanning
-// both SMs; otherwise one block per 128 x 256 tile, or two such blocks sharing
-// each B tile by multicast.  In the last, partial wave each tile is cut into
-// up to 8 blocks (or pairs) by ranges of groups t (tail_split below) so that
-// the wave ends sooner.  Per block:
+// both SMs; otherwise one block per 128 x 256 tile.  In the last, partial wave
+// each tile is cut into up to 8 blocks (or pairs) by ranges of groups t
+// (tail_split below) so that the wave ends sooner.  Per block:
 //
 //   warp 0      TMA producer: 128x64 A and 256x64 (pair: 128x64) B tiles
 //               (128-byte swizzle) into a shared-memory ring of stages
@@ -44,15 +43,15 @@ alp_status make_tmap_3d_bf16(CUtensorMap* map, const void* base, uint64_t d0, ui
                              uint64_t d2, uint32_t box0, uint32_t box1);
 
 // Block arrangement when the config does not say (env ALP_EMUL_CLUSTER: 1 =
-// one block per tile, 2 = two blocks sharing B tiles, 3 = CTA pairs sharing
-// each MMA; default 3, the fastest at 8192^3 on GB300).
+// one block per tile, 3 = CTA pairs sharing each MMA; default 3, the fastest
+// at 8192^3 on GB300).
 static int emul_cluster() {
     static int c = 0;
     if (c == 0) {
         c = kEmulPair;
         if (const char* s = std::getenv("ALP_EMUL_CLUSTER")) {
             const int v = std::atoi(s);
-            if (v == kEmulSingle || v == kEmulShareB || v == kEmulPair) c = v;
+            if (v == kEmulSingle || v == kEmulPair) c = v;
         }
     }
     return c;
@@ -258,12 +257,7 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
     }
 }
 
-// CL = 1: one block per tile.  CL = 2: clusters of two blocks on vertically
-// adjacent tiles (same 256 columns of B); each block loads one 128-row half of
-// the shared B tile and multicasts it to both, and each block's MMA thread
-// releases a stage in both blocks, so a stage is refilled only after both
-// blocks have consumed it.  Halves the B bytes read from L2 and DRAM.
-template <int CL>
+// One block per 128 x 256 tile.
 __global__ void __launch_bounds__(kThreads, 1)
     emul_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
@@ -285,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], CL);   // one release per block of the cluster
+            mbar_init(&empty[i], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -309,31 +303,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_relinquish();
     }
     tc_fence_before();
-    if (CL > 1) cluster_sync_all();   // the peer's barriers exist before any multicast
-    else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int njobs = *njobs_slot;
-    const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1);
 
     // grouped raster: blocks run down group_m tile-rows before moving one
     // tile-column right, so a wave of blocks shares a compact set of A and B
     // digit panels in L2
-    // (with clusters, in units of CL tile-rows; a block whose tile lies past M
-    // still loads its half of B for its peer and stores nothing)
     int m0, n0;
     {
-        const int tiles_mc = (prm.tiles_m + CL - 1) / CL;
-        const int gm = prm.group_m / CL > 0 ? prm.group_m / CL : 1;
-        const int tile = (int)blockIdx.x < prm.n_full
-                             ? (int)blockIdx.x
-                             : prm.n_full + ((int)blockIdx.x - prm.n_full) / prm.pieces;
-        const int pid = tile / CL, in_group = gm * prm.tiles_n;
+        const int gm = prm.group_m > 0 ? prm.group_m : 1;
+        const int pid = (int)blockIdx.x < prm.n_full
+                            ? (int)blockIdx.x
+                            : prm.n_full + ((int)blockIdx.x - prm.n_full) / prm.pieces;
+        const int in_group = gm * prm.tiles_n;
         const int first_m = (pid / in_group) * gm;
-        const int gsz = min(tiles_mc - first_m, gm);
+        const int gsz = min(prm.tiles_m - first_m, gm);
         const int local = pid % in_group;
-        m0 = ((first_m + local % gsz) * CL + rank) * kTM;
+        m0 = (first_m + local % gsz) * kTM;
         n0 = (local / gsz) * kTN;
     }
     const uint64_t tmo = prm.timeout_ns;
@@ -357,27 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive_expect_tx(&full[st], kStageBytes);
                     unsigned char* a = tiles + st * kStageBytes;
                     tma_load_3d(a, &tmA, &full[st], kb * kTK, m0, job_p(jd) - 1);
-                    if (CL == 1) {
-                        tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
-                    } else {
-                        constexpr uint32_t half = kBTile / CL;
-                        tma_load_3d_multicast(a + kATile + rank * half, &tmB, &full[st], kb * kTK,
-                                              n0 + rank * (kTN / CL), job_q(jd) - 1, kMask);
-                    }
+                    tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
                 }
             }
             // every copy issued must land before the block may exit
             for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
                 mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err,
                                   false);
-            if (CL > 1) {
-                // and every release the peer sends to this block's barriers must
-                // have arrived: the last round of each stage completes only
-                // after both blocks' releases
-                for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
-                    mbar_wait_bounded(&empty[j % kStages], (j / kStages) & 1, tmo, nullptr,
-                                      prm.err, false);
-            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -412,8 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         umma_bf16(d_tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, accumulate);
                         accumulate = 1;
                     }
-                    if (CL == 1) umma_commit(&empty[st]);
-                    else umma_commit_multicast(&empty[st], kMask);
+                    umma_commit(&empty[st]);
                 }
                 if (!ok) break;
                 umma_commit(&accf[b]);
@@ -428,8 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncwarp();
-    if (CL > 1) cluster_sync_all();   // no block leaves while its peer may still signal it
-    else __syncthreads();
+    __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -506,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
     const int njobs = *njobs_slot;
 
-    // grouped raster in units of 256-row tile pairs (as the B-sharing clusters)
+    // grouped raster in units of 256-row tile pairs
     int m0, n0;
     {
         const int tiles_mc = (prm.tiles_m + 1) / 2;
@@ -691,9 +663,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
             }
         if (njobs > kMaxJobs || kblocks > 1023) return ALP_ERR_UNSUPPORTED;
     }
-    const int arr = (cluster == kEmulSingle || cluster == kEmulShareB || cluster == kEmulPair)
-                        ? cluster
-                        : emul_cluster();
+    const int arr = (cluster == kEmulSingle || cluster == kEmulPair) ? cluster : emul_cluster();
     const int cl = arr == kEmulSingle ? 1 : 2;   // blocks per cluster
     CUtensorMap ta, tb;
     alp_status st = make_tmap_3d_bf16(&ta, da, (uint64_t)kpad, (uint64_t)M, (uint64_t)s, kTK, kTM);
@@ -735,17 +705,16 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
         const int64_t grid = p.n_full >= tiles
                                  ? (int64_t)tiles
                                  : (int64_t)p.n_full + (int64_t)(tiles - p.n_full) * p.pieces;
-        cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel<1>,
+        cudaError_t e = cudaFuncSetAttribute(emul_gemm_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return cuda_status(e);
-        emul_gemm_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(ta, tb, p);
+        emul_gemm_kernel<<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(ta, tb, p);
         return cuda_status(cudaGetLastError());
     }
-    const bool pair = arr == kEmulPair;
-    const int smem_bytes = pair ? kPairSmemBytes : kSmemBytes;
+    const int smem_bytes = kPairSmemBytes;
     const int64_t pair_tiles = ((tiles_m + 1) / 2) * tiles_n;
     int64_t clusters = pair_tiles;
-    if (pair && emul_tail_split_on()) {   // in units of pairs, half the SMs each
+    if (emul_tail_split_on()) {   // in units of pairs, half the SMs each
         const TailSplit ts = tail_split((int)pair_tiles, s, device_sm_count() / 2, trim, crt);
         p.n_full = ts.n_full;
         p.pieces = ts.pieces;
@@ -754,14 +723,10 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
             p.t_ranges |= (uint64_t)((ts.t_lo[i] - 2) | (ts.t_hi[i] - 2) << 4) << (8 * i);
         if (ts.n_full < pair_tiles) clusters = ts.n_full + (pair_tiles - ts.n_full) * ts.pieces;
     }
-    cudaError_t e = pair ? cudaFuncSetAttribute(emul_gemm_pair_kernel,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                smem_bytes)
-                         : cudaFuncSetAttribute(emul_gemm_kernel<2>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(emul_gemm_pair_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return cuda_status(e);
-    const int64_t grid = 2 * (pair ? clusters : pair_tiles);
+    const int64_t grid = 2 * clusters;
     if (grid > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)grid);
@@ -775,8 +740,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     attr[0].val.clusterDim.z = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    e = pair ? cudaLaunchKernelEx(&lc, emul_gemm_pair_kernel, ta, tb, p)
-             : cudaLaunchKernelEx(&lc, emul_gemm_kernel<2>, ta, tb, p);
+    e = cudaLaunchKernelEx(&lc, emul_gemm_pair_kernel, ta, tb, p);
     return cuda_status(e);
 }
 

@@ -23,20 +23,6 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
-// Same, multicast to the CTAs of the cluster in `mask`: the tile lands at the
-// same shared-memory offset in each and completes bytes on the mbarrier at
-// the same offset in each.
-__device__ __forceinline__ void tma_load_3d_multicast(void* smem_dst, const CUtensorMap* map,
-                                                      uint64_t* bar, int32_t x, int32_t y,
-                                                      int32_t z, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(smem_dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z),
-        "h"(mask)
-        : "memory");
-}
-
 // ---- clusters ----
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
@@ -88,16 +74,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
-        : "memory");
-}
-
-// Arrives once on the mbarrier at `bar`'s offset in every CTA of `mask` when
-// the thread's prior tcgen05 operations have completed.
-__device__ __forceinline__ void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
         : "memory");
 }
 

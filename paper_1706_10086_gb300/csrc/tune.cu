@@ -79,8 +79,7 @@ std::vector<alp_config> native_configs() {
 
 std::vector<alp_config> emul_configs() {
     std::vector<alp_config> v;
-    for (int cl = 1; cl <= 2; ++cl)
-        for (int g : kGroups) v.push_back(alp_config{128, 256, 64, cl, 0, g});
+    for (int g : kGroups) v.push_back(alp_config{128, 256, 64, 1, 0, g});   // one block
     for (int g : kGroups) v.push_back(alp_config{256, 256, 64, 2, 0, g});   // CTA pairs
     return v;
 }

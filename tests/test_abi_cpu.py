@@ -98,17 +98,19 @@ def test_config_rules(alp):
 
 
 def test_emul_config_rules(alp):
-    """Emulated-path configs: one block per 128 x 256 tile or two sharing B
-    (tm 1, 2), CTA pairs on 256 x 256 (bm 256, tm 2), raster groups 1..32."""
+    """Emulated-path configs: one block per 128 x 256 tile (bm 128, tm 1) or
+    CTA pairs on 256 x 256 (bm 256, tm 2), raster groups 1..32.  No
+    arrangement shares operand tiles between blocks through multicast loads."""
     E = alp.ALP_PATH_EMUL
     n = alp.alp_config_count(E)
     got = {alp.alp_config_at(E, i).astuple() for i in range(n)}
     groups = (1, 2, 4, 8, 16, 32)
-    want = {(128, 256, 64, cl, 0, g) for cl in (1, 2) for g in groups}
+    want = {(128, 256, 64, 1, 0, g) for g in groups}
     want |= {(256, 256, 64, 2, 0, g) for g in groups}
     assert got == want and n == len(want)
     assert all(alp.alp_config_valid(c, E) for c in want)
     for bad in ((256, 256, 64, 1, 0, 8), (256, 256, 64, 3, 0, 8), (128, 256, 64, 2, 0, 3),
+                (128, 256, 64, 2, 0, 8),
                 (128, 128, 64, 1, 0, 8), (128, 256, 32, 1, 0, 8), (128, 256, 64, 1, 1, 8)):
         assert not alp.alp_config_valid(bad, E), bad
 
