@@ -138,15 +138,17 @@ alp_status alp_batched_graph_destroy(void* graph);
 
 /* Same computation as alp_gemm_batched_varsize (same arguments minus the
  * workspace), for callers that cannot allocate device memory where they issue
- * the GEMM: code running during CUDA graph capture, frameworks whose device
- * memory belongs to their own pool, loops that must not enter the allocator.
+ * the GEMM: frameworks whose device memory belongs to their own pool
+ * allocator, and real-time or long-running loops that must not enter the
+ * allocator (cudaMalloc / cudaFree take locks and may synchronise the device).
  * The paper has no counterpart; this is an interface convenience.
  * The persistent kernel's work list lives in a 1 MiB array compiled into the
  * library (held on every GPU that loads it until the process exits), so
  * count is limited to about 65,000 problems: larger batches return
  * ALP_ERR_WORKSPACE and must use alp_gemm_batched_varsize.  Nothing is
- * allocated.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * allocated, by this call or by the library's one-time set-up.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and the SM count; make that first call before any stream capture.
  * All calls share the one array and each call rewrites it completely, so no
  * clearing is needed between calls, but two calls whose kernels overlap on
  * the GPU (e.g. on different streams without ordering) race on it. */
@@ -189,7 +191,8 @@ alp_status alp_host_access(int* pageable, int* host_page_tables);
 /* ---- FP64 peak probe ----------------------------------------------------- */
 
 /* Measured FP64 throughput of this GPU: kind 0 = m16n8k4 DMMA chains (the
- * native kernel's instruction), kind 1 = scalar DFMA chains; blocks_per_sm x
+ * native kernel's instruction), kind 1 = scalar DFMA chains, kind 2 = m16n8k8
+ * DMMA chains, kind 3 = m16n8k16 DMMA chains; blocks_per_sm x
  * SM-count blocks of `threads` threads, each warp/thread running 8 independent
  * chains for `iters` iterations.  One warm-up launch, one launch timed with
  * CUDA events on `stream` (synchronises it).  Result in TFLOP/s (2 per FMA). */

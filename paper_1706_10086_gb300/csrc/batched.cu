@@ -261,9 +261,10 @@ alp_status launch_persistent(const BatchArgs& a, const Plan& pl, const ClassTabl
 
 }  // namespace
 
-// Launches plan + persistent kernel for the whole batch.
+// Launches plan + persistent kernel for the whole batch on `sms` SMs, with the
+// work list in `workspace` (256-byte aligned, plan_layout(count).bytes).
 alp_status batched_launch(const BatchArgs& a, const int64_t* hM, const int64_t* hN,
-                          void* workspace, cudaStream_t stream) {
+                          void* workspace, cudaStream_t stream, int sms) {
     const ClassTable tab = current_table();
     const PlanLayout L = plan_layout(a.count);
     char* ws = static_cast<char*>(workspace);
@@ -287,7 +288,7 @@ alp_status batched_launch(const BatchArgs& a, const int64_t* hM, const int64_t* 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     if (tiles == 0) return ALP_OK;
-    return launch_persistent(a, pl, tab, tiles, present, device_sm_count(), stream);
+    return launch_persistent(a, pl, tab, tiles, present, sms, stream);
 }
 
 }  // namespace alp
@@ -353,7 +354,8 @@ alp_status alp_gemm_batched_varsize(int64_t count, const int64_t* dM, const int6
         return st;
     if (!workspace || workspace_bytes < plan_layout(count).bytes || ((uintptr_t)workspace & 255))
         return ALP_ERR_WORKSPACE;
-    return batched_launch(a, hM, hN, workspace, reinterpret_cast<cudaStream_t>(stream));
+    return batched_launch(a, hM, hN, workspace, reinterpret_cast<cudaStream_t>(stream),
+                          device_sm_count());
 }
 
 alp_status alp_batched_set_class_config(int cls, int bm, int bn, int bk) {
@@ -437,11 +439,10 @@ alp_status alp_batched_graph_destroy(void* graph) {
 // Batched GEMM without a caller-provided workspace.
 //
 // Some callers cannot allocate device memory at the point where they issue
-// the GEMM: code that runs while a CUDA graph is being captured (an
-// allocation there is either forbidden or becomes part of the graph),
-// frameworks whose device memory is owned by their own pool allocator, and
-// real-time loops that must not take the allocator's locks or trigger a
-// device synchronisation.  For them this entry point keeps the work list of
+// the GEMM: frameworks whose device memory is owned by their own pool
+// allocator, and real-time or long-running loops that must not take the
+// allocator's locks or risk the implicit device synchronisation of
+// cudaMalloc / cudaFree.  For them this entry point keeps the work list of
 // the persistent kernel in one file-scope device array instead of a
 // workspace.  The array is part of the library image: every GPU that loads
 // the library holds these kNoAllocScratchBytes until the process exits.
@@ -452,20 +453,27 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64];   // device address of g_noalloc_scratch per device (nullptr: not set up)
+int g_noalloc_sms[64];     // SM count per device
 
-// Device address of the scratch array on the current device.  The first call
-// on a device looks it up (cudaGetSymbolAddress, which allocates nothing);
-// later calls reuse it.
-alp_status noalloc_scratch(void** out) {
+// Device address of the scratch array on the current device and its SM count.
+// The first call on a device looks both up (cudaGetSymbolAddress and an
+// attribute query, neither of which allocates); later calls reuse them.
+alp_status noalloc_scratch(void** out, int* sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ALP_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ALP_ERR_CUDA;
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n < 1)
+            return ALP_ERR_CUDA;
+        g_noalloc_sms[dev] = n;
         g_noalloc_ptr[dev] = p;
     }
     *out = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
     return ALP_OK;
 }
 }  // namespace
@@ -484,35 +492,12 @@ extern "C" alp_status alp_gemm_batched_varsize_noalloc(
         ALP_OK)
         return st;
     void* scratch = nullptr;
-    if ((st = noalloc_scratch(&scratch)) != ALP_OK) return st;
-    // The plan kernel rewrites every part of the scratch it later reads
-    // (keys, order, prefix sums, counts, and the tile counter it sets to 0), so
-    // the previous call's contents need no clearing.
-    const ClassTable tab = current_table();
-    const PlanLayout L = plan_layout(count);
-    char* ws = static_cast<char*>(scratch);
-    Plan pl;
-    pl.key = reinterpret_cast<int32_t*>(ws + L.off_key);
-    pl.order = reinterpret_cast<int32_t*>(ws + L.off_order);
-    pl.prefix = reinterpret_cast<int64_t*>(ws + L.off_prefix);
-    pl.meta = reinterpret_cast<int64_t*>(ws + L.off_meta);
-    pl.counter = reinterpret_cast<unsigned long long*>(ws + L.off_counter);
-    int64_t tiles = 0;
-    unsigned present = 0;
-    for (int64_t p = 0; p < count; ++p) {
-        if (hM[p] <= 0 || hN[p] <= 0) continue;
-        const int c = class_of(hM[p], hN[p]);
-        tiles += ((hM[p] + tab.bm[c] - 1) / tab.bm[c]) * ((hN[p] + tab.bn[c] - 1) / tab.bn[c]);
-        present |= 1u << c;
-    }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    batched_plan_kernel<<<1, kPlanThreads, 0, s>>>(a, pl, tab);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_status(e);
-    if (tiles == 0) return ALP_OK;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-        return ALP_ERR_CUDA;
-    return launch_persistent(a, pl, tab, tiles, present, sms, s);
+    int sms = 0;
+    if ((st = noalloc_scratch(&scratch, &sms)) != ALP_OK) return st;
+    // The same launch as alp_gemm_batched_varsize with the scratch array as its
+    // workspace (256-byte aligned, as a workspace must be).  The plan kernel
+    // rewrites every part of it that it later reads (keys, order, prefix sums,
+    // counts, and the tile counter it sets to 0), so the previous call's
+    // contents need no clearing.
+    return batched_launch(a, hM, hN, scratch, reinterpret_cast<cudaStream_t>(stream), sms);
 }

@@ -45,8 +45,11 @@ def test_forward_matches_oracle(alp):
 
 
 def test_backward_matches_oracle(alp):
-    """GPU float32 gradients within 1e-4 relative of the float64 backward pass
-    (itself pinned by finite differences in the CPU tests)."""
+    """GPU float32 gradients, element by element, within 1e-4 relative of the
+    float64 backward pass (itself pinned by finite differences in the CPU
+    tests), plus an absolute floor of 1e-5 of the tensor's largest gradient for
+    elements whose contributions cancel to near zero (float32 sums over the
+    batch carry about 1e-6 of the summands' magnitude)."""
     import torch
     C, B = 9, 37
     flat, X, T, Mk, d = setup(C, B)
@@ -62,8 +65,11 @@ def test_backward_matches_oracle(alp):
     y, cch = mlp.forward(P, X.astype(np.float64))
     g_ref = mlp.backward(P, cch, y, T.astype(np.float64), Mk.astype(np.float64))
     g = to_list(grads.cpu().numpy(), C)
-    for a, b in zip(g, g_ref):
-        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-7
+    names = ("W1", "b1", "W2", "b2", "W3", "b3")
+    for name, a, b in zip(names, g, g_ref):
+        tol = 1e-4 * np.abs(b) + 1e-5 * np.abs(b).max() + 1e-12
+        bad = np.abs(a - b) > tol
+        assert not bad.any(), (name, int(bad.sum()), float((np.abs(a - b) / tol).max()))
     assert abs(loss[0].item() - mlp.loss(y, T, Mk)) <= 1e-5 * mlp.loss(y, T, Mk)
     assert loss[1].item() == Mk.sum()
 
