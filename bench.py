@@ -3,19 +3,25 @@
 
 Workload (default): C = alpha*A*B + beta*C with M = N = K = 8192, FP64
 row-major operands u * 2^e (u uniform in [-1,1), e uniform in [-phi, phi],
-phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path with 7
-slices of 8-bit digits held in BF16, the last group trimmed to its two
-leading-digit pairs (ALP_SLICE_BF16_B8_TRIM: 23 slice products): for these
-inputs its largest elementwise error relative to |A||B| and its normwise
-error are both no worse than the native FP64 kernel's, which the run checks
-over the whole result (the "accuracy" object).
-One step = one full emulated GEMM: exponent scans, digit splits, the
-tensor-core slice products and the exact recombination -- the same kernels
-alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
-bracket the tensor-core kernel.  Inputs (1.5 GB) are larger than L2, so no
-flush is needed between steps.  The native DMMA path is measured on the same
-matrices in the same run (its own object), as is the end-to-end call with
-host buffers and the CPU oracle on a bounded sample of rows.
+phi = 0), alpha = 1, beta = 0, computed by the emulated FP64 path's modular
+scheme (ALP_SLICE_BF16_CRT: the operands rounded to k-bit integers per row and
+column, their exact product from residues modulo n moduli, one tensor-core
+product per modulus); n is the library's automatic count for these operands
+(alp_emul_crt_choose; 15 for phi = 0).
+One step = one full emulated GEMM: exponent scans, residue splits, the
+tensor-core residue products and the Chinese remainder reconstruction -- the
+same kernels alp_gemm_f64_emul launches, issued stage by stage so that CUDA
+events can bracket each.  Inputs (1.5 GB) are larger than L2, so no flush is
+needed between steps.
+
+Beside the headline, in the same JSON line: the end-to-end call with host
+buffers; the native DMMA kernel and the FP64 peak probes (with the vendor FP64
+GEMM timed as a comparison); per phi in {0, 8, 32}, the errors of the native
+kernel and of 13..16 moduli against the long-double oracle on sampled rows,
+the smallest count no worse than native on both measures, its throughput and
+the automatic count's; a short native size scan (default and autotuned
+config); the batched variable-size GEMM (4096 problems) against loops of
+single-problem launches; and the CPU oracle's own throughput.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl alp|reference]
 
@@ -57,37 +63,40 @@ def parse_args():
     ap.add_argument("--impl", choices=("alp", "reference"), default="alp")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--nslices", type=int, default=None,
-                    help="moduli for bf16_crt (default 15: more accurate than native FP64 "
-                         "for the default uniform inputs, checked live against 8 slices of "
-                         "7-bit digits), digit slices for the other kinds (default 7)")
+                    help="moduli for bf16_crt (default 0: the library's automatic count for "
+                         "the operands, 15 for the default uniform inputs), digit slices for "
+                         "the other kinds (default 7)")
     ap.add_argument("--kind", choices=tuple(KINDS), default="bf16_crt",
                     help="scheme: bf16 (7-bit digits, up to 8 slices), bf16_b8 (8-bit, "
                          "up to 7), bf16_b8_trim (8-bit, last group keeps only its two "
                          "leading-digit pairs), bf16_crt (residues modulo 4..16 moduli, one "
                          "product each)")
     ap.add_argument("--phi", type=int, default=0)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="target CPU time of the oracle sample")
+    ap.add_argument("--oracle-rows", type=int, default=32,
+                    help="rows of each 8192^3 product the long-double oracle computes for the "
+                         "accuracy legs (also the CPU baseline's sample)")
     ap.add_argument("--no-native", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the oracle: no accuracy legs and no CPU baseline")
+    ap.add_argument("--no-scan", action="store_true", help="skip the native size scan leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched GEMM leg")
     ap.add_argument("--workload", choices=("emul8192", "batched", "native_scan", "sgemm8192"),
                     default="emul8192",
-                    help="emul8192 (default, the headline), batched (4096 variable-size "
-                         "problems, persistent graph launch vs a loop of launches), "
-                         "native_scan (native FP64 GEMM at N = 1024..16384, default and "
-                         "autotuned config) or sgemm8192 (emulated FP32 GEMM, 3 slices of 8-bit "
-                         "digits, against the vendor FP32 GEMM)")
+                    help="emul8192 (default, the headline and every leg), batched (4096 "
+                         "variable-size problems alone), native_scan (native FP64 GEMM at N = "
+                         "1024..16384 alone) or sgemm8192 (emulated FP32 GEMM, 3 slices of "
+                         "8-bit digits, against the vendor FP32 GEMM)")
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true",
                     help="batched: keep the default class tiles instead of autotuning them")
     ap.add_argument("--profile", action="store_true",
-                    help="timed steps only (no API check, native, e2e or CPU legs): for ncu")
+                    help="timed steps only (no other leg): for ncu")
     a = ap.parse_args()
     if a.nslices is None:
-        a.nslices = 15 if a.kind == "bf16_crt" else 7
+        a.nslices = 0 if a.kind == "bf16_crt" else 7
     if a.profile:
-        a.no_native = a.no_e2e = a.no_cpu = True
+        a.no_native = a.no_e2e = a.no_cpu = a.no_scan = a.no_batched = True
     return a
 
 
@@ -212,28 +221,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_oracle_sample(A_rows, B, alpha, target_s):
-    """Times the long-double oracle on a bounded number of rows of the product
-    (all host cores).  Returns (TFLOP/s, rows, seconds, threads)."""
+def oracle_rows(n, count):
+    """Rows of an n x n product the oracle computes: `count` evenly spaced,
+    first and last included."""
     import numpy as np
-
-    import oracle
-    oracle.build()
-    n_threads = os.cpu_count() or 1
-    K = B.shape[0]
-    N = B.shape[1]
-    # one row per thread as the probe, then whole rounds of rows up to the target
-    probe = min(len(A_rows), n_threads)
-    t0 = time.perf_counter()
-    oracle.gemm(alpha, A_rows[:probe], B, 0.0, nthreads=n_threads)
-    dt = time.perf_counter() - t0
-    rounds = max(1, int(target_s / max(dt, 1e-3)))
-    rows = min(len(A_rows), probe * rounds)
-    t0 = time.perf_counter()
-    oracle.gemm(alpha, A_rows[:rows], B, 0.0, nthreads=n_threads)
-    dt = time.perf_counter() - t0
-    flops = 2.0 * rows * N * K
-    return flops / dt / 1e12, rows, dt, n_threads
+    return np.unique(np.linspace(0, n - 1, count).round().astype(np.int64))
 
 
 def workload_name(n, s, kind, phi):
@@ -252,6 +244,174 @@ def make_inputs(torch, n, phi, seed, device):
                           dtype=torch.int32).to(torch.float64)
         return torch.ldexp(u, e)
     return mat(), mat()
+
+
+def product_roofline(pairs, M, N, K, s, crt, kern_ms, region_ms, clk, workload):
+    """Roofline of the tensor-core product kernel: algorithmic flops per launch
+    (pairs x 2MNK) over its average event-timed duration, against the measured
+    bf16 peak.  The timed region lasts well under a second, so the burst figure
+    is the denominator; the sustained one and the nominal rate are given
+    beside it, and a clock-normalised fraction (the kernel's flops per SM clock
+    over the peak's, each at its own median SM clock) separates clock from
+    kernel.  DRAM traffic comes from a committed ncu summary of this kernel
+    source and workload (null otherwise), next to the algorithmic bytes:
+    operand slices read once (2 bytes per entry of A and B per product) and
+    the per-product sums written once (1 byte per entry of C per modulus, 4
+    bytes per group sum for the digit schemes)."""
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    sustained = float(peaks.get("bf16_tflops_sustained", peak))
+    achieved = pairs * 2.0 * M * N * K / (kern_ms * 1e-3) / 1e12
+    traffic = profiled_traffic(workload)
+    alg_bytes = 2.0 * s * (M + N) * K + (1.0 if crt else 4.0) * s * M * N
+    peak_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    run_mhz = clk.get("sm_mhz")
+    clock_frac = (achieved / run_mhz) / (peak / peak_mhz) if peak_mhz and run_mhz else None
+    return {"bound": "tensor", "kernel": "emul_gemm_pair_kernel (tcgen05 bf16 residue products)",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_kind}); the "
+                           f"timed region is {region_ms / 1e3:.2f} s",
+            "sustained_peak": sustained, "frac_of_sustained": round(achieved / sustained, 4),
+            "clock_normalised_frac": round(clock_frac, 4) if clock_frac else None,
+            "peak_sm_mhz": peak_mhz, "run_sm_mhz": run_mhz,
+            "algorithmic_flops_per_launch": pairs * 2.0 * M * N * K,
+            "kernel_ms": round(kern_ms, 3),
+            "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+            "dram_ratio": round(traffic / alg_bytes, 3) if traffic else None,
+            "nominal_peak": NOMINAL_BF16_TFLOPS,
+            "frac_of_nominal": round(achieved / NOMINAL_BF16_TFLOPS, 4),
+            "tensor_active_pct_ncu": profiled_tensor_active(workload)}
+
+
+def errors_vs_oracle(got_rows, ref, absAB):
+    """Largest componentwise error |dC| / (|A||B|) in units of 2^-53 and
+    normwise ||dC||_F / ||C||_F of result rows against oracle rows."""
+    import numpy as np
+    d = np.abs(got_rows - ref)
+    return {"max_componentwise_u": float(np.max(d / np.maximum(absAB, 1e-300)) / 2.0 ** -53),
+            "normwise": float(np.linalg.norm(d) / np.linalg.norm(ref))}
+
+
+def no_worse(e, nat):
+    return (e["max_componentwise_u"] <= nat["max_componentwise_u"]
+            and e["normwise"] <= nat["normwise"])
+
+
+def time_calls(torch, stream, fn, reps):
+    """Average ms of `reps` calls after one untimed call (CUDA events)."""
+    fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def accuracy_leg(args, torch, alp, dev, stream, native_ms):
+    """Per phi in {0, 8, 32}: the long-double oracle on sampled rows of the
+    8192^3 product (u 2^e entries, alpha = 1, beta = 0); the native kernel's
+    and 13..16 moduli's errors against it; the smallest count no worse than
+    native on both measures and its throughput; the automatic count.  Returns
+    (list of per-phi objects, CPU baseline object)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n = args.n
+    M = N = K = n
+    rows = oracle_rows(n, args.oracle_rows)
+    thr = os.cpu_count() or 1
+    crt = alp.ALP_SLICE_BF16_CRT
+    cpu_s, cpu_flops = 0.0, 0.0
+    ws16 = alp.alp_gemm_f64_emul_workspace(M, N, K, 16, crt)
+    work = torch.empty(ws16, dtype=torch.uint8, device=dev)
+    C = torch.empty(n, n, dtype=torch.float64, device=dev)
+    out = []
+    for phi in (0, 8, 32):
+        A, B = make_inputs(torch, n, phi, 1706 + 2 + phi, dev)
+        hA = A[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        hB = B.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = oracle.gemm(1.0, hA, hB, 0.0, nthreads=thr)
+        cpu_s += time.perf_counter() - t0
+        cpu_flops += 2.0 * len(rows) * N * K
+        # |A||B| on the sampled rows, from the native kernel on |A|, |B|
+        absA = torch.from_numpy(np.abs(hA)).to(dev)
+        absB = B.abs()
+        absAB = torch.empty(len(rows), N, dtype=torch.float64, device=dev)
+        alp.alp_gemm_f64(len(rows), N, K, 1.0, absA, K, absB, N, 0.0, absAB, N, stream=stream)
+        torch.cuda.synchronize()
+        absAB = absAB.cpu().numpy()
+        del absA, absB
+        alp.alp_gemm_f64(M, N, K, 1.0, A, K, B, N, 0.0, C, N, stream=stream)
+        torch.cuda.synchronize()
+        nat = errors_vs_oracle(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref, absAB)
+        emu = {}
+        for nm in (13, 14, 15, 16):
+            alp.alp_gemm_f64_emul(M, N, K, 1.0, A, K, B, N, 0.0, C, N, nm, crt, work, ws16,
+                                  stream)
+            torch.cuda.synchronize()
+            emu[nm] = errors_vs_oracle(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref,
+                                       absAB)
+        ok = [nm for nm in sorted(emu) if no_worse(emu[nm], nat)]
+        n_min = ok[0] if ok else None
+        n_auto, pred = alp.alp_emul_crt_choose(0, 0, M, N, K, A, K, B, N, work, ws16, stream)
+        assert alp.alp_get_device_error(stream) == alp.ALP_OK
+        flops = 2.0 * M * N * K
+
+        def tflops(nm):
+            ws = alp.alp_gemm_f64_emul_workspace(M, N, K, nm, crt)
+            ms = time_calls(torch, stream, lambda: alp.alp_gemm_f64_emul(
+                M, N, K, 1.0, A, K, B, N, 0.0, C, N, nm, crt, work, ws, stream), 5)
+            return round(flops / (ms * 1e-3) / 1e12, 3)
+        row = {"phi": phi, "rows_sampled": int(len(rows)),
+               "native": nat, "native_tflops": round(flops / (native_ms * 1e-3) / 1e12, 4)
+               if native_ms else None,
+               "emulated": {str(k): v for k, v in emu.items()},
+               "smallest_n_no_worse_than_native": n_min,
+               "tflops_at_smallest_n": tflops(n_min) if n_min else None,
+               "auto_n": n_auto, "auto_predicted_componentwise_u": round(pred[0], 4),
+               "auto_predicted_normwise_ratio_to_native": round(pred[1], 4),
+               "auto_no_worse_than_native": no_worse(emu[n_auto], nat) if n_auto in emu
+               else None,
+               "tflops_at_auto_n": tflops(n_auto)}
+        out.append(row)
+        del A, B, hB
+    del work, C
+    cpu = {"value": cpu_flops / cpu_s / 1e12, "unit": UNIT, "cores": thr, "kind": "oracle",
+           "sample": f"{len(rows)} rows of each of three {n}^3 products (phi = 0, 8, 32; "
+                     f"long-double triple loop, {cpu_s:.1f} s, {os.cpu_count()} host cores)"}
+    return out, cpu
+
+
+def native_leg(args, torch, alp, A, B, dev, stream):
+    """The native DMMA kernel at alpha = 1.5, beta = 0.5 on the same operands,
+    against the FP64 peak probes (every DMMA shape and DFMA); the vendor FP64
+    GEMM (torch.matmul on float64) timed beside it as a comparison only."""
+    n = args.n
+    C2 = torch.rand(n, n, dtype=torch.float64, device=dev) * 2 - 1
+    nat_ms = time_calls(torch, stream, lambda: alp.alp_gemm_f64(
+        n, n, n, 1.5, A, n, B, n, 0.5, C2, n, stream=stream), 2)
+    flops = 2.0 * n ** 3
+    nat_tf = flops / (nat_ms * 1e-3) / 1e12
+    probes = {name: round(alp.alp_probe_fp64_peak(kind, 20000, 2, 256, stream), 4)
+              for kind, name in ((0, "dmma_m16n8k4"), (2, "dmma_m16n8k8"),
+                                 (3, "dmma_m16n8k16"), (1, "dfma"))}
+    best = max(probes["dmma_m16n8k4"], probes["dmma_m16n8k8"], probes["dmma_m16n8k16"])
+    vend_ms = time_calls(torch, stream, lambda: torch.matmul(A, B, out=C2), 2)
+    return {"tflops": round(nat_tf, 4), "ms": round(nat_ms, 2),
+            "roofline": {"bound": "fp64_dmma", "achieved": round(nat_tf, 4), "peak": best,
+                         "unit": "TFLOP/s", "frac": round(nat_tf / best, 4),
+                         "peak_source": "the fastest of the FP64 MMA probes measured in this "
+                                        "run (alp_probe_fp64_peak, chains on all SMs)"},
+            "fp64_probes_tflops": probes,
+            "vendor_fp64_gemm": {"tflops": round(flops / (vend_ms * 1e-3) / 1e12, 4),
+                                 "ms": round(vend_ms, 2),
+                                 "note": "torch.matmul on float64 (a comparison only)"},
+            "vs_vendor": round(vend_ms / nat_ms, 4)}, nat_ms
 
 
 def run_alp(args):
@@ -274,6 +434,14 @@ def run_alp(args):
     C = torch.empty(n, n, dtype=torch.float64, device=dev)
     alpha, beta = 1.0, 0.0
     stream = torch.cuda.current_stream(dev)
+    auto = kind == alp.ALP_SLICE_BF16_CRT and s == 0
+    if auto:
+        # the library's automatic modulus count for these operands (outside
+        # the timed region; the timed step then issues the stages with it)
+        wsa = alp.alp_gemm_f64_emul_workspace(M, N, K, 0, kind)
+        worka = torch.empty(wsa, dtype=torch.uint8, device=dev)
+        s, _ = alp.alp_emul_crt_choose(0, 0, M, N, K, A, K, B, N, worka, wsa, stream)
+        del worka
     # workspace carved exactly as alp_gemm_f64_emul does
     kpad = (K + 63) // 64 * 64
     ldg = (N + 255) // 256 * 256
@@ -342,21 +510,8 @@ def run_alp(args):
     value = total_flops / (total_ms * 1e-3) / 1e12
     pairs = pairs_of(s)
     kern_avg = statistics.mean(kern_ms)
-    peaks, peak_kind = load_peaks()
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    achieved = pairs * 2.0 * M * N * K / (kern_avg * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "kernel": "emul_gemm_kernel (tcgen05 bf16 slice products)",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4),
-                "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
-                "algorithmic_flops_per_launch": pairs * 2.0 * M * N * K,
-                "kernel_ms": round(kern_avg, 3),
-                "traffic": profiled_traffic(workload_name(n, s, args.kind, phi)),
-                # the measured peak is the library GEMM's; against the nominal
-                # dense bf16 rate and the tensor pipe's own activity counter
-                "nominal_peak": NOMINAL_BF16_TFLOPS,
-                "frac_of_nominal": round(achieved / NOMINAL_BF16_TFLOPS, 4),
-                "tensor_active_pct_ncu": profiled_tensor_active(workload_name(n, s, args.kind, phi))}
+    roofline = product_roofline(pairs, M, N, K, s, kind == alp.ALP_SLICE_BF16_CRT, kern_avg,
+                                total_ms, clk, workload_name(n, s, args.kind, phi))
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": max(3, args.warmup),
@@ -365,6 +520,8 @@ def run_alp(args):
            "data": "synthetic (seeded torch generator on the GPU; u*2^e, u~U[-1,1), e~U{-phi..phi})",
            "config": {"workload": workload_name(n, s, args.kind, phi), "M": M, "N": N,
                       "K": K, "nslices": s, "slice_kind": args.kind, "digit_pairs": pairs,
+                      "nslices_from": "automatic count (alp_emul_crt_choose)" if auto
+                      else "--nslices",
                       "phi": phi, "alpha": alpha, "beta": beta,
                       "result_dtype": "f64", "parallelism": f"replicas{ws}",
                       "l2": "inputs 1.5 GB > 129 MB L2; no flush"},
@@ -476,64 +633,34 @@ def run_alp(args):
             "note": "A, B, C in pageable host memory, read and written by the kernels in place"}
         del hA2, hB2, hC2
 
+    native_ms = None
     if not args.no_native:
-        # native DMMA path, alpha = 1.5, beta = 0.5 on the same operands
-        C2 = torch.rand(n, n, dtype=torch.float64, device=dev) * 2 - 1
-        alp.alp_gemm_f64(M, N, K, 1.5, A, K, B, N, 0.5, C2, N, stream=stream)
-        reps = 2
-        e0.record(stream)
-        for _ in range(reps):
-            alp.alp_gemm_f64(M, N, K, 1.5, A, K, B, N, 0.5, C2, N, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        nat_ms = e0.elapsed_time(e1) / reps
-        nat_tf = flops_step / (nat_ms * 1e-3) / 1e12
-        fp64_peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
-        out["native"] = {"tflops": round(nat_tf, 4), "ms": round(nat_ms, 2),
-                         "roofline": {"bound": "fp64_dmma", "achieved": round(nat_tf, 4),
-                                      "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                                      "frac": round(nat_tf / fp64_peak, 4),
-                                      "peak_source": "alp_probe_fp64_peak (DMMA chains on all "
-                                                     "SMs, measured in this run)"},
-                         "emulated_speedup": round(value / ws / nat_tf, 2)}
-
-    if not args.no_native:
-        # accuracy of this run's emulated result, over every element: against 8
-        # slices (within 0.1 u of the long-double oracle on sampled rows) and
-        # relative to |A||B| from the native kernel; the native result likewise
-        C8 = torch.empty_like(C)
-        ws8 = alp.alp_gemm_f64_emul_workspace(M, N, K, 8, alp.ALP_SLICE_BF16)
-        work8 = torch.empty(ws8, dtype=torch.uint8, device=dev)
-        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, C8, N, 8, alp.ALP_SLICE_BF16,
-                              work8, ws8, stream)
-        del work8
-        Cs = torch.empty_like(C)
-        alp.alp_gemm_f64_emul(M, N, K, alpha, A, K, B, N, 0.0, Cs, N, s, kind, work, wsb,
-                              stream)
-        Cn = torch.empty_like(C)
-        alp.alp_gemm_f64(M, N, K, alpha, A, K, B, N, 0.0, Cn, N, stream=stream)
-        absAB = torch.empty_like(C)
-        alp.alp_gemm_f64(M, N, K, 1.0, A.abs(), K, B.abs(), N, 0.0, absAB, N, stream=stream)
-        torch.cuda.synchronize()
-        u = 2.0 ** -53
-        out["accuracy"] = {
-            "reference": "8 slices (within 0.1 u of the long-double oracle on sampled rows)",
-            "emulated_max_componentwise_u": float(((Cs - C8).abs() / absAB).max()) / u,
-            "native_max_componentwise_u": float(((Cn - C8).abs() / absAB).max()) / u,
-            "emulated_normwise": float(torch.linalg.norm(Cs - C8) / torch.linalg.norm(C8)),
-            "native_normwise": float(torch.linalg.norm(Cn - C8) / torch.linalg.norm(C8))}
-        del C8, Cs, Cn, absAB
-
+        out["native"], native_ms = native_leg(args, torch, alp, A, B, dev, stream)
+        out["native"]["emulated_speedup"] = round(value / ws / out["native"]["tflops"], 2)
+    del A, B, C
+    torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu:
-        # CPU baseline: the long-double oracle on a bounded sample of rows
-        rows = 512
-        A_rows = A[:rows].cpu().numpy()
-        Bh = B.cpu().numpy()
-        tf, r, dt, thr = cpu_oracle_sample(A_rows, Bh, alpha, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": tf, "unit": UNIT, "cores": thr, "kind": "oracle",
-                               "sample": f"{r} of {M} rows of the {n}^3 product "
-                                         f"(long-double triple loop, {dt:.1f} s, "
-                                         f"{os.cpu_count()} host cores)"}
+        # accuracy per phi against the long-double oracle on sampled rows; the
+        # oracle's time on those rows is the CPU baseline
+        out["accuracy_per_phi"], out["cpu_baseline"] = accuracy_leg(args, torch, alp, dev,
+                                                                    stream, native_ms)
+        torch.cuda.empty_cache()
+        # the headline's own scheme and count at its phi, when the leg covers them
+        head = [r for r in out["accuracy_per_phi"] if r["phi"] == phi]
+        if kind == alp.ALP_SLICE_BF16_CRT and head and str(s) in head[0]["emulated"]:
+            r = head[0]
+            out["accuracy"] = {"reference": f"long-double oracle on {r['rows_sampled']} "
+                                            "evenly spaced rows",
+                               "nslices": s, "emulated": r["emulated"][str(s)],
+                               "native": r["native"],
+                               "no_worse_than_native": no_worse(r["emulated"][str(s)],
+                                                                r["native"])}
+    if rank == 0 and ws == 1 and not args.no_scan:
+        out["native_scan"] = native_scan_leg(torch, alp, dev, stream, (4096, 8192))
+        torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not args.no_batched:
+        out["batched"] = batched_leg(args, torch, alp, dev, stream)
+        torch.cuda.empty_cache()
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -579,51 +706,65 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_batched(args):
-    """4096 independent problems, M, N, K log-uniform in [16, 1024], alpha =
-    1.5, beta = 0.5: one replay of the persistent batched CUDA graph per step,
-    against a loop of single-problem launches (plain, and captured in a graph)."""
+def batched_problems(torch, alp, inputs, dev, count):
+    """The batched workload's storage: sizes log-uniform in [16, 1024], one
+    buffer per operand with 16-byte aligned matrices, device arrays of sizes,
+    scalars, pointers and leading dimensions."""
     import numpy as np
-    import torch
-
-    from paper_1706_10086_gb300 import alp, inputs
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    shapes = inputs.shapes(inputs.workload_seed("batched_4096"), args.count, 16, 1024)
+    shapes = inputs.shapes(inputs.workload_seed("batched_4096"), count, 16, 1024)
     M, N, K = (np.ascontiguousarray(shapes[:, i]) for i in range(3))
-    sizeA, sizeB, sizeC = M * K, K * N, M * N
-    pad = lambda x: (x + 1) // 2 * 2            # 16-byte aligned starts
-    offA = np.concatenate([[0], np.cumsum(pad(sizeA))])
-    offB = np.concatenate([[0], np.cumsum(pad(sizeB))])
-    offC = np.concatenate([[0], np.cumsum(pad(sizeC))])
+    pad = lambda x: (x + 1) // 2 * 2
+    offA = np.concatenate([[0], np.cumsum(pad(M * K))])
+    offB = np.concatenate([[0], np.cumsum(pad(K * N))])
+    offC = np.concatenate([[0], np.cumsum(pad(M * N))])
     g = torch.Generator(device=dev)
     g.manual_seed(inputs.workload_seed("batched_4096"))
     bufA = torch.rand(int(offA[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
     bufB = torch.rand(int(offB[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
     bufC = torch.rand(int(offC[-1]), dtype=torch.float64, device=dev, generator=g) * 2 - 1
-    bufC0 = bufC.clone()
-    pA = bufA.data_ptr() + 8 * offA[:-1]
-    pB = bufB.data_ptr() + 8 * offB[:-1]
-    pC = bufC.data_ptr() + 8 * offC[:-1]
+    b = {"M": M, "N": N, "K": K, "bufA": bufA, "bufB": bufB, "bufC": bufC,
+         "pA": bufA.data_ptr() + 8 * offA[:-1], "pB": bufB.data_ptr() + 8 * offB[:-1],
+         "pC": bufC.data_ptr() + 8 * offC[:-1]}
     t = lambda a, dt=torch.int64: torch.tensor(np.asarray(a), dtype=dt, device=dev)
+    b["dev"] = (count, t(M), t(N), t(K), t(np.full(count, 1.5), torch.float64), t(b["pA"]), t(K),
+                t(b["pB"]), t(N), t(np.full(count, 0.5), torch.float64), t(b["pC"]), t(N), M, N,
+                K)
+    b["flops"] = float(np.sum(2.0 * M * N * K))
+    return b
+
+
+# Native configs the fair loop baseline chooses from per size class.
+LOOP_CANDIDATES = ((64, 64, 16, 4, 4, 0), (64, 64, 32, 8, 4, 0), (64, 128, 16, 4, 4, 0),
+                   (128, 128, 16, 8, 8, 0))
+
+
+def batched_leg(args, torch, alp, dev, stream, tune=True):
+    """4096 independent problems, M, N, K log-uniform in [16, 1024], alpha =
+    1.5, beta = 0.5: one replay of the persistent batched CUDA graph (class
+    tiles autotuned first, outside the timed region), against loops of
+    single-problem native launches: with the default config on one stream, the
+    same captured in a CUDA graph, and a fairer loop whose problems take the
+    best of LOOP_CANDIDATES for their size class (timed per class) and run
+    round-robin on four streams."""
+    import numpy as np
+
+    from paper_1706_10086_gb300 import inputs
     n = args.count
-    dM, dN, dK = t(M), t(N), t(K)
-    dal, dbe = t(np.full(n, 1.5), torch.float64), t(np.full(n, 0.5), torch.float64)
-    dA, dB, dC = t(pA), t(pB), t(pC)
-    dlda, dldb, dldc = t(K), t(N), t(N)
-    flops = float(np.sum(2.0 * M * N * K))
+    b = batched_problems(torch, alp, inputs, dev, n)
+    M, N, K, pA, pB, pC = b["M"], b["N"], b["K"], b["pA"], b["pB"], b["pC"]
+    bufC0 = b["bufC"].clone()
+    flops = b["flops"]
     tuned = None
-    if not args.no_tune:
-        # per-size-class tiles from the autotuner (outside the timed region)
+    t0 = time.perf_counter()
+    if tune:
         from paper_1706_10086_gb300 import tuning
         res = tuning.tune_batched_classes(M, N, K, pA, pB, pC, runs=2)
         tuned = {int(c): list(v[0]) for c, v in res.items()}
-        bufC.copy_(bufC0)
+        b["bufC"].copy_(bufC0)
+    tune_s = time.perf_counter() - t0
     ws = alp.alp_gemm_batched_workspace(n, M, N, K)
     work = torch.empty(ws, dtype=torch.uint8, device=dev)
-    graph = alp.alp_batched_graph_create(n, dM, dN, dK, dal, dA, dlda, dB, dldb, dbe, dC, dldc,
-                                         M, N, K, work, ws)
-    stream = torch.cuda.current_stream(dev)
+    graph = alp.alp_batched_graph_create(*b["dev"], work, ws)
 
     def timed(fn, steps, warm):
         for _ in range(warm):
@@ -637,87 +778,141 @@ def run_batched(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    clocks = ClockSampler(0)
-    clocks.start()
-    ms_graph = timed(lambda: alp.alp_batched_graph_launch(graph, stream), args.steps,
-                     max(3, args.warmup))
-    clk = clocks.stop()
+    ms_graph = timed(lambda: alp.alp_batched_graph_launch(graph, stream), max(3, args.steps // 2),
+                     3)
 
-    def loop(st=stream):
+    def loop(st=stream, cfgs=None, streams=None):
         for p in range(n):
+            s_p = streams[p % len(streams)] if streams else st
             alp.alp_gemm_f64(int(M[p]), int(N[p]), int(K[p]), 1.5, int(pA[p]), int(K[p]),
-                             int(pB[p]), int(N[p]), 0.5, int(pC[p]), int(N[p]), stream=st)
-    ms_loop = timed(loop, max(1, args.steps // 2), 1)
+                             int(pB[p]), int(N[p]), 0.5, int(pC[p]), int(N[p]),
+                             cfg=cfgs[p] if cfgs is not None else None, stream=s_p)
+    ms_loop = timed(loop, 1, 1)
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     gl = torch.cuda.CUDAGraph()
     with torch.cuda.graph(gl, stream=side):
         loop(side)
     stream.wait_stream(side)
-    ms_loop_graph = timed(gl.replay, max(1, args.steps // 2), 1)
+    ms_loop_graph = timed(gl.replay, 1, 1)
+    del gl
+    # fairer loop: per size class the fastest candidate config, four streams
+    cls = np.array([alp.alp_batched_class_of(int(m), int(q)) for m, q in zip(M, N)])
+    best = {}
+    for c in sorted(set(cls.tolist())):
+        idx = np.where(cls == c)[0]
+
+        def run_class(cfg, idx=idx):
+            for p in idx:
+                alp.alp_gemm_f64(int(M[p]), int(N[p]), int(K[p]), 1.5, int(pA[p]), int(K[p]),
+                                 int(pB[p]), int(N[p]), 0.5, int(pC[p]), int(N[p]), cfg=cfg,
+                                 stream=stream)
+        times = {cfg: timed(lambda cfg=cfg: run_class(cfg), 1, 1) for cfg in LOOP_CANDIDATES}
+        best[c] = min(times, key=lambda k: (times[k], k))
+    cfgs = [best[c] for c in cls]
+    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+
+    def fair():
+        for st in streams:
+            st.wait_stream(stream)
+        loop(cfgs=cfgs, streams=streams)
+        for st in streams:
+            stream.wait_stream(st)
+    ms_fair = timed(fair, 1, 1)
     alp.alp_batched_graph_destroy(graph)
+    assert alp.alp_get_device_error(stream) == alp.ALP_OK
+    tf = lambda ms: round(flops / (ms * 1e-3) / 1e12, 4)
     fp64_peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
-    value = flops / (ms_graph * 1e-3) / 1e12
-    out = {"metric": "batched FP64 GEMM TFLOP/s", "value": round(value, 4), "unit": UNIT,
-           "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-           "ms_per_step": round(ms_graph, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded: sizes SplitMix64 log-uniform, entries torch generator)",
-           "config": {"workload": f"batched_dgemm_{n}_loguniform_16_1024", "count": n,
-                      "flops_per_step": flops, "alpha": 1.5, "beta": 0.5,
-                      "l2": "operands 4.6 GB > L2; no flush"},
-           "roofline": {"bound": "fp64_dmma", "achieved": round(value, 4),
-                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                        "frac": round(value / fp64_peak, 4),
-                        "peak_source": "alp_probe_fp64_peak (measured in this run)"},
-           "loop_of_launches": {"ms": round(ms_loop, 3),
-                                "tflops": round(flops / (ms_loop * 1e-3) / 1e12, 4)},
-           "loop_of_launches_graph": {"ms": round(ms_loop_graph, 3),
-                                      "tflops": round(flops / (ms_loop_graph * 1e-3) / 1e12, 4)},
-           "class_tiles": tuned if tuned is not None else "defaults",
-           "speedup_vs_loop": round(ms_loop / ms_graph, 3),
-           "speedup_vs_loop_graph": round(ms_loop_graph / ms_graph, 3),
-           "gpu_launches": 2 * args.steps, "clocks": clk}
-    print(json.dumps(out), flush=True)
+    return {"workload": f"batched_dgemm_{n}_loguniform_16_1024", "count": n,
+            "flops_per_step": flops, "alpha": 1.5, "beta": 0.5,
+            "graph_ms": round(ms_graph, 3), "tflops": tf(ms_graph),
+            "frac_of_fp64_dmma_probe": round(tf(ms_graph) / fp64_peak, 4),
+            "class_tiles": tuned if tuned is not None else "defaults",
+            "class_tuning_s": round(tune_s, 1),
+            "loop_of_launches": {"ms": round(ms_loop, 3), "tflops": tf(ms_loop)},
+            "loop_of_launches_graph": {"ms": round(ms_loop_graph, 3), "tflops": tf(ms_loop_graph)},
+            "loop_tuned_per_class_4_streams": {
+                "ms": round(ms_fair, 3), "tflops": tf(ms_fair),
+                "configs": {str(c): list(v) for c, v in best.items()}},
+            "speedup_vs_loop": round(ms_loop / ms_graph, 3),
+            "speedup_vs_tuned_loop_4_streams": round(ms_fair / ms_graph, 3)}
 
 
-def run_native_scan(args):
-    """Native DGEMM size scan: square N in {1024, ..., 16384}, U[-1,1), alpha =
-    1.5, beta = 0.5; the default config and the autotuner's pick, each timed on
-    the full problem (best of 3 after a warm-up, CUDA events)."""
+def run_batched(args):
+    """The batched leg alone, as its own JSON line."""
     import torch
 
     from paper_1706_10086_gb300 import alp
     dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = batched_leg(args, torch, alp, dev, stream, tune=not args.no_tune)
+    clk = clocks.stop()
+    out = {"metric": "batched FP64 GEMM TFLOP/s", "value": res["tflops"], "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": res["graph_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded: sizes SplitMix64 log-uniform, entries torch generator)",
+           "config": {"workload": res["workload"], "l2": "operands 4.6 GB > L2; no flush"},
+           "batched": res, "gpu_launches": 2 * max(3, args.steps // 2), "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def native_scan_leg(torch, alp, dev, stream, sizes):
+    """Native DGEMM size scan: square N, U[-1,1), alpha = 1.5, beta = 0.5; the
+    library's default config (no tuned entry yet) and the autotuner's pick
+    (alp_tune, exhaustive sweep), each timed on the full problem (best of 2
+    after a warm-up, CUDA events)."""
     g = torch.Generator(device=dev)
     g.manual_seed(1706 + 1)
-    peak = alp.alp_probe_fp64_peak(0, 20000, 2, 256, stream)
+    peak = max(alp.alp_probe_fp64_peak(k, 20000, 2, 256, stream) for k in (0, 2, 3))
     rows = []
-    for n in (1024, 2048, 4096, 8192, 16384):
+    for n in sizes:
         A = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
         B = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
         C = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
-        _, tuned, _ = alp.alp_tune(n, n, n, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_EXHAUSTIVE)
-        res = {"N": n, "tuned_config": list(tuned.astuple())}
-        for name, cfg in (("untuned_128x128", (128, 128, 16, 8, 8, 0)), ("tuned", tuned)):
-            times = []
+        res = {"N": n}
+
+        def best_ms(cfg):
             alp.alp_gemm_f64(n, n, n, 1.5, A, n, B, n, 0.5, C, n, cfg=cfg, stream=stream)
-            for _ in range(3 if n <= 8192 else 1):
+            times = []
+            for _ in range(2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 alp.alp_gemm_f64(n, n, n, 1.5, A, n, B, n, 0.5, C, n, cfg=cfg, stream=stream)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
-            tf = 2.0 * n ** 3 / (min(times) * 1e-3) / 1e12
-            res[name] = {"ms": round(min(times), 3), "tflops": round(tf, 4),
+            return min(times)
+        for name in ("default", "tuned"):
+            cfg = None
+            if name == "tuned":
+                t0 = time.perf_counter()
+                _, tuned, _ = alp.alp_tune(n, n, n, alp.ALP_PATH_NATIVE, alp.ALP_TUNE_EXHAUSTIVE)
+                res["tune_s"] = round(time.perf_counter() - t0, 2)
+                res["tuned_config"] = list(tuned.astuple())
+                cfg = tuned
+            ms = best_ms(cfg)
+            tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+            res[name] = {"ms": round(ms, 3), "tflops": round(tf, 4),
                          "frac_of_fp64_peak": round(tf / peak, 4)}
         rows.append(res)
         del A, B, C
-    print(json.dumps({"metric": "native FP64 GEMM TFLOP/s, size scan", "unit": UNIT,
-                      "fp64_dmma_peak_measured": round(peak, 4), "alpha": 1.5, "beta": 0.5,
-                      "rows": rows}), flush=True)
+    return {"fp64_peak_measured": round(peak, 4), "alpha": 1.5, "beta": 0.5, "rows": rows}
+
+
+def run_native_scan(args):
+    """Native DGEMM size scan at N = 1024 .. 16384, as its own JSON line."""
+    import torch
+
+    from paper_1706_10086_gb300 import alp
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    res = native_scan_leg(torch, alp, dev, stream, (1024, 2048, 4096, 8192, 16384))
+    print(json.dumps({"metric": "native FP64 GEMM TFLOP/s, size scan", "unit": UNIT, **res}),
+          flush=True)
 
 
 def run_sgemm(args):
@@ -783,7 +978,7 @@ def run_sgemm(args):
     flops = 2.0 * M * N * K
     pairs = s * (s + 1) // 2
     peaks, peak_kind = load_peaks()
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    peak = float(peaks.get("bf16_tflops", 1900.0))
     achieved = pairs * flops / (kern_ms * 1e-3) / 1e12
     # the vendor FP32 GEMM on the same float operands (a comparison, not this library)
     old = torch.backends.cuda.matmul.allow_tf32
@@ -834,7 +1029,7 @@ def run_sgemm(args):
            "roofline": {"bound": "tensor", "kernel": "emul_gemm_pair_kernel (tcgen05 bf16)",
                         "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4),
-                        "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
+                        "peak_source": f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_kind})",
                         "algorithmic_flops_per_launch": pairs * flops,
                         "kernel_ms": round(kern_ms, 3), "traffic": None},
            "vendor_fp32": {"tflops": round(flops / (vend_ms * 1e-3) / 1e12, 3),

@@ -204,11 +204,17 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  * l-1 of G; the recombination forms sum_l x_l (Mn/m_l) = P mod Mn in 128-bit
  * integers (the Chinese remainder theorem) and rounds once.  n products of
  * K digits instead of the digit scheme's s(s+1)/2.
- * n in 4..16, K <= 65472 (1023 blocks of 64; |Q_l| <= K 2^14 < 2^30); FP64 only (the FP32 calls return
- * ALP_ERR_UNSUPPORTED for this kind).  The error is about
- * K 2^(-k) max|A_i.| max|B_.j| per element, from the two operand roundings:
- * for K = 8192 and similar magnitudes, 15 moduli (k = 51) stay below native
- * FP64's error.  alp_gemm_f64_emul, alp_gemm_f64_emul_ex, the workspace
+ * n in 4..16, or n = 0 for an automatic count (below), K <= 65472 (1023
+ * blocks of 64; |Q_l| <= K 2^14 < 2^30); FP64 only (the FP32 calls return
+ * ALP_ERR_UNSUPPORTED for this kind).  The error comes from the two operand
+ * roundings, at most 2^(e_i-k-1) per entry of A (2^(f_j-k-1) of B): for
+ * K = 8192 and entries of one magnitude, 14 moduli (k = 48) stay below the
+ * native kernel's error and 15 (k = 51) well below; entries spread over
+ * 2^(+-8) need 15, over 2^(+-32) 16.  With nslices = 0, alp_gemm_f64_emul and
+ * alp_gemm_f64_emul_ex choose n as alp_emul_crt_choose does: this
+ * synchronises `stream` once (the statistics are read back) and needs
+ * alp_gemm_f64_emul_workspace(M, N, K, 0, ALP_SLICE_BF16_CRT) bytes (the
+ * 16-moduli layout).  alp_gemm_f64_emul, alp_gemm_f64_emul_ex, the workspace
  * query, alp_emul_split and alp_emul_slice_products accept the kind;
  * alp_emul_recombine does not (it has no K): use alp_emul_recombine_crt,
  * which reads the n byte planes R[l][i][j] = (P_ij y_{l+1}) mod m_{l+1}
@@ -216,6 +222,31 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  * writes.  Bytes not below their modulus give unspecified results.
  */
 int alp_emul_crt_bits(int64_t K, int nmoduli);   /* k above; 0 if invalid */
+
+/* The automatic modulus count for C = op(A) op(B) (not in the paper; a
+ * heuristic of this library).  Scans the exponents e_i, f_j and, per row of
+ * op(A) and column of op(B) with x = |entry| 2^-e, S1 = sum x and S2 = sum x^2;
+ * reads back the maxima over rows of 1/S1^2, S2/S1^2, 1/S2 (stats[0..2]) and
+ * over columns (stats[3..5]) (one stream synchronisation) and returns in
+ * *nmoduli the rule's count (alp_emul_crt_moduli_rule).  workspace: as for
+ * alp_gemm_f64_emul with nslices = 0; its sections are overwritten.
+ * predicted[0..1] (may be NULL): the rule's predictions for that count. */
+alp_status alp_emul_crt_choose(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                               const double* A, int64_t lda, const double* B, int64_t ldb,
+                               void* workspace, size_t workspace_bytes, void* stream,
+                               int* nmoduli, double* predicted);
+/* The rule alone (host only, no GPU): the smallest n in 4..16 with
+ * crt_bits(K, n) >= 1 whose predicted largest componentwise error (units of
+ * 2^-53, relative to |A||B|; the operand roundings as independent uniform
+ * errors, the maximum over M*N elements at sqrt(2 ln(MN)) deviations) is at
+ * most half of 0.045 sqrt(K), the native FP64 kernel's modelled error, and
+ * whose predicted normwise error is at most half the native kernel's
+ * (modelled as 0.311 * 2^-53 * sqrt(S2_i T2_j) per element); else 16.
+ * stats[6] as above.  predicted[0] = the componentwise prediction (units of
+ * 2^-53), predicted[1] = the normwise ratio to native.  Returns 0 for invalid
+ * arguments. */
+int alp_emul_crt_moduli_rule(int64_t M, int64_t N, int64_t K, const double* stats,
+                             double* predicted);
 alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
                                   const uint8_t* R, int64_t ldr, const int32_t* e,
                                   const int32_t* f, double alpha, double beta, double* C,

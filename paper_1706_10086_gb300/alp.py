@@ -76,6 +76,11 @@ _SIGS = {
                             _vp],
                            _int),
     "alp_emul_crt_bits": ([_i64, _int], _int),
+    "alp_emul_crt_choose": ([_int, _int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp,
+                             ctypes.c_size_t, _vp, ctypes.POINTER(_int), ctypes.POINTER(_f64)],
+                            _int),
+    "alp_emul_crt_moduli_rule": ([_i64, _i64, _i64, ctypes.POINTER(_f64), ctypes.POINTER(_f64)],
+                                 _int),
     "alp_emul_recombine_crt": ([_i64, _i64, _i64, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp,
                                 _i64, _vp], _int),
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
@@ -273,6 +278,29 @@ def alp_emul_crt_bits(K, nmoduli):
     return int(lib().alp_emul_crt_bits(K, int(nmoduli)))
 
 
+def alp_emul_crt_choose(trans_a, trans_b, M, N, K, A, lda, B, ldb, workspace, workspace_bytes,
+                        stream=None, raise_on_error=True):
+    """The automatic modulus count for op(A) op(B) (one stream synchronisation).
+    Returns (count, (predicted componentwise error in units of 2^-53,
+    predicted normwise ratio to native))."""
+    n = _int(0)
+    pred = (_f64 * 2)()
+    st = lib().alp_emul_crt_choose(int(trans_a), int(trans_b), M, N, K, _p(A), lda, _p(B), ldb,
+                                   _p(workspace), workspace_bytes, _s(stream), ctypes.byref(n),
+                                   pred)
+    _check(st, "alp_emul_crt_choose", raise_on_error)
+    return n.value, (pred[0], pred[1])
+
+
+def alp_emul_crt_moduli_rule(M, N, K, stats):
+    """The automatic-count rule on given statistics (host only).  Returns
+    (count, (componentwise prediction, normwise ratio))."""
+    st = (_f64 * 6)(*[float(v) for v in stats])
+    pred = (_f64 * 2)()
+    n = lib().alp_emul_crt_moduli_rule(M, N, K, st, pred)
+    return int(n), (pred[0], pred[1])
+
+
 def alp_emul_recombine_crt(M, N, K, nmoduli, G, ldg, e, f, alpha, beta, C, ldc, stream=None,
                            raise_on_error=True):
     st = lib().alp_emul_recombine_crt(M, N, K, int(nmoduli), _p(G), ldg, _p(e), _p(f),
@@ -440,7 +468,8 @@ def alp_debug_inject_skip(kt):
 
 
 def alp_probe_fp64_peak(kind=0, iters=20000, blocks_per_sm=2, threads=256, stream=None):
-    """Measured FP64 TFLOP/s (kind 0: DMMA chains, 1: DFMA chains)."""
+    """Measured FP64 TFLOP/s (kind 0: m16n8k4 DMMA chains, 1: DFMA chains, 2: m16n8k8
+    DMMA chains, 3: m16n8k16 DMMA chains)."""
     out = ctypes.c_double(0.0)
     _check(lib().alp_probe_fp64_peak(int(kind), int(iters), int(blocks_per_sm), int(threads),
                                      ctypes.byref(out), _s(stream)), "alp_probe_fp64_peak", True)

@@ -29,6 +29,10 @@ alp_status validate_gemm(int64_t M, int64_t N, int64_t K, double alpha, const vo
                          int64_t ldc);
 bool select_config(int64_t M, int64_t N, int64_t K, alp_path path, alp_config* out,
                    cudaStream_t stream);
+alp_status crt_choose_moduli(int ta, int tb, int64_t M, int64_t N, int64_t K, const double* A,
+                             int64_t lda, const double* B, int64_t ldb, const int32_t* e,
+                             const int32_t* f, void* scratch, cudaStream_t stream, int* n_out,
+                             double* comp_u, double* norm_ratio);
 
 // ---------------------------------------------------------------------------
 // 1. exponent scan
@@ -594,7 +598,10 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     if (!emul_scheme_of(kind, &sc)) return ALP_ERR_INVALID_ARG;
     if (kF32 && sc.crt) return ALP_ERR_UNSUPPORTED;           // the modular scheme is FP64 only
     const int b = sc.b;
-    if (!emul_slices_ok(sc, nslices, kF32)) return ALP_ERR_INVALID_ARG;
+    // nslices = 0 with the modular scheme: the count is chosen from the
+    // operands (emul_auto.cu) once their exponents are known
+    const bool auto_n = !kF32 && sc.crt && nslices == 0;
+    if (!auto_n && !emul_slices_ok(sc, nslices, kF32)) return ALP_ERR_INVALID_ARG;
     if (M == 0 || N == 0) return ALP_OK;
     if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N || !C) return ALP_ERR_INVALID_ARG;
     const bool reads_ab = alpha != T(0) && K > 0;
@@ -615,22 +622,34 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     }
     if (K > emul_scheme_max_k(sc) || M > 0x7fffffffLL || N > 0x7fffffffLL)
         return ALP_ERR_UNSUPPORTED;
-    const int kcrt = sc.crt ? crt_bits(K, nslices) : 0;
-    if (sc.crt && kcrt < 1) return ALP_ERR_UNSUPPORTED;
-    const EmulLayout L = emul_layout(M, N, K, nslices, sc.crt ? 1 : 4);
-    if (!workspace || workspace_bytes < L.bytes || ((uintptr_t)workspace & 255))
+    // with an automatic count the workspace is laid out for the most moduli;
+    // e and f stay where that layout puts them, beyond every section of the
+    // chosen count's layout
+    const EmulLayout L0 = emul_layout(M, N, K, auto_n ? kCrtMaxModuli : nslices, sc.crt ? 1 : 4);
+    if (!workspace || workspace_bytes < L0.bytes || ((uintptr_t)workspace & 255))
         return ALP_ERR_WORKSPACE;
+    if (!auto_n && sc.crt && crt_bits(K, nslices) < 1) return ALP_ERR_UNSUPPORTED;
     char* ws = static_cast<char*>(workspace);
-    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
-    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
-    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
-    auto* e = reinterpret_cast<int32_t*>(ws + L.off_e);
-    auto* f = reinterpret_cast<int32_t*>(ws + L.off_f);
+    auto* e = reinterpret_cast<int32_t*>(ws + L0.off_e);
+    auto* f = reinterpret_cast<int32_t*>(ws + L0.off_f);
     // rows of op(A): rows of A, or columns of its K x M storage; columns of
     // op(B): columns of B, or rows of its N x K storage
     alp_status st;
     if ((st = emul_exponents(M, K, A, lda, ta, e, s)) != ALP_OK) return st;
     if ((st = emul_exponents(N, K, B, ldb, 1 - tb, f, s)) != ALP_OK) return st;
+    if constexpr (!kF32) {
+        if (auto_n) {   // statistics in the (not yet written) residue-byte section
+            if ((st = crt_choose_moduli(ta, tb, M, N, K, A, lda, B, ldb, e, f, ws + L0.off_g, s,
+                                        &nslices, nullptr, nullptr)) != ALP_OK)
+                return st;
+        }
+    }
+    const int kcrt = sc.crt ? crt_bits(K, nslices) : 0;
+    if (sc.crt && kcrt < 1) return ALP_ERR_UNSUPPORTED;
+    const EmulLayout L = auto_n ? emul_layout(M, N, K, nslices, 1) : L0;
+    auto* da = reinterpret_cast<__nv_bfloat16*>(ws + L.off_da);
+    auto* db = reinterpret_cast<__nv_bfloat16*>(ws + L.off_db);
+    auto* G = reinterpret_cast<int32_t*>(ws + L.off_g);
     if constexpr (kF32) {
         if ((st = emul_split(M, K, A, lda, ta, e, nslices, da, L.kpad, s, b)) != ALP_OK) return st;
         if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK)
@@ -672,9 +691,44 @@ extern "C" {
 size_t alp_gemm_f64_emul_workspace(int64_t M, int64_t N, int64_t K, int nslices,
                                    alp_slice_kind kind) {
     EmulScheme sc;
-    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc) || !emul_slices_ok(sc, nslices, false))
-        return 0;
+    if (M < 0 || N < 0 || K < 0 || !emul_scheme_of(kind, &sc)) return 0;
+    if (sc.crt && nslices == 0) return emul_layout(M, N, K, kCrtMaxModuli, 1).bytes;
+    if (!emul_slices_ok(sc, nslices, false)) return 0;
     return emul_layout(M, N, K, nslices, sc.crt ? 1 : 4).bytes;
+}
+
+alp_status alp_emul_crt_choose(int trans_a, int trans_b, int64_t M, int64_t N, int64_t K,
+                               const double* A, int64_t lda, const double* B, int64_t ldb,
+                               void* workspace, size_t workspace_bytes, void* stream,
+                               int* nmoduli, double* predicted) {
+    if (M < 0 || N < 0 || K < 0 || (trans_a != 0 && trans_a != 1) ||
+        (trans_b != 0 && trans_b != 1) || !nmoduli)
+        return ALP_ERR_INVALID_ARG;
+    if (K > kCrtMaxK || M > 0x7fffffffLL || N > 0x7fffffffLL) return ALP_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0 || K == 0) {
+        *nmoduli = kCrtMinModuli;
+        if (predicted) predicted[0] = predicted[1] = 0.0;
+        return ALP_OK;
+    }
+    if (!A || !B || lda < (trans_a ? M : K) || ldb < (trans_b ? K : N)) return ALP_ERR_INVALID_ARG;
+    const EmulLayout L0 = emul_layout(M, N, K, kCrtMaxModuli, 1);
+    if (!workspace || workspace_bytes < L0.bytes || ((uintptr_t)workspace & 255))
+        return ALP_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    auto* e = reinterpret_cast<int32_t*>(ws + L0.off_e);
+    auto* f = reinterpret_cast<int32_t*>(ws + L0.off_f);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    alp_status st;
+    if ((st = emul_exponents(M, K, A, lda, trans_a, e, s)) != ALP_OK) return st;
+    if ((st = emul_exponents(N, K, B, ldb, 1 - trans_b, f, s)) != ALP_OK) return st;
+    double c = 0.0, r = 0.0;
+    st = crt_choose_moduli(trans_a, trans_b, M, N, K, A, lda, B, ldb, e, f, ws + L0.off_g, s,
+                           nmoduli, &c, &r);
+    if (st == ALP_OK && predicted) {
+        predicted[0] = c;
+        predicted[1] = r;
+    }
+    return st;
 }
 
 alp_status alp_emul_tail_split(int tiles, int nslices, alp_slice_kind kind, int sms, int* n_full,

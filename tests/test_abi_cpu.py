@@ -249,3 +249,42 @@ def test_crt_moduli_and_bits_rule(alp):
     assert alp.alp_emul_crt_bits(65473, 16) == 0 and alp.alp_emul_crt_bits(65472, 16) == 54
     assert alp.alp_emul_crt_bits(100, 3) == 0 and alp.alp_emul_crt_bits(100, 17) == 0
     assert alp.alp_emul_crt_bits(8192, 15) == 51 and alp.alp_emul_crt_bits(8192, 14) == 48
+
+
+def _stats_of(K, phi):
+    """Expected statistics of rows (and columns) of K entries u 2^e, u uniform
+    in [-1, 1), e uniform in [-phi, phi], scaled by the row maximum's 2^phi:
+    S1 = K E|x|, S2 = K E x^2."""
+    es = range(-phi, phi + 1)
+    e1 = 0.5 * sum(2.0 ** (e - phi) for e in es) / len(es)
+    e2 = sum(4.0 ** (e - phi) for e in es) / (3 * len(es))
+    s1, s2 = K * e1, K * e2
+    return [1 / s1 ** 2, s2 / s1 ** 2, 1 / s2] * 2
+
+
+def test_crt_moduli_rule(alp):
+    """The automatic-count rule (host only).  For K = 8192 and entries of one
+    magnitude the predicted errors at 15 moduli (k = 51) are 0.25 u
+    componentwise (g/sqrt(12) 2^2 K sqrt(2 (4/K^2)(4/(3K))), g = sqrt(2 ln
+    8192^2)) and 0.10 of the native kernel normwise, inside the targets (half of
+    0.045 sqrt(K) = 2.04 u, and 0.5), while 14 moduli (k = 48) predict 0.80 of
+    native normwise: 15 is chosen.  Wider exponent ranges need more; an
+    all-zero operand needs none beyond the minimum."""
+    import math
+    K = 8192
+    n, (comp, norm) = alp.alp_emul_crt_moduli_rule(K, K, K, _stats_of(K, 0))
+    g = math.sqrt(2 * math.log(K * K))
+    want_comp = g / math.sqrt(12) * 4 * K * math.sqrt(2 * (4 / K ** 2) * (4 / (3 * K)))
+    want_norm = 4 / (math.sqrt(12) * 0.311) * math.sqrt(2 * 3 / K)
+    assert n == 15 and abs(comp / want_comp - 1) < 1e-12 and abs(norm / want_norm - 1) < 1e-12
+    assert want_norm * 8 > 0.5                   # 14 moduli (k = 48) miss the normwise target
+    assert alp.alp_emul_crt_bits(K, 15) == 51 and alp.alp_emul_crt_bits(K, 14) == 48
+    counts = [alp.alp_emul_crt_moduli_rule(K, K, K, _stats_of(K, phi))[0] for phi in (0, 2, 8, 32)]
+    assert counts == sorted(counts) and counts[-1] == 16, counts
+    assert alp.alp_emul_crt_moduli_rule(K, K, K, [0.0] * 6)[0] == 4
+    # larger statistics (a worse-conditioned operand) never lower the count
+    base = _stats_of(K, 0)
+    for f in (1.0, 4.0, 64.0, 1e4):
+        assert alp.alp_emul_crt_moduli_rule(K, K, K, [v * f for v in base])[0] >= n
+    assert alp.alp_emul_crt_moduli_rule(-1, K, K, base)[0] == 0
+    assert alp.alp_emul_crt_moduli_rule(K, K, 70000, base)[0] == 0

@@ -1,6 +1,7 @@
 """Host logic of bench.py (no GPU): the slice-kind table agrees with the ABI's
-enum, the defaults select the modular scheme with 15 moduli, and the committed
-ncu summaries parse into the roofline's traffic and tensor-activity fields."""
+enum, the defaults select the modular scheme with the library's automatic
+modulus count, the oracle rows and error measures, and the committed ncu
+summaries parse into the roofline's traffic and tensor-activity fields."""
 import glob
 import os
 import re
@@ -31,13 +32,13 @@ def test_defaults(monkeypatch):
     bench = _bench()
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse_args()
-    assert (a.kind, a.nslices, a.n, a.gpus, a.impl) == ("bf16_crt", 15, 8192, 1, "alp")
+    assert (a.kind, a.nslices, a.n, a.gpus, a.impl) == ("bf16_crt", 0, 8192, 1, "alp")
     assert a.warmup >= 3
     monkeypatch.setattr(sys, "argv", ["bench.py", "--kind", "bf16_b8_trim"])
     assert bench.parse_args().nslices == 7
     monkeypatch.setattr(sys, "argv", ["bench.py", "--profile"])
     a = bench.parse_args()
-    assert a.no_native and a.no_e2e and a.no_cpu
+    assert a.no_native and a.no_e2e and a.no_cpu and a.no_scan and a.no_batched
     assert bench.workload_name(8192, 15, "bf16_crt", 0) == \
         "emulated_dgemm_8192_bf16_crtx15slices_phi0"
 
@@ -63,3 +64,21 @@ def test_committed_profiles_parse(monkeypatch):
         assert active is None or 0.0 < active <= 100.0
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.profiled_traffic(workload) is None
+
+
+def test_oracle_rows_and_error_measures():
+    import numpy as np
+    bench = _bench()
+    r = bench.oracle_rows(8192, 32)
+    assert len(r) == 32 and r[0] == 0 and r[-1] == 8191 and np.all(np.diff(r) > 0)
+    ref = np.array([[1.0, -2.0], [4.0, 0.5]])
+    absAB = np.array([[2.0, 4.0], [8.0, 1.0]])
+    got = ref + np.array([[2.0 ** -52, 0.0], [0.0, -2.0 ** -53]])
+    e = bench.errors_vs_oracle(got, ref, absAB)
+    # |dC|/|A||B|: 2^-52/2 = 1 u and 2^-53/1 = 1 u
+    assert e["max_componentwise_u"] == 1.0
+    assert abs(e["normwise"] - np.linalg.norm([2.0 ** -52, 2.0 ** -53]) / np.linalg.norm(ref)) \
+        < 1e-30
+    nat = {"max_componentwise_u": 1.0, "normwise": e["normwise"]}
+    assert bench.no_worse(e, nat)
+    assert not bench.no_worse(e, {"max_componentwise_u": 0.5, "normwise": 1.0})

@@ -392,3 +392,89 @@ def test_crt_full_size_sampled_rows(alp, orc):
         assert st == alp.ALP_OK and err == alp.ALP_OK
         ref, _ = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, n), rows=rows)
         assert np.array_equal(got[rows], ref), n
+
+
+# ---- automatic modulus count (nslices = 0) ----
+
+U53 = 2.0 ** -53
+
+
+def _line_stats(X, e):
+    """Statistics of the lines of X (rows), scale exponents e, in float64:
+    x = |entry| 2^-e, S1 = sum x, S2 = sum x^2 -> (max 1/S1^2, max S2/S1^2,
+    max 1/S2) over the nonzero lines."""
+    x = np.abs(X) * np.ldexp(1.0, -np.asarray(e, dtype=np.int64))[:, None]
+    s1, s2 = x.sum(axis=1), (x * x).sum(axis=1)
+    keep = s1 > 0
+    s1, s2 = s1[keep], s2[keep]
+    return [float(np.max(1 / s1 ** 2)), float(np.max(s2 / s1 ** 2)), float(np.max(1 / s2))]
+
+
+@pytest.mark.parametrize("phi", [0, 8, 32])
+def test_crt_auto_count_no_worse_than_native(alp, orc, phi):
+    """nslices = 0: the count the library picks from the operands' statistics
+    gives a result bit-exact with the oracle's definition at that count, and,
+    against the long-double oracle on sampled rows, a largest componentwise
+    error (relative to |A||B|) and a normwise error no worse than the native
+    FP64 kernel's on the same inputs, for entries u 2^e with e in [-phi, phi].
+    The statistics the GPU read agree with a float64 recomputation here (the
+    rule's predictions within 1e-3)."""
+    import torch
+    M, N, K = 512, 384, 4096
+    A, B, _ = inputs.gemm_operands(7700 + phi, M, N, K, kind="scaled", phi=phi, with_c=False)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, 0, CRT)
+    assert ws == alp.alp_gemm_f64_emul_workspace(M, N, K, 16, CRT)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    n, pred = alp.alp_emul_crt_choose(0, 0, M, N, K, dA, K, dB, N, work, ws)
+    assert 4 <= n <= 16
+    st = _line_stats(A, orc.row_exponents(A)[0]) + _line_stats(B.T, orc.col_exponents(B)[0])
+    n_cpu, pred_cpu = alp.alp_emul_crt_moduli_rule(M, N, K, st)
+    assert np.allclose(pred, pred_cpu, rtol=1e-3), (pred, pred_cpu)
+    assert n == n_cpu
+    dC = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    alp.alp_gemm_f64_emul(M, N, K, 1.0, dA, K, dB, N, 0.0, dC, N, 0, CRT, work, ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    got = dC.cpu().numpy()
+    rows = np.arange(0, M, 8)
+    want, rc = orc.crt_gemm(1.0, A, B, 0.0, None, crt_k(K, n), rows=rows)
+    assert rc == 0 and np.array_equal(got[rows], want)
+    ref = orc.gemm(1.0, A, B, 0.0, rows=rows)
+    absAB = orc.absgemm(A, B, rows=rows)
+    dN = torch.empty_like(dC)
+    alp.alp_gemm_f64(M, N, K, 1.0, dA, K, dB, N, 0.0, dN, N)
+    torch.cuda.synchronize()
+    nat = dN.cpu().numpy()[rows]
+
+    def errs(x):
+        d = np.abs(x - ref)
+        return float(np.max(d / absAB) / U53), float(np.linalg.norm(d) / np.linalg.norm(ref))
+    e_auto, e_nat = errs(got[rows]), errs(nat)
+    print({"phi": phi, "n": n, "pred": pred, "auto": e_auto, "native": e_nat})
+    assert e_auto[0] <= e_nat[0] and e_auto[1] <= e_nat[1], (n, e_auto, e_nat)
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_crt_auto_count_transposed_and_ragged(alp, orc, ta, tb):
+    """The automatic count through alp_gemm_f64_emul_ex with transposed
+    operands, a ragged shape and alpha/beta: the same count as
+    alp_emul_crt_choose on the same storage, and bit-exact with the oracle's
+    definition at that count."""
+    import torch
+    M, N, K = 133, 70, 517
+    A, B, C = inputs.gemm_operands(7800 + 2 * ta + tb, M, N, K, kind="scaled", phi=4)
+    sA = np.ascontiguousarray(A.T) if ta else A
+    sB = np.ascontiguousarray(B.T) if tb else B
+    dA, lda = dev(sA)
+    dB, ldb = dev(sB)
+    dC, ldc = dev(C)
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, 0, CRT)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    n, _ = alp.alp_emul_crt_choose(ta, tb, M, N, K, dA, lda, dB, ldb, work, ws)
+    alp.alp_gemm_f64_emul_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, ldc, 0, CRT, work,
+                             ws)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    want, rc = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, n))
+    assert rc == 0 and np.array_equal(dC.cpu().numpy()[:M, :N], want)

@@ -164,3 +164,13 @@ def test_native_transposed_operands(alp, orc, ta, tb):
     assert alp.alp_gemm_f64_ex(ta, tb, M, N, K, 1.5, dA, lda, dB, ldb, 0.5, dC, N,
                                raise_on_error=False) == alp.ALP_ERR_WORKSPACE
     assert alp.alp_gemm_f64_ex_workspace(2, 0, M, N, K) == 0
+
+
+def test_fp64_peak_probes(alp):
+    """The FP64 denominators: every probe kind runs and reports a positive
+    rate; the native kernel's m16n8k4 rate is within 2x of the best DMMA shape
+    (a probe that measured nothing would sit far off)."""
+    rates = [alp.alp_probe_fp64_peak(kind, 2000, 2, 256) for kind in range(4)]
+    assert all(r > 0 for r in rates), rates
+    best = max(rates[0], rates[2], rates[3])
+    assert rates[0] >= 0.5 * best, rates
