@@ -452,6 +452,7 @@ def run_alp(args):
                     dtype=torch.uint8, device=dev)
     e = torch.empty(M, dtype=torch.int32, device=dev)
     f = torch.empty(N, dtype=torch.int32, device=dev)
+    crt = kind == alp.ALP_SLICE_BF16_CRT
     launches_per_step = 7   # scan rows, scan cols (2), split A, split B, slice products, recombine
 
     def step(ev=None):
@@ -468,7 +469,7 @@ def run_alp(args):
         rec(4)
         alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
         rec(5)
-        if kind == alp.ALP_SLICE_BF16_CRT:
+        if crt:
             alp.alp_emul_recombine_crt(M, N, K, s, G, ldg, e, f, alpha, beta, C, N, stream)
         else:
             alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)

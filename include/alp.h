@@ -335,13 +335,20 @@ alp_status alp_emul_recombine_f32(int64_t M, int64_t N, int nslices, alp_slice_k
                                   int64_t ldc, void* stream);
 
 /*
- * Batched variable-size native GEMM: `count` independent problems
+ * Batched variable-size native GEMM: `count` independent problems, each the
+ * GEMM of Eq. 1 (Sect. 2, C = alpha A B + beta C) in the row-major form above,
  *   C_p = alpha_p * A_p * B_p + beta_p * C_p,  p = 0..count-1,
- * all arrays (sizes, scalars, pointers, leading dims) in DEVICE memory, plus
+ * each problem's C tiles computed as in Sect. 2.1 (one block per C tile,
+ * register tiles per thread), with the tile size chosen per size class (the
+ * parameter the paper tunes, Sect. 3 / Table 4).
+ * All arrays (sizes, scalars, pointers, leading dims) in DEVICE memory, plus
  * HOST copies hM, hN, hK used only to plan tile classes and grid sizes.
  * Every tile of every problem is taken from a device work list by a persistent
  * kernel per size class; the whole call is stream-ordered and capturable in a
- * CUDA graph (see alp_batched_graph_*).  workspace >= alp_gemm_batched_workspace().
+ * CUDA graph (see alp_batched_graph_*).  workspace >= alp_gemm_batched_workspace()
+ * bytes, 256-byte aligned, owned by the caller.  Errors: negative sizes or a
+ * NULL array -> ALP_ERR_INVALID_ARG, a short or misaligned workspace ->
+ * ALP_ERR_WORKSPACE, both before any launch.
  */
 alp_status alp_gemm_batched_varsize(int64_t count, const int64_t* dM, const int64_t* dN,
                                     const int64_t* dK, const double* dalpha,

@@ -48,7 +48,10 @@ alp_status alp_set_wait_timeout_ms(double ms);
 /* Test hook for the timeout path: while kt >= 0, the producer warp of block 0
  * of each native TMA GEMM arms stage kt's barrier but issues no copy into it,
  * so that the consumers' wait runs out, ALP_ERR_TIMEOUT is recorded and the
- * kernel returns.  kt = -1 switches it off.  No copy is left in flight. */
+ * kernel returns.  The emulated path's tensor-core kernel does the same with
+ * its kt-th pipeline stage (counted over all jobs of block 0; for CTA pairs
+ * block 0 of the first pair skips its half, so the pair's stage never fills).
+ * kt = -1 switches it off.  No copy is left in flight. */
 alp_status alp_debug_inject_skip(int kt);
 
 /* ---- autotuner helpers --------------------------------------------------- */

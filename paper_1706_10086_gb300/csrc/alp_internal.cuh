@@ -25,6 +25,7 @@ int* device_error_word();             // address of the current device's word
 uint64_t wait_timeout_ns();           // limit of every device-side wait
 int device_sm_count();
 alp_status cuda_status(cudaError_t e);
+int inject_skip_kt();                 // test hook of the timeout path (-1: off)
 
 // ----------------------------------------------------------------------------
 // Time and barriers.

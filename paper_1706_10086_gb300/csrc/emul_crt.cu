@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "crt.cuh"
+#include "crt_rec.cuh"
 #include "emul.cuh"
 #include "emul_split.cuh"
 
@@ -141,47 +142,37 @@ template alp_status emul_split_crt<double>(int64_t, int64_t, const double*, int6
                                            const int32_t*, int, __nv_bfloat16*, int64_t, int,
                                            cudaStream_t);
 
-// Chinese remainder reconstruction constants for n moduli: Mn = prod m_l and
-// M_l = Mn / m_l as four 32-bit limbs, and F_l = round(2^32 / m_l).
-struct CrtRecConsts {
-    uint32_t ml[kCrtMaxModuli][4];
-    uint32_t mn[4];
-    uint32_t F[kCrtMaxModuli];
-    int k;
-};
-
-static CrtRecConsts crt_consts(int n, int k) {
+CrtRecConsts crt_rec_consts(int n, int k) {
     CrtRecConsts c{};
     unsigned __int128 M = 1;
     for (int l = 0; l < n; ++l) M *= crt_modulus(l);
     for (int i = 0; i < 4; ++i) c.mn[i] = (uint32_t)(M >> (32 * i));
-    for (int l = 0; l < n; ++l) {
-        const uint32_t m = crt_modulus(l);
-        const unsigned __int128 Ml = M / m;
-        for (int i = 0; i < 4; ++i) c.ml[l][i] = (uint32_t)(Ml >> (32 * i));
-        c.F[l] = (uint32_t)(((1ull << 32) + m / 2) / m);
+    for (int g = 0; 3 * g < n && g < kCrtMaxGroups; ++g) {
+        uint32_t mg = 1;
+        for (int l = 3 * g; l < 3 * g + 3 && l < n; ++l) mg *= crt_modulus(l);
+        const unsigned __int128 Mg = M / mg;
+        for (int i = 0; i < 4; ++i) c.mg[g][i] = (uint32_t)(Mg >> (32 * i));
+        const uint64_t F = (uint64_t)(((unsigned __int128)1 << 58) + mg / 2) / mg;
+        c.fg_lo[g] = (uint32_t)F;
+        c.fg_hi[g] = (uint32_t)(F >> 32);
+        for (int l = 3 * g; l < 3 * g + 3 && l < n; ++l) c.cl[l] = mg / crt_modulus(l);
     }
+    c.n = n;
     c.k = k;
     return c;
 }
 
-__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
-    uint64_t d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
-}
-
-// Four columns per thread: the n bytes x_l = (P y_l) mod m_l (four adjacent
-// columns in one 32-bit load per plane) give sum_l x_l M_l = P + c Mn for the
-// integer c = round(sum_l x_l / m_l) (|P| / Mn <= 1/2 - 2^-19).  The sum is
-// kept as four 64-bit column sums of 32-bit limbs (each below 16 * 2^8 *
-// 2^32), c from a 32.32 fixed-point sum whose error is below 2^-21, and P =
-// sum - c Mn follows by one carry pass, exact modulo 2^128, which holds it.
+// Four columns per thread: the n bytes of four adjacent columns arrive in one
+// 32-bit load per plane (crt_rec.cuh for the arithmetic); one rounding to
+// double per element, then alpha (amode 0: 1, 1: -1, 2: any) and the fused
+// beta term (bmode 1), decided on the host so that the loop holds no FP64
+// comparison.
 template <int S>
 __global__ void __launch_bounds__(128) recombine_crt_kernel(
     const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
     const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
-    double* __restrict__ C, int64_t ldc, bool rvec, const CrtRecConsts cc) {
+    double* __restrict__ C, int64_t ldc, bool rvec, int amode, int bmode,
+    const CrtRecConsts cc) {
     for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
         const int ei = e[i] - 2 * cc.k;
         const uint8_t* ri = R + i * ldr;
@@ -189,6 +180,7 @@ __global__ void __launch_bounds__(128) recombine_crt_kernel(
         const bool cvec = (reinterpret_cast<uintptr_t>(ci) & 15) == 0;
         for (int64_t j = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N;
              j += 4 * (int64_t)gridDim.x * blockDim.x) {
+            const bool full = j + 3 < N;
             uint32_t v[S];
 #pragma unroll
             for (int t = 0; t < S; ++t) {
@@ -202,51 +194,30 @@ __global__ void __launch_bounds__(128) recombine_crt_kernel(
                         if (j + b < N) v[t] |= (uint32_t)__ldg(g + b) << (8 * b);
                 }
             }
-            // two columns at a time (two independent chains), byte u of each
-            // plane word by one byte permute
-            double o[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 1
-            for (int up = 0; up < 2; ++up) {
-                if (j + 2 * up >= N) break;
-                const uint32_t s0 = 0x4440u + 2u * (uint32_t)up, s1 = s0 + 1u;
-                uint64_t a[2][4] = {}, qa[2] = {};
+            int64_t hi[4];
+            uint64_t lo[4];
+            crt_reconstruct4<S>(v, cc, hi, lo);
+            int fj[4];
+            if (full) {
 #pragma unroll
-                for (int t = 0; t < S; ++t) {
-                    const uint32_t x0 = __byte_perm(v[t], 0u, s0), x1 = __byte_perm(v[t], 0u, s1);
+                for (int u = 0; u < 4; ++u) fj[u] = __ldg(f + j + u);
+            } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        a[0][q] = mad_wide(x0, cc.ml[t][q], a[0][q]);
-                        a[1][q] = mad_wide(x1, cc.ml[t][q], a[1][q]);
-                    }
-                    qa[0] = mad_wide(x0, cc.F[t], qa[0]);
-                    qa[1] = mad_wide(x1, cc.F[t], qa[1]);
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t jj = j + 2 * up + h;
-                    const uint32_t qi = (uint32_t)((qa[h] + 0x80000000ull) >> 32);
-                    int64_t c = (int64_t)a[h][0] - (int64_t)((uint64_t)qi * cc.mn[0]);
-                    const uint32_t w0 = (uint32_t)c;
-                    c = (c >> 32) + (int64_t)a[h][1] - (int64_t)((uint64_t)qi * cc.mn[1]);
-                    const uint32_t w1 = (uint32_t)c;
-                    c = (c >> 32) + (int64_t)a[h][2] - (int64_t)((uint64_t)qi * cc.mn[2]);
-                    const uint32_t w2 = (uint32_t)c;
-                    c = (c >> 32) + (int64_t)a[h][3] - (int64_t)((uint64_t)qi * cc.mn[3]);
-                    const uint32_t w3 = (uint32_t)c;
-                    const int64_t hi = (int64_t)(((uint64_t)w3 << 32) | w2);
-                    const uint64_t lo = ((uint64_t)w1 << 32) | w0;
-                    // a column past N computes from the row's padding and is not stored
-                    const double w = i128_scaled_to_double_rn(hi, lo, ei + (jj < N ? __ldg(f + jj) : 0));
-                    double out = (alpha == 1.0) ? w : (alpha == -1.0) ? -w : alpha * w;
-                    if (beta != 0.0 && jj < N) out = __fma_rn(beta, ci[jj], out);
-                    if (up == 0) {
-                        if (h == 0) o[0] = out; else o[1] = out;
-                    } else {
-                        if (h == 0) o[2] = out; else o[3] = out;
-                    }
-                }
+                for (int u = 0; u < 4; ++u) fj[u] = j + u < N ? __ldg(f + j + u) : 0;
             }
-            if (cvec && j + 3 < N) {
+            double o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                // a column past N computes from the row's padding and is not stored
+                const double w = i128_scaled_to_double_rn(hi[u], lo[u], ei + fj[u]);
+                o[u] = amode == 0 ? w : amode == 1 ? -w : alpha * w;
+            }
+            if (bmode) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (full || j + u < N) o[u] = __fma_rn(beta, ci[j + u], o[u]);
+            }
+            if (cvec && full) {
                 reinterpret_cast<double2*>(ci + j)[0] = make_double2(o[0], o[1]);
                 reinterpret_cast<double2*>(ci + j)[1] = make_double2(o[2], o[3]);
             } else {
@@ -264,14 +235,16 @@ alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const 
                                 int64_t M, int64_t N, double alpha, double beta, double* C,
                                 int64_t ldc) {
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
-    const CrtRecConsts cc = crt_consts(n, k);
+    const CrtRecConsts cc = crt_rec_consts(n, k);
     const bool rvec = (reinterpret_cast<uintptr_t>(R) & 3) == 0 && rplane % 4 == 0 && ldr % 4 == 0;
+    const int amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
+    const int bmode = beta != 0.0 ? 1 : 0;
     // four columns per thread, 128-thread blocks: 512 columns per block, as
     // the grid was sized
 #define ALP_CRT_REC_CASE(x)                                                                       \
     case x:                                                                                      \
         recombine_crt_kernel<x><<<grid, 128, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
-                                                      ldc, rvec, cc);                            \
+                                                      ldc, rvec, amode, bmode, cc);              \
         break;
     switch (n) {
         ALP_CRT_REC_CASE(4) ALP_CRT_REC_CASE(5) ALP_CRT_REC_CASE(6) ALP_CRT_REC_CASE(7)

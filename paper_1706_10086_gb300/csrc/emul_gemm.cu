@@ -111,6 +111,9 @@ struct EmulGemmParams {
     uint64_t t_ranges;
     uint64_t timeout_ns;
     int* err;
+    // test hook: block 0's producer arms pipeline stage inject_skip_it (its
+    // running stage count) without issuing the copies (-1: off)
+    int64_t inject_skip_it;
     // modular scheme: y_l = (Mn / m_l)^-1 mod m_l, the weight of residue l
     uint8_t crt_y[kCrtMaxModuli];
 };
@@ -332,6 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_prefetch_desc(&tmA);
             tma_prefetch_desc(&tmB);
             uint32_t it = 0;
+            int64_t skipped = -1;
             bool ok = true;
             for (int j = 0; j < njobs && ok; ++j) {
                 const uint32_t jd = jobs[j];
@@ -343,6 +347,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&full[st], kStageBytes);
+                    if ((int64_t)it == prm.inject_skip_it && blockIdx.x == 0) {
+                        skipped = it;   // fault injection: the stage never fills
+                        continue;
+                    }
                     unsigned char* a = tiles + st * kStageBytes;
                     tma_load_3d(a, &tmA, &full[st], kb * kTK, m0, job_p(jd) - 1);
                     tma_load_3d(a + kATile, &tmB, &full[st], kb * kTK, n0, job_q(jd) - 1);
@@ -350,8 +358,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // every copy issued must land before the block may exit
             for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
-                mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr, prm.err,
-                                  false);
+                if ((int64_t)j != skipped)
+                    mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, tmo, nullptr,
+                                      prm.err, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -419,6 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // stages and chunks in both blocks by multicast commits; block 1's epilogue
 // hands accumulators back on block 0's "acce" barriers.
 constexpr int kPairStages = 6;
+// Limit of the pair producer's final waits once the launch has aborted (2 ms).
+constexpr uint64_t kDrainNs = 2000000ull;
 constexpr uint32_t kPairBTile = kBTile / 2;
 constexpr uint32_t kPairStageBytes = kATile + kPairBTile;
 constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + 1024 /*align*/ + 256 /*barriers*/ +
@@ -512,17 +523,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     if (leader) mbar_arrive_expect_tx(&full[st], 2 * kPairStageBytes);
+                    // fault injection: block 0 issues no copy, the stage never fills
+                    if ((int64_t)it == prm.inject_skip_it && blockIdx.x == 0) continue;
                     unsigned char* a = tiles + st * kPairStageBytes;
                     tma_load_3d_pair(a, &tmA, full0 + st * 8, kb * kTK, m0, job_p(jd) - 1);
                     tma_load_3d_pair(a + kATile, &tmB, full0 + st * 8, kb * kTK,
                                      n0 + (int)rank * (kTN / 2), job_q(jd) - 1);
                 }
             }
-            // the MMAs of every issued stage must have consumed it (so this
-            // block's copies have landed) and its release reached this block
+            // The MMAs of every issued stage must have consumed it (so this
+            // block's copies have landed, on block 0's barrier) and its
+            // release reached this block.  After an abort (this block's, or a
+            // timeout recorded by any block) the stages not consumed are never
+            // released: their copies were issued before the abort was seen and
+            // land within microseconds, so those waits are cut to kDrainNs.
+            const bool aborted =
+                *abort_flag ||
+                (prm.err && *reinterpret_cast<volatile int*>(prm.err) == ALP_ERR_TIMEOUT);
+            const uint64_t drain = aborted && tmo > kDrainNs ? kDrainNs : tmo;
             for (uint32_t j = it > (uint32_t)kPairStages ? it - kPairStages : 0; j < it; ++j)
-                mbar_wait_bounded(&empty[j % kPairStages], (j / kPairStages) & 1, tmo, nullptr,
-                                  prm.err, false);
+                if (!mbar_wait_bounded(&empty[j % kPairStages], (j / kPairStages) & 1, drain,
+                                       nullptr, prm.err, false) &&
+                    aborted)
+                    break;   // not consumed; neither is any later stage
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
@@ -562,10 +585,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_commit_pair(&accf[b], 3);
             }
             // all MMAs must have completed before TMEM and shared memory go away,
-            // and both blocks' hand-backs of the last two chunks must have arrived
+            // and both blocks' hand-backs of the last two chunks must have
+            // arrived.  After an abort the epilogue warps leave without handing
+            // back; an arrival block 1 did send precedes its cluster barrier
+            // arrival, which block 0 waits for before it exits.
             umma_commit_pair(done, 1);
             mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
-            for (int job = njobs > 2 ? njobs - 2 : 0; job < njobs; ++job)
+            for (int job = njobs > 2 ? njobs - 2 : 0; job < njobs && ok; ++job)
                 mbar_wait_bounded(&acce[job & 1], (job >> 1) & 1, tmo, nullptr, prm.err, false);
         }
     } else {
@@ -689,6 +715,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     p.group_m = group_m > 0 ? group_m : emul_group_m(arr == kEmulPair);
     p.timeout_ns = wait_timeout_ns();
     p.err = device_error_word();
+    p.inject_skip_it = inject_skip_kt();
     const int tiles = (int)(tiles_m * tiles_n);
     p.n_full = 0x7fffffff;   // every block a whole tile unless split below
     p.pieces = 1;

@@ -8,6 +8,8 @@ import pytest
 
 from paper_1706_10086_gb300 import inputs
 
+from .test_emul_crt_gpu import crt_k
+
 pytestmark = pytest.mark.gpu
 
 
@@ -33,3 +35,47 @@ def test_wait_timeout_reported_and_context_usable(alp, orc):
     torch.cuda.synchronize()
     assert alp.alp_get_device_error() == alp.ALP_OK
     assert np.array_equal(dC.cpu().numpy(), orc.gemm(1.0, A, B, 0.0))
+
+
+@pytest.mark.parametrize("cfg", [(128, 256, 64, 1, 0, 8), (256, 256, 64, 2, 0, 8)],
+                         ids=["one_block", "cta_pair"])
+def test_emulated_wait_timeout_reported_and_context_usable(alp, orc, cfg):
+    """The emulated path's tensor-core kernel, one block per tile and CTA
+    pairs: block 0's producer arms its fourth pipeline stage without issuing
+    the copies, the MMA thread's wait on that stage runs out (limit 200 ms),
+    ALP_ERR_TIMEOUT is recorded, every block of the launch leaves (its own
+    copies landed, its TMEM freed), and the next call on the same context is
+    bit-exact against the oracle's definition of the modular scheme."""
+    import time
+
+    import torch
+    M, N, K, n = 512, 768, 2048, 4
+    CRT = alp.ALP_SLICE_BF16_CRT
+    A, B, C = inputs.gemm_operands(7200 + cfg[0], M, N, K, kind="scaled", phi=2)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.from_numpy(C).cuda()
+    ws = alp.alp_gemm_f64_emul_workspace(M, N, K, n, CRT)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    alp.alp_tune_set_cached(M, N, K, alp.ALP_PATH_EMUL, cfg)
+    alp.alp_set_wait_timeout_ms(200)
+    alp.alp_debug_inject_skip(3)
+    try:
+        t0 = time.perf_counter()
+        alp.alp_gemm_f64_emul(M, N, K, 1.5, dA, K, dB, N, 0.5, dC, N, n, CRT, work, ws)
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        assert alp.alp_get_device_error() == alp.ALP_ERR_TIMEOUT
+        assert elapsed < 5.0, elapsed       # one limit, not one per stage or block
+    finally:
+        alp.alp_debug_inject_skip(-1)
+        alp.alp_set_wait_timeout_ms(4000)
+    try:
+        dC = torch.from_numpy(C).cuda()
+        alp.alp_gemm_f64_emul(M, N, K, 1.5, dA, K, dB, N, 0.5, dC, N, n, CRT, work, ws)
+        torch.cuda.synchronize()
+        assert alp.alp_get_device_error() == alp.ALP_OK
+    finally:
+        alp.alp_tune_clear_cache()
+    want, rc = orc.crt_gemm(1.5, A, B, 0.5, C, crt_k(K, n))
+    assert rc == 0 and np.array_equal(dC.cpu().numpy(), want)
