@@ -168,7 +168,7 @@ CrtRecConsts crt_rec_consts(int n, int k) {
 // beta term (bmode 1), decided on the host so that the loop holds no FP64
 // comparison.
 template <int S>
-__global__ void __launch_bounds__(128) recombine_crt_kernel(
+__global__ void __launch_bounds__(128, 5) recombine_crt_kernel(
     const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
     const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
     double* __restrict__ C, int64_t ldc, bool rvec, int amode, int bmode,

@@ -192,50 +192,39 @@ __global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
 
 // Nearest double (ties to even) of the 128-bit two's-complement integer
 // hi:lo, multiplied by 2^E: built from 64-bit integer operations on the IEEE
-// encoding (FP64 arithmetic is slow on this GPU).  When the scaled result
-// would leave the normal range it falls back to ldexp of the rounded value
-// (which rounds a subnormal result a second time, as the definition does).
+// encoding (FP64 arithmetic is slow on this GPU), with selects instead of
+// branches for the sign and the rounding (they differ between neighbouring
+// elements).  When the scaled result would leave the normal range it falls
+// back to ldexp of the rounded value (which rounds a subnormal result a second
+// time, as the definition does).
 __device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_t lo, int E) {
-    const bool neg = hi_s < 0;
-    uint64_t hi = (uint64_t)hi_s;
-    if (neg) {   // magnitude: two's complement negation
-        lo = ~lo + 1;
-        hi = ~hi + (lo == 0 ? 1 : 0);
-    }
-    if ((hi | lo) == 0) return neg ? -0.0 : 0.0;
-    // top: the 64 bits below and including the leading one; sticky: any bit below
-    uint64_t top;
-    bool sticky;
-    int msb;
-    if (hi) {
-        const int n = __clzll((long long)hi);
-        top = n ? (hi << n) | (lo >> (64 - n)) : hi;
-        sticky = (n ? lo << n : lo) != 0;
-        msb = 127 - n;
-    } else {
-        const int n = __clzll((long long)lo);
-        top = lo << n;
-        sticky = false;
-        msb = 63 - n;
-    }
+    // magnitude: (x XOR s) - s with s = 0 or all ones, a 128-bit subtraction
+    const uint64_t sgn = (uint64_t)(hi_s >> 63);
+    uint64_t l = lo ^ sgn, h = (uint64_t)hi_s ^ sgn;
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %2;" : "+l"(l), "+l"(h) : "l"(sgn));
+    if ((h | l) == 0) return 0.0;
+    // top: the 64 bits from the leading one down; sticky: any one bit below
+    const bool hz = h == 0;
+    const uint64_t x = hz ? l : h, y = hz ? 0ull : l;
+    const int nz = __clzll((long long)x);
+    const uint64_t top = (x << nz) | ((y >> 1) >> (63 - nz));
+    const uint32_t sticky = (y << nz) != 0 ? 1u : 0u;
+    int msb = (hz ? 63 : 127) - nz;
     uint64_t m = top >> 11;                      // 53 bits, leading one at bit 52
-    const uint64_t low = top & 0x7FF;            // 11 bits below them
-    if (low > 0x400 || (low == 0x400 && (sticky || (m & 1)))) {
-        ++m;
-        if (m >> 53) {
-            m >>= 1;
-            ++msb;
-        }
-    }
+    const uint32_t low = (uint32_t)top & 0x7FFu;
+    const uint32_t up = (low > 0x400u ? 1u : 0u) |
+                        (low == 0x400u ? (sticky | ((uint32_t)m & 1u)) : 0u);
+    m += up;
+    const uint32_t carry = (uint32_t)(m >> 53);  // rounded up to 2^53
+    m >>= carry;
+    msb += (int)carry;
     // m in [2^52, 2^53): value = m * 2^(msb - 52) * 2^E
     const int be = msb + E + 1023;
-    if (be >= 1 && be <= 2046) {
-        const uint64_t bits =
-            ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & ((1ull << 52) - 1));
-        return __longlong_as_double((long long)bits);
-    }
+    const uint64_t frac = m & ((1ull << 52) - 1);
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double((long long)((sgn << 63) | ((uint64_t)be << 52) | frac));
     const double v = __longlong_as_double(
-        (long long)(((uint64_t)neg << 63) | ((uint64_t)(msb + 1023) << 52) | (m & ((1ull << 52) - 1))));
+        (long long)((sgn << 63) | ((uint64_t)(msb + 1023) << 52) | frac));
     return ldexp(v, E);
 }
 
