@@ -272,6 +272,46 @@ def evaluate(model, train_ds, test_ds, tuning_shape=(10240, 10240, 10240), tunin
     return res
 
 
+def validate_full_runs(model, train_ds, test_ds, tuning_ds=None, count=50, max_flops=4e11,
+                       seed=1706 + 7, runs=2):
+    """Checks the proxy-based regret on whole problems: for up to `count`
+    held-out (shape, path) cases with 2MNK <= max_flops (chosen with a seeded
+    generator), times on the full problem the configs chosen by the MLP, by
+    the config tuned once, by the nearest training shape and the proxy
+    sweep's winner, and returns per choice the mean and p90 of the proxy
+    regret and of the full-run regret against the fastest of those four, plus
+    how often the proxy winner is the fastest on the full run."""
+    nat, emu = config_lists()
+    allc = nat + emu
+    flops = 2.0 * test_ds["M"] * test_ds["N"] * test_ds["K"]
+    idx = np.where(flops <= max_flops)[0]
+    pick = idx[np.argsort(inputs.uniform(seed, 0, (len(idx),)))[:count]]
+    sub = {k: (v[pick] if isinstance(v, np.ndarray) and len(v) == len(test_ds["M"]) else v)
+           for k, v in test_ds.items()}
+    choices = {"mlp": choose_by_model(model, sub),
+               "fixed_tuned_once": fixed_config_choice(train_ds, sub, tuning_ds=tuning_ds,
+                                                       tuning_shape=(10240, 10240, 10240)),
+               "nearest_shape": nearest_shape_choice(train_ds, sub),
+               "proxy_best": np.array([int(np.nanargmin(r)) for r in sub["times"]])}
+    full = {name: np.empty(len(pick)) for name in choices}
+    for i in range(len(pick)):
+        M, N, K, p = (int(sub["M"][i]), int(sub["N"][i]), int(sub["K"][i]), int(sub["path"][i]))
+        cache = {}
+        for name, ch in choices.items():
+            c = int(ch[i])
+            if c not in cache:
+                cache[c] = alp.alp_tune_time_config(M, N, K, alp.ALP_PATH_EMUL if p else
+                                                    alp.ALP_PATH_NATIVE, allc[c], False, runs)
+            full[name][i] = cache[c]
+    best_full = np.min(np.stack(list(full.values())), axis=0)
+    res = {"cases": int(len(pick)), "max_flops": max_flops,
+           "proxy_winner_fastest_on_full_run": float(np.mean(full["proxy_best"] <= best_full))}
+    for name, ch in choices.items():
+        res[name] = {"proxy": summarize(regret(sub, ch)),
+                     "full_run_vs_best_of_four": summarize(full[name] / best_full - 1.0)}
+    return res
+
+
 def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
                          tiles=(32, 64, 128), bks=(16, 32), log=None):
     """Autotunes the batched GEMM's tile per size class: for every class
@@ -366,7 +406,7 @@ def tune_batched_classes(M, N, K, pA, pB, pC, alpha=1.5, beta=0.5, runs=3,
 
 
 def run(db, n_train=2000, n_test=500, lo=64, hi=16384, paths=("native", "emul"), runs=2,
-        epochs=3000, lr=3e-3, out=None, log_every=100):
+        epochs=3000, lr=3e-3, out=None, log_every=100, validate=0):
     """The whole predictor workload: sweep, train on the GPU, evaluate."""
     import time
     seed = inputs.workload_seed("mlp_predictor")
@@ -399,6 +439,11 @@ def run(db, n_train=2000, n_test=500, lo=64, hi=16384, paths=("native", "emul"),
         sub = {k: (v[sel] if isinstance(v, np.ndarray) and len(v) == len(sel) else v)
                for k, v in test_ds.items()}
         res[pname] = evaluate(model, train_ds, sub, tuning_ds=tuning_ds)
+    if validate:
+        t0 = time.time()
+        res["full_run_validation"] = validate_full_runs(model, train_ds, test_ds, tuning_ds,
+                                                        count=validate)
+        res["full_run_validation"]["seconds"] = round(time.time() - t0, 1)
     control = dataset([r for r in recs if (r["M"], r["N"], r["K"]) == tuning_shapes[1]])
     nat, _ = config_lists()
     res["tuning_shape_winners"] = {
@@ -422,7 +467,9 @@ if __name__ == "__main__":
     ap.add_argument("--runs", type=int, default=2)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--paths", default="native,emul")
+    ap.add_argument("--validate", type=int, default=0,
+                    help="held-out cases also timed on whole problems")
     a = ap.parse_args()
     res, _ = run(a.db, a.train, a.test, paths=tuple(a.paths.split(",")), runs=a.runs,
-                 epochs=a.epochs, out=a.out)
+                 epochs=a.epochs, out=a.out, validate=a.validate)
     print(json.dumps({k: v for k, v in res.items() if k != "loss_history"}))
