@@ -22,7 +22,9 @@
  *   pointers owned by the caller; the library never frees them.  "h"-prefixed
  *   arrays and alp_config / out-parameters are HOST pointers.
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *   stream).  GEMM calls are asynchronous and enqueue work only on `stream`.
+ *   stream).  GEMM calls are asynchronous and enqueue work only on `stream`;
+ *   the one exception is the modular scheme with nslices = 0, which waits for
+ *   its operand statistics once (alp_emul_crt_choose).
  * BLAS semantics (the paper does not say): beta == 0 reads no C (NaN in C does
  *   not propagate); alpha == 0 or K == 0 reads neither A nor B and sets
  *   C = beta*C; M == 0 or N == 0 returns ALP_OK without launching anything.
