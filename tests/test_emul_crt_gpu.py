@@ -246,6 +246,47 @@ def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
     assert np.array_equal(dC.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("cfg", [None, (256, 256, 64, 2, 0, 1), (128, 256, 64, 1, 0, 8)])
+@pytest.mark.parametrize("M,N,K,n", [(1000, 1300, 700, 15), (3 * 256 + 1, 5 * 256 - 3, 2100, 13),
+                                     (64, 2000, 300, 16), (300, 200, 5000, 14)])
+def test_crt_gemm_call_matches_its_stages(alp, orc, cfg, M, N, K, n):
+    """The GEMM call for both block arrangements, on shapes whose last wave is
+    cut into pieces by moduli and on ragged ones: bit-exact against the
+    oracle's definition on rows across tile edges, and equal element for
+    element to its stages run one by one through the C-ABI (exponents,
+    splits, alp_emul_slice_products, alp_emul_recombine_crt)."""
+    import torch
+    A, B, C = inputs.gemm_operands(5900 + M + N + n, M, N, K, kind="scaled", phi=3)
+    if cfg is not None:
+        alp.alp_tune_set_cached(M, N, K, alp.ALP_PATH_EMUL, cfg)
+    try:
+        got, st, err = run_crt(alp, A, B, C, -1.0, 0.25, n)
+    finally:
+        alp.alp_tune_clear_cache()
+    assert st == alp.ALP_OK and err == alp.ALP_OK
+    rows = np.unique(np.clip([0, 1, 127, 128, 129, 255, 256, 257, M // 2, M - 2, M - 1], 0, M - 1))
+    ref, rc = orc.crt_gemm(-1.0, A, B, 0.25, C, crt_k(K, n), rows=rows)
+    assert rc == 0 and np.array_equal(got[rows], ref)
+    kpad = (K + 63) // 64 * 64
+    ldg = (N + 255) // 256 * 256
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    de = torch.empty(M, dtype=torch.int32, device="cuda")
+    df = torch.empty(N, dtype=torch.int32, device="cuda")
+    alp.alp_emul_exponents(M, K, dA, K, 0, de)
+    alp.alp_emul_exponents(N, K, dB, N, 1, df)
+    da = torch.empty((n, M, kpad), dtype=torch.bfloat16, device="cuda")
+    db = torch.empty((n, N, kpad), dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(M, K, dA, K, 0, de, n, CRT, da, kpad)
+    alp.alp_emul_split(N, K, dB, N, 1, df, n, CRT, db, kpad)
+    G = torch.full((n, M, ldg), 255, dtype=torch.uint8, device="cuda")
+    alp.alp_emul_slice_products(M, N, K, n, CRT, da, db, kpad, G, ldg)
+    dC = torch.from_numpy(C.copy()).cuda()
+    alp.alp_emul_recombine_crt(M, N, K, n, G, ldg, de, df, -1.0, 0.25, dC, N)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    assert np.array_equal(got, dC.cpu().numpy())
+
+
 @pytest.mark.parametrize("n", list(range(4, 17)))
 def test_crt_recombine_rounding(alp, n):
     """alp_emul_recombine_crt on crafted residues: P anywhere in [-L, L],
