@@ -90,9 +90,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
                                                   int* err, bool follow_global = true) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (true) {
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort && *abort) return false;
+        // the global error word and the clock every 64 polls: a global load in
+        // every poll would delay noticing the phase by its latency
+        if ((i & 63u) != 0) continue;
         if (follow_global && err && *reinterpret_cast<volatile int*>(err) == ALP_ERR_TIMEOUT) {
             if (abort) *abort = 1;
             return false;

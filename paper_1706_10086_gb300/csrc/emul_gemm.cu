@@ -186,15 +186,33 @@ __device__ __forceinline__ void store4_and_zero(int32_t* g, uint32_t do_store, u
         : "memory");
 }
 
+// Hands accumulator b back to the MMA thread after this warp's drain of job
+// `job`: an arrive on acce[b] of this block, or, in block 1 of a CTA pair
+// (acce_remote = the shared::cluster address of block 0's acce), an arrive on
+// the local agg[b]; warp 2 waits for all kEpiWarps of them and then forwards
+// them to block 0 as one remote arrival of that count (remote arrivals from
+// one SM take their turns, so eight per chunk lengthen the hand-back).  A wait
+// that gives up leaves the hand-back undone; the launch is aborting.
+__device__ __forceinline__ void hand_back(uint64_t* acce, uint32_t acce_remote, uint64_t* agg,
+                                          uint32_t b, int job, int warp, uint64_t tmo,
+                                          volatile int* abort_flag, int* err) {
+    if (!acce_remote) {
+        mbar_arrive(&acce[b]);
+        return;
+    }
+    mbar_arrive(&agg[b]);
+    if (warp == 2 && mbar_wait_bounded(&agg[b], (job >> 1) & 1, tmo, abort_flag, err))
+        mbar_arrive_cluster(acce_remote + b * 8, kEpiWarps);
+}
+
 // Epilogue warps (2..9): for each finished chunk, drain this warp's 32 TMEM
 // lanes x 128 columns of accumulator b into exact int32 sums, hand the
-// accumulator back (an arrive on acce[b] of this block, or, when acce_remote
-// is nonzero, on the mbarrier at that shared::cluster address), and at the
-// end of a group store S^t to G[t-2].
+// accumulator back (hand_back), and at the end of a group store S^t to
+// G[t-2].
 __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const uint32_t* jobs,
                                               int njobs, uint32_t tmem_base, uint64_t* accf,
-                                              uint64_t* acce, uint32_t acce_remote, int m0,
-                                              int n0, int warp, int lane, uint64_t tmo,
+                                              uint64_t* acce, uint32_t acce_remote, uint64_t* agg,
+                                              int m0, int n0, int warp, int lane, uint64_t tmo,
                                               volatile int* abort_flag) {
     const int quarter = warp & 3;          // TMEM lanes this warp may access
     const int half = (warp - 2) >> 2;      // columns [128*half, 128*half + 128)
@@ -214,10 +232,7 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
         for (int c = 0; c < 4; ++c) tmem_drain32_cvt(taddr + c * 32, &acc[c * 32]);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-            if (acce_remote) mbar_arrive_cluster(acce_remote + b * 8);
-            else mbar_arrive(&acce[b]);
-        }
+        if (lane == 0) hand_back(acce, acce_remote, agg, b, job, warp, tmo, abort_flag, prm.err);
         const uint32_t jd = jobs[job];
         if (job_last(jd) && prm.crt) {
             // modular scheme: plane l of modulus m_l receives x = (Q y_l) mod
@@ -405,8 +420,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
         }
     } else {
-        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0], 0u, m0, n0, warp, lane, tmo,
-                      abort_flag);
+        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0], 0u, nullptr, m0, n0, warp,
+                      lane, tmo, abort_flag);
     }
     tc_fence_before();
     __syncwarp();
@@ -447,7 +462,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* accf = empty + kPairStages;
     uint64_t* acce = accf + 2;
     uint64_t* done = acce + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* agg = done + 1;   // block 1: its epilogue warps' hand-backs, gathered
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(agg + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     int* njobs_slot = const_cast<int*>(reinterpret_cast<volatile int*>(abort_flag + 1));
     uint32_t* jobs = reinterpret_cast<uint32_t*>(smem + kPairStages * kPairStageBytes + 256);
@@ -463,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], 2 * kEpiWarps);   // epilogue warps of both blocks
+            mbar_init(&agg[b], kEpiWarps);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -596,7 +613,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0],
-                      leader ? 0u : cluster_addr(acce, 0), m0, n0, warp, lane, tmo, abort_flag);
+                      leader ? 0u : cluster_addr(acce, 0), agg, m0, n0, warp, lane, tmo,
+                      abort_flag);
     }
     tc_fence_before();
     __syncwarp();

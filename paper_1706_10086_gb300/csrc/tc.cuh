@@ -106,6 +106,13 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
                  : "memory");
 }
+// `count` arrivals at once on an mbarrier of another block of the cluster.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster, uint32_t count) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(
+                     bar_cluster),
+                 "r"(count)
+                 : "memory");
+}
 
 // TMEM allocation for a CTA pair: one warp of each CTA executes each call.
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
