@@ -49,8 +49,9 @@ uint32_t crt_weight(int n, int l) {
     return 0;
 }
 
-// The splitter.  A' = RN(a 2^(k - e)) straight from the IEEE fields: a =
-// +-mant 2^E, shifted left when sh = E + k - e >= 0 (exact; |A'| < 2^k since
+// The splitter.  A' = RN(a 2^(k - e)): for k <= 51 (and a normal power of two
+// 2^(k - e)) by one FP64 fma, else straight from the IEEE fields: a =
+// +-mant 2^E, shifted left when sh = E + k - e >= 0 (exact; |A'| <= 2^k since
 // |a| < 2^e), else rounded half to even at bit -sh (0 below 2^-54 of mant).
 // Then the signed A' = hi 2^40 + mid 2^20 + lo (hi signed, |hi| <= 2^20; mid,
 // lo in [0, 2^20)) and per modulus x = hi (2^40 mod m) + mid (2^20 mod m) + lo
@@ -67,25 +68,40 @@ struct CrtSplit {
     __device__ __forceinline__ void split(double a, int e, int (&d)[S]) const {
         const uint64_t bits = (uint64_t)__double_as_longlong(a);
         const int ex = (int)((bits >> 52) & 0x7FF);
-        uint64_t mant = bits & ((1ull << 52) - 1);
-        int E = -1074;
-        if (ex == 0x7FF) mant = 0;   // Inf/NaN: reported by the scan; residues 0
-        else if (ex) {
-            mant |= 1ull << 52;
-            E = ex - 1075;
-        }
-        const int sh = E + k - e;
-        uint64_t u;
-        if (sh >= 0) {
-            u = mant << (sh > 63 ? 63 : sh);
-        } else if (sh < -54) {
-            u = 0;
+        const int se = k - e;
+        int64_t v;
+        if (k <= 51 && se >= -1022 && se <= 1023) {
+            // a 2^se is exact (a scaling by a normal power of two; a result
+            // below the normal range is below 1/2 in magnitude), so one fma
+            // with 1.5 2^52 rounds it to the nearest integer, ties to even:
+            // |a 2^se| <= 2^51 keeps the sum in [2^52, 2^53], where the
+            // encoding grows by one per unit, and the difference of the two
+            // encodings is the integer
+            const double y =
+                __fma_rn(a, __longlong_as_double((long long)(se + 1023) << 52), 6755399441055744.0);
+            v = ex == 0x7FF ? 0 : (int64_t)__double_as_longlong(y) - 0x4338000000000000ll;
         } else {
-            const int r = -sh;
-            const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1), half = 1ull << (r - 1);
-            u = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+            uint64_t mant = bits & ((1ull << 52) - 1);
+            int E = -1074;
+            if (ex == 0x7FF) mant = 0;   // Inf/NaN: reported by the scan; residues 0
+            else if (ex) {
+                mant |= 1ull << 52;
+                E = ex - 1075;
+            }
+            const int sh = E + se;
+            uint64_t u;
+            if (sh >= 0) {
+                u = mant << (sh > 63 ? 63 : sh);
+            } else if (sh < -54) {
+                u = 0;
+            } else {
+                const int r = -sh;
+                const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1),
+                               half = 1ull << (r - 1);
+                u = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+            }
+            v = (int64_t)bits < 0 ? -(int64_t)u : (int64_t)u;
         }
-        const int64_t v = (int64_t)bits < 0 ? -(int64_t)u : (int64_t)u;
         const int32_t hi = (int32_t)(v >> 40);
         const uint32_t mid = (uint32_t)(v >> 20) & 0xFFFFFu, lo = (uint32_t)v & 0xFFFFFu;
 #pragma unroll

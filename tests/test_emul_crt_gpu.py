@@ -163,6 +163,50 @@ def test_crt_alpha_beta_padding_special_cases_and_limits(alp, orc):
                                   raise_on_error=False) == alp.ALP_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("n", [4, 8, 14])
+def test_crt_split_rounding_at_the_range_ends(alp, orc, n):
+    """k <= 51 (here 4, 8 or 14 moduli): the split rounds a 2^(k - e) by one
+    FP64 fma when 2^(k - e) is a normal double, else from the IEEE fields.
+    Rows at the top of the range (entries near the largest double, scale
+    2^(k - 1024)), rows of tiny entries (scale up to 2^1023), rows of
+    subnormals (scale beyond 2^1023: the field path), exact ties at the units
+    of the scaled value, and a column of subnormals: bit-exact against the
+    oracle's definition, and the residues equal Python's."""
+    import torch
+    M, N, K = 40, 300, 200
+    k = crt_k(K, n)
+    assert k <= 51
+    rng = np.random.default_rng(8000 + n)
+    A = rng.uniform(-1, 1, (M, K))
+    B = rng.uniform(-1, 1, (K, N))
+    A[0] = rng.uniform(-1, 1, K) * 1.7976931348623157e308        # e = 1024
+    A[1] = rng.uniform(-1, 1, K) * 2.0 ** -1000                  # scale 2^(k + 1000)
+    A[2] = rng.integers(-4, 5, K) * 5e-324                       # subnormal row
+    A[3] = np.ldexp(2 * rng.integers(-2 ** 20, 2 ** 20, K) + 1.0, -k - 1)   # ties
+    A[3, 0] = 1.0 - 2.0 ** -53                                   # rounds up to 2^k
+    A[4] = rng.uniform(-1, 1, K) * 2.0 ** (-1022 - k + 30)       # scale 2^1023 - ...
+    B[:, 5] = rng.integers(-3, 4, K) * 5e-324                    # subnormal column
+    B[:, 6] = rng.uniform(-1, 1, K) * 2.0 ** 1000
+    got, st, err = run_crt(alp, A, B, None, 1.0, 0.0, n)
+    assert st == alp.ALP_OK and err == alp.ALP_OK
+    ref, rc = orc.crt_gemm(1.0, A, B, 0.0, None, k)
+    assert rc == 0 and np.array_equal(got, ref)
+    # the residues of the crafted rows, against exact integers formed here
+    e, _ = orc.row_exponents(A)
+    kpad = (K + 63) // 64 * 64
+    dA = torch.from_numpy(A).cuda()
+    de = torch.from_numpy(e).cuda()
+    da = torch.zeros((n, M, kpad), dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(M, K, dA, K, 0, de, n, CRT, da, kpad)
+    torch.cuda.synchronize()
+    ra = da.float().cpu().numpy().astype(np.int64)
+    for i in range(6):
+        ints = [round(Fraction(float(a)) * Fraction(2) ** (k - int(e[i]))) for a in A[i]]
+        for l in range(n):
+            want = residue(np.array(ints, dtype=object), MODULI[l]).astype(np.int64)
+            assert np.array_equal(ra[l, i, :K], want), (i, l)
+
+
 @pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
 def test_crt_transposed_operands_bit_exact(alp, orc, ta, tb):
     import torch
