@@ -246,6 +246,99 @@ __global__ void __launch_bounds__(128, 5) recombine_crt_kernel(
     }
 }
 
+// The same reconstruction with the residue rows staged in shared memory: a
+// block keeps 512 columns (four per thread) and walks its rows, thread 0
+// prefetching kCrtRecSlots rows ahead by bulk copies (one per plane, 512 bytes
+// or the row's 16-byte-rounded tail), so that the loads of later rows overlap
+// the arithmetic of this one.  Needs R, the plane stride and the row stride
+// 16-byte aligned (the copies may read up to 15 padding bytes of a row past N).
+// Every thread waits for its row's slot (bounded); one block barrier per row
+// then agrees on success and frees the slot for its refill.
+constexpr int kCrtRecSlots = 4;
+
+template <int S>
+__global__ void __launch_bounds__(128, 5) recombine_crt_staged_kernel(
+    const uint8_t* __restrict__ R, int64_t rplane, int64_t ldr, const int32_t* __restrict__ e,
+    const int32_t* __restrict__ f, int64_t M, int64_t N, double alpha, double beta,
+    double* __restrict__ C, int64_t ldc, int amode, int bmode, const CrtRecConsts cc,
+    uint64_t tmo, int* err) {
+    __shared__ __align__(16) uint8_t slots[kCrtRecSlots][S][512];
+    __shared__ uint64_t full[kCrtRecSlots];
+    const int64_t j0 = (int64_t)blockIdx.x * 512;
+    const int64_t jt = j0 + 4 * threadIdx.x;
+    const uint32_t cb = (uint32_t)((N - j0 >= 512 ? 512 : ((N - j0) + 15) / 16 * 16));
+    // rows of this block: blockIdx.y, blockIdx.y + gridDim.y, ...
+    const int64_t nrows = M > blockIdx.y ? (M - blockIdx.y + gridDim.y - 1) / gridDim.y : 0;
+    auto row_of = [&](int64_t r) { return (int64_t)blockIdx.y + r * gridDim.y; };
+    auto issue = [&](int64_t r) {
+        const int slot = (int)(r % kCrtRecSlots);
+        mbar_arrive_expect_tx(&full[slot], (uint32_t)S * cb);
+        const uint8_t* src = R + row_of(r) * ldr + j0;
+#pragma unroll
+        for (int t = 0; t < S; ++t) bulk_load(slots[slot][t], src + (int64_t)t * rplane, cb, &full[slot]);
+    };
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kCrtRecSlots; ++i) mbar_init(&full[i], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int64_t r = 0; r < nrows && r < kCrtRecSlots; ++r) issue(r);
+    int fj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) fj[u] = jt + u < N ? __ldg(f + jt + u) : 0;
+    const bool cfull = jt + 3 < N;
+    int64_t r = 0;
+    for (; r < nrows; ++r) {
+        const int slot = (int)(r % kCrtRecSlots);
+        bool ok = mbar_wait_bounded(&full[slot], (uint32_t)(r / kCrtRecSlots) & 1, tmo, nullptr, err);
+        uint32_t v[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) v[t] = *reinterpret_cast<const uint32_t*>(&slots[slot][t][4 * threadIdx.x]);
+        // all threads have read the slot (and agree that it had arrived)
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        if (threadIdx.x == 0 && r + kCrtRecSlots < nrows) {
+            fence_proxy_async_smem();
+            issue(r + kCrtRecSlots);
+        }
+        if (jt >= N) continue;
+        const int64_t i = row_of(r);
+        const int ei = e[i] - 2 * cc.k;
+        double* ci = C + i * ldc + jt;
+        int64_t hi[4];
+        uint64_t lo[4];
+        crt_reconstruct4<S>(v, cc, hi, lo);
+        double o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            // a column past N computes from padding bytes and is not stored
+            const double w = i128_scaled_to_double_rn(hi[u], lo[u], ei + fj[u]);
+            o[u] = amode == 0 ? w : amode == 1 ? -w : alpha * w;
+        }
+        if (bmode) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cfull || jt + u < N) o[u] = __fma_rn(beta, ci[u], o[u]);
+        }
+        if (cfull && (reinterpret_cast<uintptr_t>(ci) & 15) == 0) {
+            reinterpret_cast<double2*>(ci)[0] = make_double2(o[0], o[1]);
+            reinterpret_cast<double2*>(ci)[1] = make_double2(o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cfull || jt + u < N) ci[u] = o[u];
+        }
+    }
+    if (r < nrows && threadIdx.x == 0) {
+        // aborted: the copies already issued (rows r .. r + slots - 1) must
+        // land before the block's shared memory goes away
+        for (int64_t q = r; q < nrows && q < r + kCrtRecSlots; ++q)
+            mbar_wait_bounded(&full[q % kCrtRecSlots], (uint32_t)(q / kCrtRecSlots) & 1, tmo,
+                              nullptr, err, false);
+    }
+}
+
 alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const uint8_t* R,
                                 int64_t rplane, int64_t ldr, const int32_t* e, const int32_t* f,
                                 int64_t M, int64_t N, double alpha, double beta, double* C,
@@ -253,14 +346,22 @@ alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const 
     if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
     const CrtRecConsts cc = crt_rec_consts(n, k);
     const bool rvec = (reinterpret_cast<uintptr_t>(R) & 3) == 0 && rplane % 4 == 0 && ldr % 4 == 0;
+    const bool staged =
+        (reinterpret_cast<uintptr_t>(R) & 15) == 0 && rplane % 16 == 0 && ldr % 16 == 0;
     const int amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
     const int bmode = beta != 0.0 ? 1 : 0;
+    const uint64_t tmo = wait_timeout_ns();
+    int* err = device_error_word();
     // four columns per thread, 128-thread blocks: 512 columns per block, as
     // the grid was sized
 #define ALP_CRT_REC_CASE(x)                                                                       \
     case x:                                                                                      \
-        recombine_crt_kernel<x><<<grid, 128, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha, beta, C, \
-                                                      ldc, rvec, amode, bmode, cc);              \
+        if (staged)                                                                              \
+            recombine_crt_staged_kernel<x><<<grid, 128, 0, st>>>(                                 \
+                R, rplane, ldr, e, f, M, N, alpha, beta, C, ldc, amode, bmode, cc, tmo, err);    \
+        else                                                                                     \
+            recombine_crt_kernel<x><<<grid, 128, 0, st>>>(R, rplane, ldr, e, f, M, N, alpha,     \
+                                                          beta, C, ldc, rvec, amode, bmode, cc); \
         break;
     switch (n) {
         ALP_CRT_REC_CASE(4) ALP_CRT_REC_CASE(5) ALP_CRT_REC_CASE(6) ALP_CRT_REC_CASE(7)

@@ -202,11 +202,11 @@ __device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_
     const uint64_t sgn = (uint64_t)(hi_s >> 63);
     uint64_t l = lo ^ sgn, h = (uint64_t)hi_s ^ sgn;
     asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %2;" : "+l"(l), "+l"(h) : "l"(sgn));
-    if ((h | l) == 0) return 0.0;
+    const bool zero = (h | l) == 0;   // selected at the end, not branched on
     // top: the 64 bits from the leading one down; sticky: any one bit below
     const bool hz = h == 0;
     const uint64_t x = hz ? l : h, y = hz ? 0ull : l;
-    const int nz = __clzll((long long)x);
+    const int nz = __clzll((long long)x) & 63;   // 64 only for zero
     const uint64_t top = (x << nz) | ((y >> 1) >> (63 - nz));
     const uint32_t sticky = (y << nz) != 0 ? 1u : 0u;
     int msb = (hz ? 63 : 127) - nz;
@@ -221,6 +221,7 @@ __device__ __forceinline__ double i128_scaled_to_double_rn(int64_t hi_s, uint64_
     // m in [2^52, 2^53): value = m * 2^(msb - 52) * 2^E
     const int be = msb + E + 1023;
     const uint64_t frac = m & ((1ull << 52) - 1);
+    if (zero) return 0.0;
     if (be >= 1 && be <= 2046)
         return __longlong_as_double((long long)((sgn << 63) | ((uint64_t)be << 52) | frac));
     const double v = __longlong_as_double(
