@@ -199,8 +199,10 @@ alp_status alp_emul_recombine(int64_t M, int64_t N, int nslices, alp_slice_kind 
  *   |.| <= 2^k, e_i and f_j the exponents above),
  *   P = A' B' exact (|P| <= K 2^(2k) < Mn / 2),
  *   C = alpha * RN(P 2^(e_i + f_j - 2k))  (+ fma(beta, C, .) when beta != 0).
- * P is reached through its residues: the split writes out[l][r][k] = A'_rk mod
- * m_{l+1}, moved to [-m/2, m/2) (exact in bf16); the tensor-core stage sums
+ * P is reached through its residues: the split writes out[l][r][k] = a residue
+ * of A'_rk modulo m_{l+1} of magnitude at most 128 (exact in bf16; the one
+ * nearest to zero, or, for k <= 51, one modulus off it when A'/m lies within
+ * 0.003 of a half-integer); the tensor-core stage sums
  * Q_l = sum_k a_l b_l exactly (|Q_l| <= K 2^14, Q_l = P mod m_l) and writes
  * the byte x_l = (Q_l y_l) mod m_l, y_l = (Mn/m_l)^-1 mod m_l, into plane
  * l-1 of G; the recombination forms sum_l x_l (Mn/m_l) = P mod Mn in 128-bit

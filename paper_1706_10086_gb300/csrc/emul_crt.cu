@@ -53,15 +53,47 @@ uint32_t crt_weight(int n, int l) {
 // 2^(k - e)) by one FP64 fma, else straight from the IEEE fields: a =
 // +-mant 2^E, shifted left when sh = E + k - e >= 0 (exact; |A'| <= 2^k since
 // |a| < 2^e), else rounded half to even at bit -sh (0 below 2^-54 of mant).
-// Then the signed A' = hi 2^40 + mid 2^20 + lo (hi signed, |hi| <= 2^20; mid,
-// lo in [0, 2^20)) and per modulus x = hi (2^40 mod m) + mid (2^20 mod m) + lo
-// + b_m with b_m = m ceil(2^28 / m) + floor(m / 2), so that 0 < x < 2^30 and
-// x = A' + floor(m / 2) (mod m); the residue moved to [-floor(m/2),
-// ceil(m/2)) is (x mod m) - floor(m / 2), whose subtraction folds into the
-// bf16 packing.
+// The residues, written as the bf16 encodings of integers r = A' (mod m)
+// with |r| <= 128 (the tensor-core stage's exactness bound):
+//  * for k <= 51 (|A'| <= 2^51) in f32 arithmetic: A' = c3 2^39 + c2 2^26 +
+//    c1 2^13 + c0 (c3 signed, |c3| <= 2^12; c2, c1, c0 in [0, 2^13)), each
+//    chunk turned into a float through its encoding (no conversion
+//    instruction), and per modulus x = c3 (2^39 mod m) + c2 (2^26 mod m) +
+//    c1 (2^13 mod m) + c0 by three fmas, exact (|x| < 2^23); q = x * RN(1/m)
+//    rounded to an integer through 1.5 2^23, and r = x - q m by one fma,
+//    exact: q is RN(x / m) or one off it when x / m lies within 0.003 of a
+//    half-integer, so |r| <= m / 2 + 0.7, an integer at most 128;
+//  * otherwise in integers: A' = hi 2^40 + mid 2^20 + lo (hi signed, |hi| <=
+//    2^20; mid, lo in [0, 2^20)) and x = hi (2^40 mod m) + mid (2^20 mod m) +
+//    lo + b_m with b_m = m ceil(2^28 / m) + floor(m / 2), so that 0 < x < 2^30
+//    and x = A' + floor(m / 2) (mod m); r = (x mod m) - floor(m / 2) in
+//    [-floor(m/2), ceil(m/2)).
+// A float holding an integer of at most 8 significant bits has that
+// integer's bf16 encoding in its upper 16 bits, so packing two residues is
+// one byte permutation.
 __host__ __device__ constexpr uint32_t crt_split_bias(uint32_t m) {
     return m * (((1u << 28) + m - 1) / m) + m / 2;
 }
+// The f32 path's constants per modulus l: 2^13, 2^26, 2^39 mod m_l, RN(1/m_l)
+// and m_l, read from the constant bank as fma operands.
+struct CrtSplitF32 {
+    float p13[kCrtMaxModuli], p26[kCrtMaxModuli], p39[kCrtMaxModuli], inv[kCrtMaxModuli],
+        m[kCrtMaxModuli];
+};
+constexpr CrtSplitF32 make_crt_split_f32() {
+    CrtSplitF32 c{};
+    for (int l = 0; l < kCrtMaxModuli; ++l) {
+        const uint32_t m = crt_modulus(l);
+        c.p13[l] = (float)crt_pow2_mod(13, m);
+        c.p26[l] = (float)crt_pow2_mod(26, m);
+        c.p39[l] = (float)crt_pow2_mod(39, m);
+        c.inv[l] = 1.0f / (float)m;
+        c.m[l] = (float)m;
+    }
+    return c;
+}
+__constant__ CrtSplitF32 c_crt_split_f32 = make_crt_split_f32();
+
 struct CrtSplit {
     int k;
     template <int S>
@@ -69,7 +101,6 @@ struct CrtSplit {
         const uint64_t bits = (uint64_t)__double_as_longlong(a);
         const int ex = (int)((bits >> 52) & 0x7FF);
         const int se = k - e;
-        int64_t v;
         if (k <= 51 && se >= -1022 && se <= 1023) {
             // a 2^se is exact (a scaling by a normal power of two; a result
             // below the normal range is below 1/2 in magnitude), so one fma
@@ -79,29 +110,43 @@ struct CrtSplit {
             // encodings is the integer
             const double y =
                 __fma_rn(a, __longlong_as_double((long long)(se + 1023) << 52), 6755399441055744.0);
-            v = ex == 0x7FF ? 0 : (int64_t)__double_as_longlong(y) - 0x4338000000000000ll;
-        } else {
-            uint64_t mant = bits & ((1ull << 52) - 1);
-            int E = -1074;
-            if (ex == 0x7FF) mant = 0;   // Inf/NaN: reported by the scan; residues 0
-            else if (ex) {
-                mant |= 1ull << 52;
-                E = ex - 1075;
+            const int64_t v =
+                ex == 0x7FF ? 0 : (int64_t)__double_as_longlong(y) - 0x4338000000000000ll;
+            const uint32_t vl = (uint32_t)v, vh = (uint32_t)((uint64_t)v >> 32);
+            const float f0 = __int_as_float(0x4B000000 | (vl & 0x1FFFu)) - 8388608.0f;
+            const float f1 = __int_as_float(0x4B000000 | ((vl >> 13) & 0x1FFFu)) - 8388608.0f;
+            const float f2 = __int_as_float(0x4B000000 | (__funnelshift_r(vl, vh, 26) & 0x1FFFu)) -
+                             8388608.0f;
+            const float f3 = __int_as_float(0x4B400000 + ((int32_t)vh >> 7)) - 12582912.0f;
+            const CrtSplitF32& c = c_crt_split_f32;
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                const float x =
+                    __fmaf_rn(f3, c.p39[l], __fmaf_rn(f2, c.p26[l], __fmaf_rn(f1, c.p13[l], f0)));
+                const float q = __fadd_rn(__fmaf_rn(x, c.inv[l], 12582912.0f), -12582912.0f);
+                d[l] = __float_as_int(__fmaf_rn(-q, c.m[l], x));
             }
-            const int sh = E + se;
-            uint64_t u;
-            if (sh >= 0) {
-                u = mant << (sh > 63 ? 63 : sh);
-            } else if (sh < -54) {
-                u = 0;
-            } else {
-                const int r = -sh;
-                const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1),
-                               half = 1ull << (r - 1);
-                u = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-            }
-            v = (int64_t)bits < 0 ? -(int64_t)u : (int64_t)u;
+            return;
         }
+        uint64_t mant = bits & ((1ull << 52) - 1);
+        int E = -1074;
+        if (ex == 0x7FF) mant = 0;   // Inf/NaN: reported by the scan; residues 0
+        else if (ex) {
+            mant |= 1ull << 52;
+            E = ex - 1075;
+        }
+        const int sh = E + se;
+        uint64_t u;
+        if (sh >= 0) {
+            u = mant << (sh > 63 ? 63 : sh);
+        } else if (sh < -54) {
+            u = 0;
+        } else {
+            const int r = -sh;
+            const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1), half = 1ull << (r - 1);
+            u = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+        }
+        const int64_t v = (int64_t)bits < 0 ? -(int64_t)u : (int64_t)u;
         const int32_t hi = (int32_t)(v >> 40);
         const uint32_t mid = (uint32_t)(v >> 20) & 0xFFFFFu, lo = (uint32_t)v & 0xFFFFFu;
 #pragma unroll
@@ -109,8 +154,13 @@ struct CrtSplit {
             const uint32_t m = crt_modulus(l);
             const int32_t x = hi * (int32_t)crt_pow2_mod(40, m) +
                               (int32_t)(mid * crt_pow2_mod(20, m) + (lo + crt_split_bias(m)));
-            d[l] = (int)crt_mod((uint32_t)x, m) - (int)(m / 2);
+            const int r = (int)crt_mod((uint32_t)x, m) - (int)(m / 2);
+            d[l] = __float_as_int(__int_as_float(0x4B400000 + r) - 12582912.0f);
         }
+    }
+    // two residues (float encodings) as packed bf16
+    __device__ __forceinline__ uint32_t pack(int lo, int hi) const {
+        return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x7632);
     }
 };
 
@@ -122,8 +172,8 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
     const CrtSplit sp{k};
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0 && kpad % 4 == 0;
     // 128-thread blocks (4 k per thread), registers capped for 6 blocks per
-    // SM (measured faster than 256 threads, and than the uncapped 100
-    // registers)
+    // SM (measured faster than 256 threads, than 5 blocks and than 2 k per
+    // thread at 8 blocks)
     const int64_t bx = (kpad + 511) / 512;
     int64_t by = (int64_t)device_sm_count() * 16 / bx;
     by = by < 1 ? 1 : by > R ? R : by > 65535 ? 65535 : by;

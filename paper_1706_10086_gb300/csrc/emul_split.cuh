@@ -1,8 +1,8 @@
 // Device helpers of the emulated GEMMs: the exact fixed-point form of a
 // scaled operand, its digits, bf16 packing, the split kernels (rows of a
 // row-major matrix, or its columns through shared memory), which take a
-// splitter object that turns one value into S small integers, and the
-// rounding of a 128-bit integer to double.
+// splitter object that turns one value into S small integers and packs two
+// of them into bf16, and the rounding of a 128-bit integer to double.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -67,14 +67,6 @@ __device__ __forceinline__ void split_digits(double a, int e, int (&d)[S]) {
 // split kernels below take a splitter object, so that other integer
 // representations of the operands (the residues of the modular scheme) reuse
 // them.
-template <int B>
-struct DigitSplit {
-    template <int S>
-    __device__ __forceinline__ void split(double a, int e, int (&d)[S]) const {
-        split_digits<S, B>(a, e, d);
-    }
-};
-
 // Two digits (|v| <= 256) as packed bf16: the float 1.5*2^23 + v - 1.5*2^23
 // is exactly v, and its upper 16 bits are its bf16 encoding (at most 9
 // significant bits), so no conversion instruction is needed.
@@ -83,6 +75,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
     const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
     return __byte_perm((uint32_t)__float_as_int(fl), (uint32_t)__float_as_int(fh), 0x7632);
 }
+
+template <int B>
+struct DigitSplit {
+    template <int S>
+    __device__ __forceinline__ void split(double a, int e, int (&d)[S]) const {
+        split_digits<S, B>(a, e, d);
+    }
+    __device__ __forceinline__ uint32_t pack(int lo, int hi) const { return pack_bf16x2(lo, hi); }
+};
 
 // A (R x K, row-major) -> out[p][r][k] (row stride kpad, zero beyond K); each
 // thread handles two consecutive k.
@@ -103,7 +104,7 @@ __global__ void split_rows_kernel(const T* __restrict__ X, int64_t R, int64_t K,
         sp.template split<S>(k + 1 < K ? (double)__ldg(X + r * ldx + k + 1) : 0.0, er, d1);
         uint32_t* o = reinterpret_cast<uint32_t*>(out + r * kpad + k);
 #pragma unroll
-        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+        for (int p = 0; p < S; ++p, o += plane >> 1) *o = sp.pack(d0[p], d1[p]);
     }
 }
 
@@ -145,15 +146,22 @@ __global__ void __launch_bounds__(THREADS, MINB) split_rows4_kernel(const T* __r
 #pragma unroll
                 for (int u = 0; u < 4; ++u) a[u] = k + u < K ? (double)__ldg(xr + k + u) : 0.0;
             }
-            int d0[S], d1[S], d2[S], d3[S];
-            sp.template split<S>(a[0], er, d0);
-            sp.template split<S>(a[1], er, d1);
+            // pairs packed as soon as they are split, so that only the packed
+            // words of the first pair stay live
+            uint32_t w01[S];
+            {
+                int d0[S], d1[S];
+                sp.template split<S>(a[0], er, d0);
+                sp.template split<S>(a[1], er, d1);
+#pragma unroll
+                for (int p = 0; p < S; ++p) w01[p] = sp.pack(d0[p], d1[p]);
+            }
+            int d2[S], d3[S];
             sp.template split<S>(a[2], er, d2);
             sp.template split<S>(a[3], er, d3);
             uint2* o = reinterpret_cast<uint2*>(out + r * kpad + k);
 #pragma unroll
-            for (int p = 0; p < S; ++p)
-                o[(p * plane) >> 2] = make_uint2(pack_bf16x2(d0[p], d1[p]), pack_bf16x2(d2[p], d3[p]));
+            for (int p = 0; p < S; ++p, o += plane >> 2) *o = make_uint2(w01[p], sp.pack(d2[p], d3[p]));
         }
     }
 }
@@ -186,7 +194,7 @@ __global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
         if (k >= kpad) continue;
         uint32_t* o = reinterpret_cast<uint32_t*>(out + j * kpad + k);
 #pragma unroll
-        for (int p = 0; p < S; ++p) o[(p * plane) >> 1] = pack_bf16x2(d0[p], d1[p]);
+        for (int p = 0; p < S; ++p, o += plane >> 1) *o = sp.pack(d0[p], d1[p]);
     }
 }
 
