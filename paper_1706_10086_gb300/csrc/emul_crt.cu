@@ -189,6 +189,10 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
         else if (!trans)                                                                         \
             split_rows_kernel<T, x, CrtSplit><<<(unsigned)blocks, 256, 0, st>>>(                  \
                 X, R, K, ldx, exps, out, kpad, sp);                                              \
+        else if (vec)                                                                            \
+            split_cols4_kernel<T, x, CrtSplit><<<dim3((unsigned)((R + 31) / 32),                  \
+                                                      (unsigned)((kpad + 127) / 128)),           \
+                                                 256, 0, st>>>(X, K, R, ldx, exps, out, kpad, sp); \
         else                                                                                     \
             split_cols_kernel<T, x, CrtSplit><<<dim3((unsigned)((R + 31) / 32),                   \
                                                      (unsigned)(kpad / 64)),                     \

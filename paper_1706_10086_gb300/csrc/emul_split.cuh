@@ -198,6 +198,52 @@ __global__ void split_cols_kernel(const T* __restrict__ X, int64_t K, int64_t N,
     }
 }
 
+// As split_cols_kernel with four consecutive k per thread: 128 x 32 tiles, the
+// tile row of column jj holding k = 4q + i at position 32 i + q (q < 32, i <
+// 4), so that the tile's fill (one k of 32 columns per warp, a row stride of
+// 129 doubles) and the reads of four consecutive k by each lane (32
+// consecutive doubles per access) are free of bank conflicts; one 8-byte store
+// per digit plane (256 contiguous bytes per warp).  Needs out 8-byte aligned
+// and kpad a multiple of 4 (the launch checks).
+template <typename T, int S, typename Sp>
+__global__ void __launch_bounds__(256, 3) split_cols4_kernel(
+    const T* __restrict__ X, int64_t K, int64_t N, int64_t ldx, const int32_t* __restrict__ f,
+    __nv_bfloat16* __restrict__ out, int64_t kpad, const Sp sp) {
+    __shared__ double t[32][129];
+    const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 128;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 warps
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int kk = ty + 8 * r;
+        const int64_t k = k0 + kk, j = j0 + tx;
+        t[tx][(kk & 3) * 32 + (kk >> 2)] = (k < K && j < N) ? (double)__ldg(X + k * ldx + j) : 0.0;
+    }
+    __syncthreads();
+    const int64_t plane = N * kpad;
+    const int64_t k = k0 + 4 * tx;
+    if (k >= kpad) return;
+#pragma unroll 1
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int64_t j = j0 + jj;
+        if (j >= N) break;
+        const int fj = f[j];
+        uint32_t w01[S];
+        {
+            int d0[S], d1[S];
+            sp.template split<S>(t[jj][tx], fj, d0);
+            sp.template split<S>(t[jj][32 + tx], fj, d1);
+#pragma unroll
+            for (int p = 0; p < S; ++p) w01[p] = sp.pack(d0[p], d1[p]);
+        }
+        int d2[S], d3[S];
+        sp.template split<S>(t[jj][64 + tx], fj, d2);
+        sp.template split<S>(t[jj][96 + tx], fj, d3);
+        uint2* o = reinterpret_cast<uint2*>(out + j * kpad + k);
+#pragma unroll
+        for (int p = 0; p < S; ++p, o += plane >> 2) *o = make_uint2(w01[p], sp.pack(d2[p], d3[p]));
+    }
+}
+
 // Nearest double (ties to even) of the 128-bit two's-complement integer
 // hi:lo, multiplied by 2^E: built from 64-bit integer operations on the IEEE
 // encoding (FP64 arithmetic is slow on this GPU), with selects instead of
