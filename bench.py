@@ -8,10 +8,11 @@ scheme (ALP_SLICE_BF16_CRT: the operands rounded to k-bit integers per row and
 column, their exact product from residues modulo n moduli, one tensor-core
 product per modulus); n is the library's automatic count for these operands
 (alp_emul_crt_choose; 15 for phi = 0).
-One step = one full emulated GEMM: exponent scans, residue splits, the
-tensor-core residue products and the Chinese remainder reconstruction -- the
-same kernels alp_gemm_f64_emul launches, issued stage by stage so that CUDA
-events can bracket each.  Inputs (1.5 GB) are larger than L2, so no flush is
+One step = one full emulated GEMM: B's column exponent scan, A's row scan and
+residue split in one kernel, B's residue split, the tensor-core residue
+products and the Chinese remainder reconstruction -- the same kernels
+alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
+bracket each.  Inputs (1.5 GB) are larger than L2, so no flush is
 needed between steps.
 
 Beside the headline, in the same JSON line: the end-to-end call with host
@@ -453,34 +454,50 @@ def run_alp(args):
     e = torch.empty(M, dtype=torch.int32, device=dev)
     f = torch.empty(N, dtype=torch.int32, device=dev)
     crt = kind == alp.ALP_SLICE_BF16_CRT
-    launches_per_step = 7   # scan rows, scan cols (2), split A, split B, slice products, recombine
+    # the stages alp_gemm_f64_emul launches for this kind and a given count:
+    # the modular scheme scans A's rows inside A's split
+    if crt:
+        stage_names = ("scan_cols", "scan_split_A", "split_B", "slice_products", "recombine")
+        launches_per_step = 6   # scan cols (2), scan+split A, split B, products, recombine
+    else:
+        stage_names = ("scan_rows", "scan_cols", "split_A", "split_B", "slice_products",
+                       "recombine")
+        launches_per_step = 7   # scan rows, scan cols (2), split A, split B, products, recombine
+    nev = len(stage_names) + 1
 
     def step(ev=None):
-        # ev: 7 events bracketing the six stages (None: no timing)
-        rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
-        rec(0)
-        alp.alp_emul_exponents(M, K, A, K, 0, e, stream)
-        rec(1)
-        alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
-        rec(2)
-        alp.alp_emul_split(M, K, A, K, 0, e, s, kind, da, kpad, stream)
-        rec(3)
+        # ev: events bracketing the stages (None: no timing)
+        it = iter(ev) if ev is not None else None
+        rec = (lambda: next(it).record(stream)) if ev is not None else (lambda: None)
+        rec()
+        if crt:
+            alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
+            rec()
+            alp.alp_emul_scan_split_rows(M, K, A, K, e, s, kind, da, kpad, stream)
+            rec()
+        else:
+            alp.alp_emul_exponents(M, K, A, K, 0, e, stream)
+            rec()
+            alp.alp_emul_exponents(N, K, B, N, 1, f, stream)
+            rec()
+            alp.alp_emul_split(M, K, A, K, 0, e, s, kind, da, kpad, stream)
+            rec()
         alp.alp_emul_split(N, K, B, N, 1, f, s, kind, db, kpad, stream)
-        rec(4)
+        rec()
         alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
-        rec(5)
+        rec()
         if crt:
             alp.alp_emul_recombine_crt(M, N, K, s, G, ldg, e, f, alpha, beta, C, N, stream)
         else:
             alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)
-        rec(6)
+        rec()
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     assert alp.alp_get_device_error(stream) == alp.ALP_OK
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -498,9 +515,9 @@ def run_alp(args):
         dist.barrier()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    step_ms = [ev[i][0].elapsed_time(ev[i][6]) for i in range(args.steps)]
-    kern_ms = [ev[i][4].elapsed_time(ev[i][5]) for i in range(args.steps)]
-    stage_names = ("scan_rows", "scan_cols", "split_A", "split_B", "slice_products", "recombine")
+    step_ms = [ev[i][0].elapsed_time(ev[i][nev - 1]) for i in range(args.steps)]
+    kp = stage_names.index("slice_products")
+    kern_ms = [ev[i][kp].elapsed_time(ev[i][kp + 1]) for i in range(args.steps)]
     stage_ms = {nm: round(statistics.median(ev[i][k].elapsed_time(ev[i][k + 1])
                                             for i in range(args.steps)), 4)
                 for k, nm in enumerate(stage_names)}

@@ -170,6 +170,16 @@ alp_status alp_emul_exponents(int64_t rows, int64_t cols, const double* X, int64
 alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, int trans,
                           const int32_t* exps, int nslices, alp_slice_kind kind, void* out_bf16,
                           int64_t kpad, void* stream);
+/* The modular kinds only: alp_emul_exponents (trans = 0) and alp_emul_split
+ * (trans = 0) of the same rows in one kernel, which reads each row twice (the
+ * second time from L2) instead of scanning the matrix in a launch of its own;
+ * exps receives the row exponents.  The same results as the two calls bit for
+ * bit.  out_bf16 8-byte aligned, kpad a multiple of 64 and >= K, ldx >= K;
+ * alp_gemm_f64_emul uses it for A when nslices > 0 and A is not transposed.
+ * ALP_ERR_INVALID_ARG for other kinds. */
+alp_status alp_emul_scan_split_rows(int64_t R, int64_t K, const double* X, int64_t ldx,
+                                    int32_t* exps, int nslices, alp_slice_kind kind,
+                                    void* out_bf16, int64_t kpad, void* stream);
 /* alp_emul_slice_products: the tensor-core stage, S^t = sum_{p+q=t}
  * D_A^p (D_B^q)^T for t = 2..nslices+1 as exact int32 into
  * G[t-2][m][n] (row stride ldg, ldg a multiple of 256 and >= N; plane stride

@@ -70,6 +70,7 @@ _SIGS = {
     "alp_gemm_f64_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
     "alp_emul_exponents": ([_i64, _i64, _vp, _i64, _int, _vp, _vp], _int),
     "alp_emul_split": ([_i64, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _i64, _vp], _int),
+    "alp_emul_scan_split_rows": ([_i64, _i64, _vp, _i64, _vp, _int, _int, _vp, _i64, _vp], _int),
     "alp_emul_slice_products": ([_i64, _i64, _i64, _int, _int, _vp, _vp, _i64, _vp, _i64, _vp],
                                 _int),
     "alp_emul_recombine": ([_i64, _i64, _int, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp, _i64,
@@ -258,6 +259,13 @@ def alp_emul_split(R, K, X, ldx, trans, exps, nslices, kind, out, kpad, stream=N
     st = lib().alp_emul_split(R, K, _p(X), ldx, int(trans), _p(exps), int(nslices), int(kind),
                               _p(out), kpad, _s(stream))
     return _check(st, "alp_emul_split", raise_on_error)
+
+
+def alp_emul_scan_split_rows(R, K, X, ldx, exps, nslices, kind, out, kpad, stream=None,
+                             raise_on_error=True):
+    st = lib().alp_emul_scan_split_rows(R, K, _p(X), ldx, _p(exps), int(nslices), int(kind),
+                                        _p(out), kpad, _s(stream))
+    return _check(st, "alp_emul_scan_split_rows", raise_on_error)
 
 
 def alp_emul_slice_products(M, N, K, nslices, kind, da, db, kpad, G, ldg, stream=None,

@@ -39,13 +39,6 @@ alp_status crt_choose_moduli(int ta, int tb, int64_t M, int64_t N, int64_t K, co
 // ---------------------------------------------------------------------------
 constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 
-__device__ __forceinline__ int frexp_exponent_of_bits(uint64_t mb) {
-    if (mb == 0) return 0;
-    const int ex = (int)(mb >> 52);
-    if (ex == 0) return (63 - __clzll((long long)mb)) - 1073;   // subnormal
-    return ex - 1022;
-}
-
 
 // |x| as ordered integer keys (larger key, larger |x|): the bits of a double
 // without its sign, or of a float.  A key at or above the infinity's is Inf
@@ -635,7 +628,11 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     // rows of op(A): rows of A, or columns of its K x M storage; columns of
     // op(B): columns of B, or rows of its N x K storage
     alp_status st;
-    if ((st = emul_exponents(M, K, A, lda, ta, e, s)) != ALP_OK) return st;
+    // the modular scheme with a given count and A not transposed scans A's
+    // rows inside its split (emul_scan_split_crt), after B's scan
+    bool fused_a = false;
+    if constexpr (!kF32) fused_a = sc.crt && !auto_n && ta == 0;
+    if (!fused_a && (st = emul_exponents(M, K, A, lda, ta, e, s)) != ALP_OK) return st;
     if ((st = emul_exponents(N, K, B, ldb, 1 - tb, f, s)) != ALP_OK) return st;
     if constexpr (!kF32) {
         if (auto_n) {   // statistics in the (not yet written) residue-byte section
@@ -655,7 +652,9 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
         if ((st = emul_split(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, s, b)) != ALP_OK)
             return st;
     } else if (sc.crt) {
-        if ((st = emul_split_crt(M, K, A, lda, ta, e, nslices, da, L.kpad, kcrt, s)) != ALP_OK)
+        if ((st = fused_a ? emul_scan_split_crt(M, K, A, lda, e, nslices, da, L.kpad, kcrt, s)
+                          : emul_split_crt(M, K, A, lda, ta, e, nslices, da, L.kpad, kcrt, s)) !=
+            ALP_OK)
             return st;
         if ((st = emul_split_crt(N, K, B, ldb, 1 - tb, f, nslices, db, L.kpad, kcrt, s)) != ALP_OK)
             return st;
@@ -777,6 +776,21 @@ alp_status alp_emul_split(int64_t R, int64_t K, const double* X, int64_t ldx, in
     return emul_split(R, K, X, ldx, trans, exps, nslices,
                       reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
                       reinterpret_cast<cudaStream_t>(stream), sc.b);
+}
+
+alp_status alp_emul_scan_split_rows(int64_t R, int64_t K, const double* X, int64_t ldx,
+                                    int32_t* exps, int nslices, alp_slice_kind kind,
+                                    void* out_bf16, int64_t kpad, void* stream) {
+    EmulScheme sc;
+    if (R < 0 || K < 0 || !emul_scheme_of(kind, &sc) || !sc.crt ||
+        !emul_slices_ok(sc, nslices, false) || kpad < K || kpad % 64 || ldx < K || !exps ||
+        !out_bf16 || (R > 0 && K > 0 && !X) || ((uintptr_t)out_bf16 & 7))
+        return ALP_ERR_INVALID_ARG;
+    if (K > kCrtMaxK || crt_bits(K, nslices) < 1) return ALP_ERR_UNSUPPORTED;
+    if (R == 0) return ALP_OK;
+    return emul_scan_split_crt(R, K, X, ldx, exps, nslices,
+                               reinterpret_cast<__nv_bfloat16*>(out_bf16), kpad,
+                               crt_bits(K, nslices), reinterpret_cast<cudaStream_t>(stream));
 }
 
 alp_status alp_emul_slice_products(int64_t M, int64_t N, int64_t K, int nslices,

@@ -58,6 +58,11 @@ template <typename T>
 alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int trans,
                           const int32_t* exps, int n, __nv_bfloat16* out, int64_t kpad, int k,
                           cudaStream_t st);
+// Rows of a row-major R x K double matrix: the exponent scan and the residue
+// split in one pass per row (exps written; out 8-byte aligned, kpad % 4 == 0).
+alp_status emul_scan_split_crt(int64_t R, int64_t K, const double* X, int64_t ldx,
+                               int32_t* exps, int n, __nv_bfloat16* out, int64_t kpad, int k,
+                               cudaStream_t st);
 alp_status launch_recombine_crt(int n, int k, dim3 grid, cudaStream_t st, const uint8_t* R,
                                 int64_t rplane, int64_t ldr, const int32_t* e, const int32_t* f,
                                 int64_t M, int64_t N, double alpha, double beta, double* C,

@@ -208,6 +208,32 @@ alp_status emul_split_crt(int64_t R, int64_t K, const T* X, int64_t ldx, int tra
 #undef ALP_CRT_SPLIT_CASE
     return cuda_status(cudaGetLastError());
 }
+alp_status emul_scan_split_crt(int64_t R, int64_t K, const double* X, int64_t ldx,
+                               int32_t* exps, int n, __nv_bfloat16* out, int64_t kpad, int k,
+                               cudaStream_t st) {
+    if (k < 1 || k > 60) return ALP_ERR_UNSUPPORTED;
+    if ((reinterpret_cast<uintptr_t>(out) & 7) != 0 || kpad % 4 != 0) return ALP_ERR_INVALID_ARG;
+    const CrtSplit sp{k};
+    int64_t blocks = (int64_t)device_sm_count() * 6 * 4;   // rows walked by the blocks
+    blocks = blocks > R ? R : blocks < 1 ? 1 : blocks;
+    int* err = device_error_word();
+#define ALP_CRT_SCAN_SPLIT_CASE(x)                                                            \
+    case x:                                                                                  \
+        scan_split_rows4_kernel<x, CrtSplit, 128, 6>                                         \
+            <<<(unsigned)blocks, 128, 0, st>>>(X, R, K, ldx, exps, out, kpad, sp, err);      \
+        break;
+    switch (n) {
+        ALP_CRT_SCAN_SPLIT_CASE(4) ALP_CRT_SCAN_SPLIT_CASE(5) ALP_CRT_SCAN_SPLIT_CASE(6)
+        ALP_CRT_SCAN_SPLIT_CASE(7) ALP_CRT_SCAN_SPLIT_CASE(8) ALP_CRT_SCAN_SPLIT_CASE(9)
+        ALP_CRT_SCAN_SPLIT_CASE(10) ALP_CRT_SCAN_SPLIT_CASE(11) ALP_CRT_SCAN_SPLIT_CASE(12)
+        ALP_CRT_SCAN_SPLIT_CASE(13) ALP_CRT_SCAN_SPLIT_CASE(14) ALP_CRT_SCAN_SPLIT_CASE(15)
+        ALP_CRT_SCAN_SPLIT_CASE(16)
+        default: return ALP_ERR_INVALID_ARG;
+    }
+#undef ALP_CRT_SCAN_SPLIT_CASE
+    return cuda_status(cudaGetLastError());
+}
+
 template alp_status emul_split_crt<double>(int64_t, int64_t, const double*, int64_t, int,
                                            const int32_t*, int, __nv_bfloat16*, int64_t, int,
                                            cudaStream_t);

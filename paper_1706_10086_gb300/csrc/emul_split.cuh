@@ -11,6 +11,15 @@
 
 namespace alp {
 
+// The frexp exponent of a double given by its bits without the sign: the e
+// with 2^(e-1) <= |x| < 2^e (0 for zero).
+__device__ __forceinline__ int frexp_exponent_of_bits(uint64_t mb) {
+    if (mb == 0) return 0;
+    const int ex = (int)(mb >> 52);
+    if (ex == 0) return (63 - __clzll((long long)mb)) - 1073;   // subnormal
+    return ex - 1022;
+}
+
 // ---------------------------------------------------------------------------
 // 2. split
 // ---------------------------------------------------------------------------
@@ -148,6 +157,93 @@ __global__ void __launch_bounds__(THREADS, MINB) split_rows4_kernel(const T* __r
             }
             // pairs packed as soon as they are split, so that only the packed
             // words of the first pair stay live
+            uint32_t w01[S];
+            {
+                int d0[S], d1[S];
+                sp.template split<S>(a[0], er, d0);
+                sp.template split<S>(a[1], er, d1);
+#pragma unroll
+                for (int p = 0; p < S; ++p) w01[p] = sp.pack(d0[p], d1[p]);
+            }
+            int d2[S], d3[S];
+            sp.template split<S>(a[2], er, d2);
+            sp.template split<S>(a[3], er, d3);
+            uint2* o = reinterpret_cast<uint2*>(out + r * kpad + k);
+#pragma unroll
+            for (int p = 0; p < S; ++p, o += plane >> 2) *o = make_uint2(w01[p], sp.pack(d2[p], d3[p]));
+        }
+    }
+}
+
+// The row exponent scan and split_rows4_kernel in one kernel, one block per
+// row at a time (double operands): pass 1 reads the row in the split's own
+// pattern for the largest magnitude (the block's maximum through one shared
+// slot per row parity, one barrier per row), which gives e_r (stored, and an
+// Inf/NaN recorded in the error word as the scan does); pass 2 splits the row
+// with it, its loads served by L2.  Needs out 8-byte aligned and kpad a
+// multiple of 4 (the launch checks).
+template <int S, typename Sp, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) scan_split_rows4_kernel(
+    const double* __restrict__ X, int64_t R, int64_t K, int64_t ldx, int32_t* __restrict__ e,
+    __nv_bfloat16* __restrict__ out, int64_t kpad, const Sp sp, int* err) {
+    __shared__ uint64_t red[2][THREADS / 32];
+    const int64_t plane = R * kpad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int par = 0;
+    for (int64_t r = blockIdx.x; r < R; r += gridDim.x, par ^= 1) {
+        const double* xr = X + r * ldx;
+        const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
+        uint64_t mx = 0;
+#pragma unroll 1
+        for (int64_t k = 4 * (int64_t)threadIdx.x; k < K; k += 4 * THREADS) {
+            uint64_t b[4];
+            if (xvec && k + 3 < K) {
+                const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(xr + k));
+                const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(xr + k + 2));
+                b[0] = ((uint64_t)p0.y << 32) | p0.x;
+                b[1] = ((uint64_t)p0.w << 32) | p0.z;
+                b[2] = ((uint64_t)p1.y << 32) | p1.x;
+                b[3] = ((uint64_t)p1.w << 32) | p1.z;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    b[u] = k + u < K ? (uint64_t)__double_as_longlong(__ldg(xr + k + u)) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t a = b[u] & 0x7FFFFFFFFFFFFFFFull;
+                mx = a > mx ? a : mx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = y > mx ? y : mx;
+        }
+        if (lane == 0) red[par][warp] = mx;
+        __syncthreads();
+        mx = red[par][0];
+#pragma unroll
+        for (int w = 1; w < THREADS / 32; ++w) mx = red[par][w] > mx ? red[par][w] : mx;
+        const int er = frexp_exponent_of_bits(mx);
+        if (threadIdx.x == 0) {
+            e[r] = er;
+            if (mx >= 0x7FF0000000000000ull) set_device_error(err, ALP_ERR_UNSUPPORTED);
+        }
+#pragma unroll 1
+        for (int64_t k = 4 * (int64_t)threadIdx.x; k < kpad; k += 4 * THREADS) {
+            double a[4];
+            if (xvec && k + 3 < K) {
+                const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
+                const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
+                a[0] = p0.x;
+                a[1] = p0.y;
+                a[2] = p1.x;
+                a[3] = p1.y;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = k + u < K ? __ldg(xr + k + u) : 0.0;
+            }
             uint32_t w01[S];
             {
                 int d0[S], d1[S];

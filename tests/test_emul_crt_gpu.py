@@ -253,6 +253,45 @@ def check_residues(r, x, m):
     assert np.all((r == near) | (np.abs(r - near) == m))
 
 
+@pytest.mark.parametrize("M,K,ldx_extra,n", [(100, 1100, 0, 15), (37, 8193, 1, 13),
+                                              (5, 63, 3, 16), (300, 2048, 0, 4)])
+def test_crt_scan_split_rows_matches_the_two_stages(alp, M, K, ldx_extra, n):
+    """alp_emul_scan_split_rows (the row scan inside the row split, the GEMM's
+    path for A) against alp_emul_exponents + alp_emul_split: the same
+    exponents and residue planes bit for bit, on ragged and odd K, a row
+    stride that breaks 16-byte alignment (ldx odd), zero, tiny and huge rows;
+    an Inf is reported."""
+    import torch
+    rng = np.random.default_rng(6100 + M + K)
+    ldx = K + ldx_extra
+    X = np.zeros((M, ldx))
+    X[:, :K] = rng.uniform(-1, 1, (M, K)) * np.ldexp(1.0, rng.integers(-20, 21, (M, K)))
+    X[0, :K] = 0.0
+    X[1 % M, :K] *= 2.0 ** -1000
+    X[2 % M, :K] *= 2.0 ** 900
+    kpad = (K + 63) // 64 * 64
+    dX = torch.from_numpy(X).cuda()
+    e1 = torch.empty(M, dtype=torch.int32, device="cuda")
+    e2 = torch.empty(M, dtype=torch.int32, device="cuda")
+    o1 = torch.full((n, M, kpad), 5.0, dtype=torch.bfloat16, device="cuda")
+    o2 = torch.full((n, M, kpad), 7.0, dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_exponents(M, K, dX, ldx, 0, e1)
+    alp.alp_emul_split(M, K, dX, ldx, 0, e1, n, CRT, o1, kpad)
+    alp.alp_emul_scan_split_rows(M, K, dX, ldx, e2, n, CRT, o2, kpad)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    assert torch.equal(e1, e2)
+    assert torch.equal(o1.view(torch.int16), o2.view(torch.int16))
+    X[M // 2, K // 2] = np.inf
+    dX = torch.from_numpy(X).cuda()
+    alp.alp_emul_scan_split_rows(M, K, dX, ldx, e2, n, CRT, o2, kpad)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_ERR_UNSUPPORTED
+    st = alp.alp_emul_scan_split_rows(M, K, dX, ldx, e2, n, alp.ALP_SLICE_BF16, o2, kpad,
+                                      raise_on_error=False)
+    assert st == alp.ALP_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("n,phi", [(15, 0), (16, 8), (4, 32)])
 def test_crt_split_and_slice_products_stages(alp, orc, n, phi):
     """alp_emul_split with the modular kind writes the residues of the scaled
