@@ -20,7 +20,8 @@ buffers; the native DMMA kernel and the FP64 peak probes (with the vendor FP64
 GEMM timed as a comparison); per phi in {0, 8, 32}, the errors of the native
 kernel and of 13..16 moduli against the long-double oracle on sampled rows,
 the smallest count no worse than native on both measures, its throughput and
-the automatic count's; a short native size scan (default and autotuned
+the automatic count's, and the digit scheme's errors and throughput for 3..8
+slices; a short native size scan (default and autotuned
 config); the batched variable-size GEMM (4096 problems) against loops of
 single-problem launches; and the CPU oracle's own throughput.
 
@@ -315,8 +316,9 @@ def accuracy_leg(args, torch, alp, dev, stream, native_ms):
     """Per phi in {0, 8, 32}: the long-double oracle on sampled rows of the
     8192^3 product (u 2^e entries, alpha = 1, beta = 0); the native kernel's
     and 13..16 moduli's errors against it; the smallest count no worse than
-    native on both measures and its throughput; the automatic count.  Returns
-    (list of per-phi objects, CPU baseline object)."""
+    native on both measures and its throughput; the automatic count; and the
+    digit scheme's (ALP_SLICE_BF16, 7-bit digits) errors and throughput for 3..8
+    slices.  Returns (list of per-phi objects, CPU baseline object)."""
     import numpy as np
 
     import oracle
@@ -329,6 +331,9 @@ def accuracy_leg(args, torch, alp, dev, stream, native_ms):
     cpu_s, cpu_flops = 0.0, 0.0
     ws16 = alp.alp_gemm_f64_emul_workspace(M, N, K, 16, crt)
     work = torch.empty(ws16, dtype=torch.uint8, device=dev)
+    dig = alp.ALP_SLICE_BF16
+    wsd = alp.alp_gemm_f64_emul_workspace(M, N, K, 8, dig)
+    workd = torch.empty(wsd, dtype=torch.uint8, device=dev)
     C = torch.empty(n, n, dtype=torch.float64, device=dev)
     out = []
     for phi in (0, 8, 32):
@@ -363,11 +368,20 @@ def accuracy_leg(args, torch, alp, dev, stream, native_ms):
         assert alp.alp_get_device_error(stream) == alp.ALP_OK
         flops = 2.0 * M * N * K
 
-        def tflops(nm):
-            ws = alp.alp_gemm_f64_emul_workspace(M, N, K, nm, crt)
+        def tflops(nm, kind=crt, wk=work):
+            ws = alp.alp_gemm_f64_emul_workspace(M, N, K, nm, kind)
             ms = time_calls(torch, stream, lambda: alp.alp_gemm_f64_emul(
-                M, N, K, 1.0, A, K, B, N, 0.0, C, N, nm, crt, work, ws, stream), 5)
+                M, N, K, 1.0, A, K, B, N, 0.0, C, N, nm, kind, wk, ws, stream), 5)
             return round(flops / (ms * 1e-3) / 1e12, 3)
+        digits = {}
+        for sd in range(3, 9):
+            alp.alp_gemm_f64_emul(M, N, K, 1.0, A, K, B, N, 0.0, C, N, sd, dig, workd, wsd,
+                                  stream)
+            torch.cuda.synchronize()
+            digits[sd] = errors_vs_oracle(C[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref,
+                                          absAB)
+            digits[sd]["tflops"] = tflops(sd, dig, workd)
+        ok_d = [sd for sd in sorted(digits) if no_worse(digits[sd], nat)]
         row = {"phi": phi, "rows_sampled": int(len(rows)),
                "native": nat, "native_tflops": round(flops / (native_ms * 1e-3) / 1e12, 4)
                if native_ms else None,
@@ -378,10 +392,13 @@ def accuracy_leg(args, torch, alp, dev, stream, native_ms):
                "auto_predicted_normwise_ratio_to_native": round(pred[1], 4),
                "auto_no_worse_than_native": no_worse(emu[n_auto], nat) if n_auto in emu
                else None,
-               "tflops_at_auto_n": tflops(n_auto)}
+               "tflops_at_auto_n": tflops(n_auto),
+               "digit_slices": {"kind": "bf16 (7-bit digits, s(s+1)/2 products)",
+                                "by_slices": {str(k): v for k, v in digits.items()},
+                                "smallest_s_no_worse_than_native": ok_d[0] if ok_d else None}}
         out.append(row)
         del A, B, hB
-    del work, C
+    del work, workd, C
     cpu = {"value": cpu_flops / cpu_s / 1e12, "unit": UNIT, "cores": thr, "kind": "oracle",
            "sample": f"{len(rows)} rows of each of three {n}^3 products (phi = 0, 8, 32; "
                      f"long-double triple loop, {cpu_s:.1f} s, {os.cpu_count()} host cores)"}
