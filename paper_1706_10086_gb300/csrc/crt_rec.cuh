@@ -56,15 +56,28 @@ __device__ __forceinline__ void crt_reconstruct4(const uint32_t (&v)[S], const C
     for (int u = 0; u < 4; ++u) a0[u] = a1[u] = a2[u] = a3[u] = q[u] = 0, qh[u] = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        uint32_t X[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int l = 3 * g + i;
-            if (l < S) {
-                const uint32_t c = cc.cl[l];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) X[u] += __byte_perm(v[l], 0u, 0x4440u + u) * c;
-            }
+        // X_g by two-way dot products: every weight m_g / m_l is a product of
+        // at most two moduli <= 256 * 255 < 2^16, so the first two moduli of
+        // the group share one 16-bit weight pair and one permuted word of
+        // residue bytes per two columns (bytes x_a, x_b of column u at 2u,
+        // 2u + 1 of the pair word); the third adds its bytes with a zero
+        // partner.
+        const int a = 3 * g, b = a + 1, c = a + 2;
+        const uint32_t wab = cc.cl[a] | (b < S ? cc.cl[b] << 16 : 0u);
+        const uint32_t vb = b < S ? v[b < S ? b : a] : 0u;
+        const uint32_t p01 = __byte_perm(v[a], vb, 0x5140u);
+        const uint32_t p23 = __byte_perm(v[a], vb, 0x7362u);
+        uint32_t X[4] = {__dp2a_lo(wab, p01, 0u), __dp2a_hi(wab, p01, 0u),
+                         __dp2a_lo(wab, p23, 0u), __dp2a_hi(wab, p23, 0u)};
+        if (c < S) {
+            const uint32_t wc = cc.cl[c < S ? c : a];
+            const uint32_t vc = v[c < S ? c : a];
+            const uint32_t q01 = __byte_perm(vc, 0u, 0x4140u);
+            const uint32_t q23 = __byte_perm(vc, 0u, 0x4342u);
+            X[0] = __dp2a_lo(wc, q01, X[0]);
+            X[1] = __dp2a_hi(wc, q01, X[1]);
+            X[2] = __dp2a_lo(wc, q23, X[2]);
+            X[3] = __dp2a_hi(wc, q23, X[3]);
         }
         const uint32_t m0 = cc.mg[g][0], m1 = cc.mg[g][1], m2 = cc.mg[g][2], m3 = cc.mg[g][3];
         const uint32_t f0 = cc.fg_lo[g], f1 = cc.fg_hi[g];
