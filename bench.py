@@ -9,10 +9,11 @@ column, their exact product from residues modulo n moduli, one tensor-core
 product per modulus); n is the library's automatic count for these operands
 (alp_emul_crt_choose; 15 for phi = 0).
 One step = one full emulated GEMM: B's column exponent scan, A's row scan and
-residue split in one kernel, B's residue split, the tensor-core residue
-products and the Chinese remainder reconstruction -- the same kernels
-alp_gemm_f64_emul launches, issued stage by stage so that CUDA events can
-bracket each.  Inputs (1.5 GB) are larger than L2, so no flush is
+residue split in one kernel, B's residue split, and the tensor-core residue
+products with the Chinese remainder reconstruction in the same persistent
+launch (the tiles of the last wave reconstructed by a small launch after it)
+-- the same kernels alp_gemm_f64_emul launches, issued stage by stage so that
+CUDA events can bracket each.  Inputs (1.5 GB) are larger than L2, so no flush is
 needed between steps.
 
 Beside the headline, in the same JSON line: the end-to-end call with host
@@ -50,8 +51,10 @@ METRIC = "FP64-accurate GEMM TFLOP/s (native vs emulated) and % of peak at N=819
 UNIT = "TFLOP/s"
 NOMINAL_BF16_TFLOPS = 2250.0   # dense bf16 tensor rate of one GB300 (nominal)
 KERNEL_SOURCES = ("paper_1706_10086_gb300/csrc/emul_gemm.cu", "paper_1706_10086_gb300/csrc/tc.cuh",
-                  "paper_1706_10086_gb300/csrc/emul.cuh", "paper_1706_10086_gb300/csrc/crt.cuh")
-TRAFFIC_PROFILES = "profiles/emul_gemm_kernel_8192_*.md"
+                  "paper_1706_10086_gb300/csrc/emul.cuh", "paper_1706_10086_gb300/csrc/crt.cuh",
+                  "paper_1706_10086_gb300/csrc/crt_rec.cuh",
+                  "paper_1706_10086_gb300/csrc/emul_split.cuh")
+TRAFFIC_PROFILES = "profiles/emul_*_8192_*.md"
 # slice kinds of alp_gemm_f64_emul: name -> (enum value, digit pairs for s slices)
 KINDS = {"bf16": (1, lambda s: s * (s + 1) // 2), "bf16_b8": (2, lambda s: s * (s + 1) // 2),
          "bf16_b8_trim": (3, lambda s: s * (s - 1) // 2 + 2), "bf16_crt": (4, lambda s: s)}
@@ -251,25 +254,35 @@ def make_inputs(torch, n, phi, seed, device):
 def product_roofline(pairs, M, N, K, s, crt, kern_ms, region_ms, clk, workload):
     """Roofline of the tensor-core product kernel: algorithmic flops per launch
     (pairs x 2MNK) over its average event-timed duration, against the measured
-    bf16 peak.  The timed region lasts well under a second, so the burst figure
+    bf16 peak.  For the modular scheme the timed stage is the fused launch
+    (products with the reconstruction in the kernel's own warps, and the tail
+    tiles' reconstruction after it), so its flops rate counts only the
+    products.  The timed region lasts well under a second, so the burst figure
     is the denominator; the sustained one and the nominal rate are given
     beside it, and a clock-normalised fraction (the kernel's flops per SM clock
     over the peak's, each at its own median SM clock) separates clock from
     kernel.  DRAM traffic comes from a committed ncu summary of this kernel
     source and workload (null otherwise), next to the algorithmic bytes:
     operand slices read once (2 bytes per entry of A and B per product) and
-    the per-product sums written once (1 byte per entry of C per modulus, 4
-    bytes per group sum for the digit schemes)."""
+    the per-product sums written once (4 bytes per group sum for the digit
+    schemes; for the modular scheme 1 byte per entry of C per modulus, read
+    back once by the reconstruction, and C written once)."""
     peaks, peak_kind = load_peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
     sustained = float(peaks.get("bf16_tflops_sustained", peak))
     achieved = pairs * 2.0 * M * N * K / (kern_ms * 1e-3) / 1e12
     traffic = profiled_traffic(workload)
-    alg_bytes = 2.0 * s * (M + N) * K + (1.0 if crt else 4.0) * s * M * N
+    # modular scheme: the fused launch also reads the residue bytes back and
+    # writes C (8 bytes per entry; beta = 0 in the bench)
+    alg_bytes = (2.0 * s * (M + N) * K + 2.0 * s * M * N + 8.0 * M * N if crt
+                 else 2.0 * s * (M + N) * K + 4.0 * s * M * N)
     peak_mhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
     run_mhz = clk.get("sm_mhz")
     clock_frac = (achieved / run_mhz) / (peak / peak_mhz) if peak_mhz and run_mhz else None
-    return {"bound": "tensor", "kernel": "emul_gemm_pair_kernel (tcgen05 bf16 residue products)",
+    kernel = ("emul_crt_fused_pair_kernel (tcgen05 bf16 residue products; C reconstructed by "
+              "its own warps) + crt_tail_recombine_kernel" if crt else
+              "emul_gemm_pair_kernel (tcgen05 bf16 digit-slice products)")
+    return {"bound": "tensor", "kernel": kernel,
             "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4),
             "peak_source": f"bf16_tflops (burst) of MEASURED_PEAKS.json ({peak_kind}); the "
@@ -471,11 +484,15 @@ def run_alp(args):
     e = torch.empty(M, dtype=torch.int32, device=dev)
     f = torch.empty(N, dtype=torch.int32, device=dev)
     crt = kind == alp.ALP_SLICE_BF16_CRT
+    sched_bytes = alp.alp_emul_products_recombine_crt_workspace(M, N) if crt else 0
+    sched = torch.empty(max(sched_bytes, 4), dtype=torch.uint8, device=dev)
     # the stages alp_gemm_f64_emul launches for this kind and a given count:
     # the modular scheme scans A's rows inside A's split
     if crt:
-        stage_names = ("scan_cols", "scan_split_A", "split_B", "slice_products", "recombine")
-        launches_per_step = 6   # scan cols (2), scan+split A, split B, products, recombine
+        stage_names = ("scan_cols", "scan_split_A", "split_B", "products_recombine")
+        # scan cols (2), scan+split A, split B, products with the reconstruction,
+        # the tail tiles' reconstruction
+        launches_per_step = 6
     else:
         stage_names = ("scan_rows", "scan_cols", "split_A", "split_B", "slice_products",
                        "recombine")
@@ -501,13 +518,15 @@ def run_alp(args):
             rec()
         alp.alp_emul_split(N, K, B, N, 1, f, s, kind, db, kpad, stream)
         rec()
-        alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
-        rec()
         if crt:
-            alp.alp_emul_recombine_crt(M, N, K, s, G, ldg, e, f, alpha, beta, C, N, stream)
+            alp.alp_emul_products_recombine_crt(M, N, K, s, da, db, kpad, G, ldg, e, f, alpha,
+                                                beta, C, N, sched, sched_bytes, stream)
+            rec()
         else:
+            alp.alp_emul_slice_products(M, N, K, s, kind, da, db, kpad, G, ldg, stream)
+            rec()
             alp.alp_emul_recombine(M, N, s, kind, G, ldg, e, f, alpha, beta, C, N, stream)
-        rec()
+            rec()
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -533,7 +552,7 @@ def run_alp(args):
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [ev[i][0].elapsed_time(ev[i][nev - 1]) for i in range(args.steps)]
-    kp = stage_names.index("slice_products")
+    kp = stage_names.index("products_recombine" if crt else "slice_products")
     kern_ms = [ev[i][kp].elapsed_time(ev[i][kp + 1]) for i in range(args.steps)]
     stage_ms = {nm: round(statistics.median(ev[i][k].elapsed_time(ev[i][k + 1])
                                             for i in range(args.steps)), 4)

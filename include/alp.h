@@ -265,6 +265,34 @@ alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
                                   const uint8_t* R, int64_t ldr, const int32_t* e,
                                   const int32_t* f, double alpha, double beta, double* C,
                                   int64_t ldc, void* stream);
+/* The modular kind's tensor-core stage and reconstruction in one launch
+ * (Eq. 1's C = alpha AB + beta C written while the products run): the same C
+ * and the same byte planes in R as alp_emul_slice_products followed by
+ * alp_emul_recombine_crt, bit for bit.  One persistent launch of CTA pairs
+ * takes the 256 x 256 tiles of C from a counter; the product kernel's
+ * reconstruction warps rebuild each finished tile from its byte planes while
+ * the next tile's products run, and a small second launch rebuilds the tiles
+ * of the last wave, whose moduli several pairs share.  alp_gemm_f64_emul runs
+ * its modular scheme this way (ALP_EMUL_CRT_FUSE=0 in the environment: as the
+ * two stages; the one-block arrangement, ALP_EMUL_CLUSTER=1, always so).
+ * da_bf16, db_bf16: the residue slices of A and B^T as alp_emul_split writes
+ * them (kpad a multiple of 64, >= K); R: the n byte planes (device, 16-byte
+ * aligned, row stride ldr bytes, ldr a multiple of 256 and >= N, plane stride
+ * M*ldr), overwritten; e, f: the exponents of the rows of A and the columns
+ * of B (device int32); C: row-major M x N (ldc >= N), read when beta != 0;
+ * workspace: device memory of alp_emul_products_recombine_crt_workspace(M, N)
+ * bytes (4-byte aligned) for the launch's schedule, overwritten.
+ * ALP_ERR_INVALID_ARG for K < 1 or an argument the two calls reject,
+ * ALP_ERR_WORKSPACE for a missing or short workspace, ALP_ERR_UNSUPPORTED
+ * when alp_emul_crt_bits(K, nmoduli) is 0, all before any launch; the device
+ * error word reports a wait that gave up. */
+size_t alp_emul_products_recombine_crt_workspace(int64_t M, int64_t N);
+alp_status alp_emul_products_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
+                                           const void* da_bf16, const void* db_bf16,
+                                           int64_t kpad, uint8_t* R, int64_t ldr,
+                                           const int32_t* e, const int32_t* f, double alpha,
+                                           double beta, double* C, int64_t ldc, void* workspace,
+                                           size_t workspace_bytes, void* stream);
 
 /*
  * Emulated FP32 GEMM (the paper evaluates single precision throughout,

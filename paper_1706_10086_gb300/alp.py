@@ -84,6 +84,10 @@ _SIGS = {
                                  _int),
     "alp_emul_recombine_crt": ([_i64, _i64, _i64, _int, _vp, _i64, _vp, _vp, _f64, _f64, _vp,
                                 _i64, _vp], _int),
+    "alp_emul_products_recombine_crt": ([_i64, _i64, _i64, _int, _vp, _vp, _i64, _vp, _i64,
+                                         _vp, _vp, _f64, _f64, _vp, _i64, _vp, ctypes.c_size_t,
+                                         _vp], _int),
+    "alp_emul_products_recombine_crt_workspace": ([_i64, _i64], ctypes.c_size_t),
     "alp_gemm_f32_emul": ([_i64, _i64, _i64, _f32, _vp, _i64, _vp, _i64, _f32, _vp, _i64, _int,
                            _int, _vp, ctypes.c_size_t, _vp], _int),
     "alp_gemm_f32_emul_workspace": ([_i64, _i64, _i64, _int, _int], ctypes.c_size_t),
@@ -314,6 +318,20 @@ def alp_emul_recombine_crt(M, N, K, nmoduli, G, ldg, e, f, alpha, beta, C, ldc, 
     st = lib().alp_emul_recombine_crt(M, N, K, int(nmoduli), _p(G), ldg, _p(e), _p(f),
                                       float(alpha), float(beta), _p(C), ldc, _s(stream))
     return _check(st, "alp_emul_recombine_crt", raise_on_error)
+
+
+def alp_emul_products_recombine_crt_workspace(M, N):
+    return int(lib().alp_emul_products_recombine_crt_workspace(M, N))
+
+
+def alp_emul_products_recombine_crt(M, N, K, nmoduli, da, db, kpad, G, ldg, e, f, alpha, beta, C,
+                                    ldc, workspace=None, workspace_bytes=0, stream=None,
+                                    raise_on_error=True):
+    st = lib().alp_emul_products_recombine_crt(M, N, K, int(nmoduli), _p(da), _p(db), kpad,
+                                               _p(G), ldg, _p(e), _p(f), float(alpha),
+                                               float(beta), _p(C), ldc, _p(workspace),
+                                               int(workspace_bytes), _s(stream))
+    return _check(st, "alp_emul_products_recombine_crt", raise_on_error)
 
 
 def alp_gemm_f32_emul(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices,

@@ -112,4 +112,67 @@ __device__ __forceinline__ void crt_reconstruct4(const uint32_t (&v)[S], const C
     }
 }
 
+// The same for a modulus count n (4..16) known only at run time: v[l] = 0
+// and the constants of moduli l >= n are zero (crt_rec_consts zero-fills
+// them), so a group or limb past the count adds nothing; groups wholly past
+// it are skipped (n is the same in every thread), and the fourth limb is
+// formed for n = 16 only.  Used where one kernel serves every count.
+__device__ __forceinline__ void crt_reconstruct4_n(const uint32_t (&v)[16], int n,
+                                                   const CrtRecConsts& cc, int64_t (&hi)[4],
+                                                   uint64_t (&lo)[4]) {
+    uint64_t a0[4], a1[4], a2[4], a3[4], q[4];
+    uint32_t qh[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a0[u] = a1[u] = a2[u] = a3[u] = q[u] = 0, qh[u] = 0;
+    const bool four = n > 15;
+#pragma unroll
+    for (int g = 0; g < kCrtMaxGroups; ++g) {
+        if (3 * g >= n) break;
+        const int a = 3 * g, b = a + 1, c = a + 2;
+        const uint32_t wab = cc.cl[a] | (b < 16 ? cc.cl[b < 16 ? b : a] << 16 : 0u);
+        const uint32_t vb = b < 16 ? v[b < 16 ? b : a] : 0u;
+        const uint32_t p01 = __byte_perm(v[a], vb, 0x5140u);
+        const uint32_t p23 = __byte_perm(v[a], vb, 0x7362u);
+        uint32_t X[4] = {__dp2a_lo(wab, p01, 0u), __dp2a_hi(wab, p01, 0u),
+                         __dp2a_lo(wab, p23, 0u), __dp2a_hi(wab, p23, 0u)};
+        if (c < 16) {
+            const uint32_t wc = cc.cl[c < 16 ? c : a];
+            const uint32_t vc = v[c < 16 ? c : a];
+            const uint32_t q01 = __byte_perm(vc, 0u, 0x4140u);
+            const uint32_t q23 = __byte_perm(vc, 0u, 0x4342u);
+            X[0] = __dp2a_lo(wc, q01, X[0]);
+            X[1] = __dp2a_hi(wc, q01, X[1]);
+            X[2] = __dp2a_lo(wc, q23, X[2]);
+            X[3] = __dp2a_hi(wc, q23, X[3]);
+        }
+        const uint32_t m0 = cc.mg[g][0], m1 = cc.mg[g][1], m2 = cc.mg[g][2], m3 = cc.mg[g][3];
+        const uint32_t f0 = cc.fg_lo[g], f1 = cc.fg_hi[g];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a0[u] = crt_mad_wide(X[u], m0, a0[u]);
+            a1[u] = crt_mad_wide(X[u], m1, a1[u]);
+            a2[u] = crt_mad_wide(X[u], m2, a2[u]);
+            if (four) a3[u] = crt_mad_wide(X[u], m3, a3[u]);
+            q[u] = crt_mad_wide(X[u], f0, q[u]);
+            qh[u] += X[u] * f1;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        // as in crt_reconstruct4
+        const uint64_t qt = q[u] + ((uint64_t)qh[u] << 32);
+        const uint32_t c = (uint32_t)((qt + (1ull << 57)) >> 58);
+        int64_t t = (int64_t)a0[u] - (int64_t)((uint64_t)c * cc.mn[0]);
+        const uint32_t w0 = (uint32_t)t;
+        t = (t >> 32) + (int64_t)a1[u] - (int64_t)((uint64_t)c * cc.mn[1]);
+        const uint32_t w1 = (uint32_t)t;
+        t = (t >> 32) + (int64_t)a2[u] - (int64_t)((uint64_t)c * cc.mn[2]);
+        const uint32_t w2 = (uint32_t)t;
+        t = (t >> 32) + (int64_t)a3[u] - (int64_t)((uint64_t)c * cc.mn[3]);
+        const uint32_t w3 = (uint32_t)t;
+        hi[u] = (int64_t)(((uint64_t)w3 << 32) | w2);
+        lo[u] = ((uint64_t)w1 << 32) | w0;
+    }
+}
+
 }  // namespace alp

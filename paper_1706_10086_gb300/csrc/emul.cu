@@ -367,7 +367,7 @@ static alp_status launch_recombine(int s, int b, dim3 grid, cudaStream_t st, con
     return ALP_ERR_INVALID_ARG;
 }
 
-static dim3 recombine_grid(int64_t M, int64_t N) {
+dim3 recombine_grid(int64_t M, int64_t N) {
     const int64_t bx = (N + 511) / 512;
     int64_t by = (int64_t)device_sm_count() * 16 / (bx > 0 ? bx : 1);
     if (by < 1) by = 1;
@@ -392,6 +392,9 @@ EmulLayout emul_layout(int64_t M, int64_t N, int64_t K, int s, int gbytes) {
     L.off_g = off;  off += up256((size_t)s * M * L.ldg * gbytes);
     L.off_e = off; off += up256((size_t)M * 4);
     L.off_f = off; off += up256((size_t)N * 4);
+    L.off_sched = off;
+    L.sched_bytes = gbytes == 1 ? emul_crt_sched_bytes(M, N) : 0;
+    off += up256(L.sched_bytes);
     L.bytes = off;
     return L;
 }
@@ -665,6 +668,13 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     }
     alp_config cfg;
     const bool have = select_config(M, N, K, ALP_PATH_EMUL, &cfg, s) && emul_config_valid(cfg);
+    if constexpr (!kF32) {
+        if (sc.crt)   // products and reconstruction (one launch with CTA pairs)
+            return emul_crt_products_recombine(
+                M, N, K, nslices, da, db, L.kpad, reinterpret_cast<uint8_t*>(G), L.ldg, e, f,
+                kcrt, alpha, beta, C, ldc, reinterpret_cast<int*>(ws + L0.off_sched),
+                L0.sched_bytes, s, have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0);
+    }
     if ((st = emul_slice_gemm(M, N, K, nslices, da, db, L.kpad, G, L.ldg, s,
                               have ? cfg.stages : 0, have ? emul_arrangement_of(cfg) : 0, b,
                               sc.trim, sc.crt)) != ALP_OK)
@@ -672,10 +682,6 @@ alp_status emul_gemm_impl(int ta, int tb, int64_t M, int64_t N, int64_t K, T alp
     if constexpr (kF32)
         return launch_recombine_f32(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e,
                                     f, M, N, alpha, beta, C, ldc);
-    else if (sc.crt)
-        return launch_recombine_crt(nslices, kcrt, recombine_grid(M, N), s,
-                                    reinterpret_cast<const uint8_t*>(G), M * L.ldg, L.ldg, e, f,
-                                    M, N, alpha, beta, C, ldc);
     else
         return launch_recombine(nslices, b, recombine_grid(M, N), s, G, M * L.ldg, L.ldg, e, f,
                                 M, N, alpha, beta, C, ldc);
@@ -843,6 +849,36 @@ alp_status alp_emul_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
     return launch_recombine_crt(nmoduli, k, recombine_grid(M, N),
                                 reinterpret_cast<cudaStream_t>(stream), R, M * ldr, ldr, e, f, M,
                                 N, alpha, beta, C, ldc);
+}
+
+size_t alp_emul_products_recombine_crt_workspace(int64_t M, int64_t N) {
+    return emul_crt_sched_bytes(M, N);
+}
+
+alp_status alp_emul_products_recombine_crt(int64_t M, int64_t N, int64_t K, int nmoduli,
+                                           const void* da_bf16, const void* db_bf16,
+                                           int64_t kpad, uint8_t* R, int64_t ldr,
+                                           const int32_t* e, const int32_t* f, double alpha,
+                                           double beta, double* C, int64_t ldc, void* workspace,
+                                           size_t workspace_bytes, void* stream) {
+    if (M < 0 || N < 0 || K < 1 || nmoduli < kCrtMinModuli || nmoduli > kCrtMaxModuli ||
+        kpad < K || kpad % kEmulBK || ldr < N || ldr % 256 || ldc < N || K > kCrtMaxK)
+        return ALP_ERR_INVALID_ARG;
+    const int k = alp_emul_crt_bits(K, nmoduli);
+    if (k < 1) return ALP_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0) return ALP_OK;
+    if (!da_bf16 || !db_bf16 || !R || ((uintptr_t)R & 15) || !e || !f || !C ||
+        ((uintptr_t)C & 7))
+        return ALP_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 3) ||
+        workspace_bytes < emul_crt_sched_bytes(M, N))
+        return ALP_ERR_WORKSPACE;
+    return emul_crt_products_recombine(M, N, K, nmoduli,
+                                       reinterpret_cast<const __nv_bfloat16*>(da_bf16),
+                                       reinterpret_cast<const __nv_bfloat16*>(db_bf16), kpad, R,
+                                       ldr, e, f, k, alpha, beta, C, ldc,
+                                       static_cast<int*>(workspace), workspace_bytes,
+                                       reinterpret_cast<cudaStream_t>(stream), 0, 0, 1);
 }
 
 alp_status alp_gemm_f64_emul(int64_t M, int64_t N, int64_t K, double alpha, const double* A,

@@ -87,6 +87,7 @@ struct EmulLayout {
     int64_t kpad;    // K rounded up to kEmulBK (digit rows, zero filled)
     int64_t ldg;     // row stride of the int32 group sums (N rounded up to 256)
     size_t off_da, off_db, off_g, off_e, off_f, bytes;
+    size_t off_sched, sched_bytes;   // the modular scheme's fused schedule (gbytes 1)
 };
 
 // gbytes: bytes per element of G (4: int32 group sums; 1: the modular
@@ -108,6 +109,27 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
                            const __nv_bfloat16* db, int64_t kpad, int32_t* G, int64_t ldg,
                            cudaStream_t stream, int group_m = 0, int cluster = 0,
                            int digit_bits = kDigitBits, bool trim = false, bool crt = false);
+
+// Grid of the reconstruction kernels: 512 columns per block, rows strided.
+dim3 recombine_grid(int64_t M, int64_t N);
+
+// The modular scheme's products and reconstruction: C = alpha RN(P 2^(e_i +
+// f_j - 2k)) (+ beta C) from the n residue slices, with G (n byte planes, row
+// stride ldg bytes, a multiple of 256) as the residue workspace.  With the
+// CTA-pair arrangement one persistent launch reconstructs each tile while the
+// next one's products run (emul_gemm.cu), then the tail tiles; otherwise (or
+// with ALP_EMUL_CRT_FUSE=0) the product stage and the reconstruction kernel.
+// sched: the fused launch's schedule (emul_crt_sched_bytes(M, N) bytes of
+// device memory, 4-byte aligned; without it the two launches run).  fuse: 1
+// fuse, 0 do not, -1 as ALP_EMUL_CRT_FUSE says.
+alp_status emul_crt_products_recombine(int64_t M, int64_t N, int64_t K, int n,
+                                       const __nv_bfloat16* da, const __nv_bfloat16* db,
+                                       int64_t kpad, uint8_t* G, int64_t ldg, const int32_t* e,
+                                       const int32_t* f, int k, double alpha, double beta,
+                                       double* C, int64_t ldc, int* sched, size_t sched_bytes,
+                                       cudaStream_t stream, int group_m = 0, int cluster = 0,
+                                       int fuse = -1);
+size_t emul_crt_sched_bytes(int64_t M, int64_t N);
 
 // Tail split of the slice-product launch (see emul_gemm.cu): whole tiles for
 // blocks [0, n_full), then each remaining tile cut into `pieces` blocks by

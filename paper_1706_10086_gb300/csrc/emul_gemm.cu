@@ -34,6 +34,7 @@
 #include <cstdlib>
 
 #include "crt.cuh"
+#include "crt_rec.cuh"
 #include "emul.cuh"
 #include "tc.cuh"
 
@@ -77,6 +78,18 @@ static bool emul_tail_split_on() {
     static int on = -1;
     if (on < 0) {
         const char* s = std::getenv("ALP_EMUL_TAIL_SPLIT");
+        on = (s && std::atoi(s) == 0) ? 0 : 1;
+    }
+    return on == 1;
+}
+
+// Whether alp_gemm_f64_emul's modular scheme reconstructs C inside the
+// product kernel (env ALP_EMUL_CRT_FUSE=0 turns it off: products, then the
+// reconstruction kernel; default on).  Only the CTA-pair arrangement fuses.
+static bool emul_crt_fuse_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char* s = std::getenv("ALP_EMUL_CRT_FUSE");
         on = (s && std::atoi(s) == 0) ? 0 : 1;
     }
     return on == 1;
@@ -450,6 +463,22 @@ constexpr uint32_t kPairStageBytes = kATile + kPairBTile;
 constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + 1024 /*align*/ + 256 /*barriers*/ +
                                4 * kMaxJobs;
 
+constexpr int kFusedSmemBytes = kPairStages * kPairStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+// Grouped raster in units of 256-row tile pairs: the origin of pair tile pid
+// (m0 = the first of the 128 rows block `rank` holds, n0 = the first column).
+__device__ __forceinline__ void pair_tile_origin(const EmulGemmParams& prm, int pid, uint32_t rank,
+                                                 int& m0, int& n0) {
+    const int tiles_mc = (prm.tiles_m + 1) / 2;
+    const int gm = prm.group_m / 2 > 0 ? prm.group_m / 2 : 1;
+    const int in_group = gm * prm.tiles_n;
+    const int first_m = (pid / in_group) * gm;
+    const int gsz = min(tiles_mc - first_m, gm);
+    const int local = pid % in_group;
+    m0 = ((first_m + local % gsz) * 2 + (int)rank) * kTM;
+    n0 = (local / gsz) * kTN;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     emul_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                           const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
@@ -506,19 +535,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
     const int njobs = *njobs_slot;
 
-    // grouped raster in units of 256-row tile pairs
     int m0, n0;
     {
-        const int tiles_mc = (prm.tiles_m + 1) / 2;
-        const int gm = prm.group_m / 2 > 0 ? prm.group_m / 2 : 1;
         const int cid = (int)blockIdx.x / 2;
         const int pid = cid < prm.n_full ? cid : prm.n_full + (cid - prm.n_full) / prm.pieces;
-        const int in_group = gm * prm.tiles_n;
-        const int first_m = (pid / in_group) * gm;
-        const int gsz = min(tiles_mc - first_m, gm);
-        const int local = pid % in_group;
-        m0 = ((first_m + local % gsz) * 2 + (int)rank) * kTM;
-        n0 = (local / gsz) * kTN;
+        pair_tile_origin(prm, pid, rank, m0, n0);
     }
     const uint64_t tmo = prm.timeout_ns;
     const uint32_t full0 = cluster_addr(full, 0);   // block 0's full barriers
@@ -623,6 +644,495 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         tc_fence_after();
         tmem_dealloc_pair(tmem_base, kTmemCols);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// The modular scheme with the reconstruction in the product kernel.
+//
+// A persistent launch of CTA pairs (P clusters, all resident) that take
+// items from a counter as they go, an item being a whole 256 x 256 tile (all
+// n moduli; items 0..n_full-1 in raster order) or one piece of a tail tile (a
+// range of moduli; tail_split).  Block 0's producer takes the cluster's next
+// item when it has issued the copies of the current one and publishes it in
+// the cluster's list in global memory; every other role of both blocks reads
+// the list (bounded waits), so that a pair that runs faster takes more items
+// and the launch ends evenly.  The producer, the MMA issuer and the epilogue walk the
+// same items and, per item, the moduli and 1024-k chunks in order, so the
+// stage ring and the accumulator double buffer run on across items as within
+// one.  Sixteen warps per block: 0 the TMA producer, 1 the MMA issuer, 4-11
+// the epilogue (the drains, hand-backs and residue bytes of
+// emul_gemm_pair_kernel), 12-15 the reconstruction; 2-3 idle.  When the
+// epilogue has stored the last residue plane of a whole tile it counts the
+// tile in shared memory (a release add per warp); the reconstruction warps
+// wait for the count (bounded) and rebuild the block's 128 rows of that tile
+// from its n byte planes, as the standalone kernels do, while the next
+// tile's products run, so that C is written during the products instead of
+// by a launch of its own.  Tail tiles (whose moduli several clusters share)
+// are reconstructed by crt_tail_recombine_kernel after the launch.
+// Registers: the epilogue's warpgroups take 176 per thread, the others give
+// theirs down to 80 (setmaxnreg): 2 x 128 x 176 + 2 x 128 x 80 = 65536, the
+// 512 threads x 128 registers of the launch.
+// ---------------------------------------------------------------------------
+struct CrtFuse {
+    const int32_t* e;   // exponents of the rows of op(A) (M)
+    const int32_t* f;   // exponents of the columns of op(B) (N)
+    double alpha, beta;
+    double* C;
+    int64_t ldc;
+    int amode;          // alpha: 0 one, 1 minus one, 2 any
+    int bmode;          // beta: 0 zero (C not read), 1 any
+    int n_items;        // whole tiles n_full, then (pair tiles - n_full) * pieces
+    // the schedule (workspace, all bytes 0xff before the launch): sched[0] the
+    // item counter, sched[1 + c * stride + k] the k-th item of cluster c
+    // (n_items or more: no more items), stride = n_items + 1
+    int* sched;
+    int stride;
+    CrtRecConsts cc;
+};
+constexpr int kFusedThreads = 512;
+constexpr int kFusedEpiWarp0 = 4;    // warps 4..11: epilogue
+constexpr int kFusedRecWarp0 = 12;   // warps 12..15: reconstruction
+constexpr int kFusedEpiRegs = 176, kFusedLowRegs = 80;
+constexpr int kMaxFusedClusters = 128;   // clusters of one launch (the schedule's bound)
+static_assert(2 * 128 * kFusedEpiRegs + 2 * 128 * kFusedLowRegs == kFusedThreads * 128,
+              "register split of the fused kernel");
+
+// Item i: the pair tile and its moduli q_lo..q_hi (planes, 0-based).
+__device__ __forceinline__ void fused_item(const EmulGemmParams& prm, int i, int& pid, int& q_lo,
+                                           int& q_hi) {
+    if (i < prm.n_full) {
+        pid = i;
+        q_lo = 0;
+        q_hi = prm.s - 1;
+        return;
+    }
+    const int pc = (i - prm.n_full) % prm.pieces;
+    pid = prm.n_full + (i - prm.n_full) / prm.pieces;
+    const uint32_t r = (uint32_t)(prm.t_ranges >> (8 * pc)) & 0xffu;
+    q_lo = (int)(r & 15u);
+    q_hi = (int)(r >> 4);
+}
+
+// The k-th item of cluster c: block 0's producer takes it from the counter
+// and publishes it (fused_take); the other roles wait for it (fused_next).
+__device__ __forceinline__ int fused_take(const CrtFuse& fz, int c, int k) {
+    int item = (int)(atomicAdd(reinterpret_cast<unsigned int*>(fz.sched), 1u) + 1u);
+    if (item > fz.n_items || item < 0) item = fz.n_items;
+    *reinterpret_cast<volatile int*>(fz.sched + 1 + (int64_t)c * fz.stride + k) = item;
+    return item;
+}
+__device__ __forceinline__ int fused_next(const CrtFuse& fz, int c, int k, uint64_t limit_ns,
+                                          volatile int* abort, int* err) {
+    const volatile int* p = fz.sched + 1 + (int64_t)c * fz.stride + k;
+    int v = *p;
+    if (v != -1) return v;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        __nanosleep(64);
+        v = *p;
+        if (v != -1) return v;
+        if (abort && *abort) return fz.n_items;
+        if ((i & 15u) != 0) continue;
+        if (err && *reinterpret_cast<volatile int*>(err) == ALP_ERR_TIMEOUT) {
+            if (abort) *abort = 1;
+            return fz.n_items;
+        }
+        if (globaltimer() - t0 > limit_ns) {
+            set_device_error(err, ALP_ERR_TIMEOUT);
+            if (abort) *abort = 1;
+            return fz.n_items;
+        }
+    }
+}
+
+// C at row i, columns j..j+3 from the n byte planes of prm.G (one 32-bit load
+// per plane: crt_fused_load), as the standalone kernels form it (crt_rec.cuh),
+// stored with alpha and beta (crt_fused_finish).  Rows past M and columns
+// past N are skipped.
+__device__ __forceinline__ void crt_fused_load(const EmulGemmParams& prm, int64_t i, int64_t j,
+                                               uint32_t (&v)[16]) {
+    const bool in = i < prm.M && j < prm.N;
+    const uint8_t* g = reinterpret_cast<const uint8_t*>(prm.G) + i * prm.ldg + j;
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+        v[l] = (in && l < prm.s)
+                   ? __ldcg(reinterpret_cast<const unsigned int*>(g + (int64_t)l * prm.gplane))
+                   : 0u;
+}
+__device__ __forceinline__ void crt_fused_finish(const EmulGemmParams& prm, const CrtFuse& fz,
+                                                 int64_t i, int64_t j, const uint32_t (&v)[16]) {
+    if (i >= prm.M || j >= prm.N) return;
+    int64_t hi[4];
+    uint64_t lo[4];
+    crt_reconstruct4_n(v, prm.s, fz.cc, hi, lo);
+    const int ei = __ldg(fz.e + i) - 2 * fz.cc.k;
+    const bool full = j + 3 < prm.N;
+    double* ci = fz.C + i * fz.ldc + j;
+    double o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        // a column past N computes from the padding bytes and is not stored
+        const int fj = (full || j + u < prm.N) ? __ldg(fz.f + j + u) : 0;
+        const double w = i128_scaled_to_double_rn(hi[u], lo[u], ei + fj);
+        o[u] = fz.amode == 0 ? w : fz.amode == 1 ? -w : fz.alpha * w;
+    }
+    if (fz.bmode) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (full || j + u < prm.N) o[u] = __fma_rn(fz.beta, ci[u], o[u]);
+    }
+    if (full && (reinterpret_cast<uintptr_t>(ci) & 15) == 0) {
+        reinterpret_cast<double2*>(ci)[0] = make_double2(o[0], o[1]);
+        reinterpret_cast<double2*>(ci)[1] = make_double2(o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (full || j + u < prm.N) ci[u] = o[u];
+    }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_cta_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+                 : "memory");
+}
+// Waits until *cnt >= target, as mbar_wait_bounded waits for a phase (gives
+// up after limit_ns, at once when the block aborts or a timeout was recorded
+// anywhere; records ALP_ERR_TIMEOUT when its own limit runs out).  Sleeps
+// between polls: a tile's products take hundreds of microseconds.
+__device__ __forceinline__ bool count_wait_bounded(const uint32_t* cnt, uint32_t target,
+                                                   uint64_t limit_ns, volatile int* abort,
+                                                   int* err) {
+    if (ld_acquire_cta(cnt) >= target) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        __nanosleep(512);
+        if (ld_acquire_cta(cnt) >= target) return true;
+        if (*abort) return false;
+        if ((i & 15u) != 0) continue;
+        if (err && *reinterpret_cast<volatile int*>(err) == ALP_ERR_TIMEOUT) {
+            *abort = 1;
+            return false;
+        }
+        if (globaltimer() - t0 > limit_ns) {
+            set_device_error(err, ALP_ERR_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// The epilogue warps of the fused kernel (4..11): the drains, hand-backs and
+// residue bytes of every modulus as epilogue_role has them; after the last
+// modulus of a whole tile each warp counts it in tiles_ready (release).
+__device__ __forceinline__ void fused_epilogue(const EmulGemmParams& prm, const CrtFuse& fz,
+                                               uint32_t tmem_base, uint64_t* accf,
+                                               uint64_t* acce, uint32_t acce_remote,
+                                               uint64_t* agg, uint32_t* tiles_ready,
+                                               uint32_t rank, int warp, int lane, uint64_t tmo,
+                                               volatile int* abort_flag) {
+    const int quarter = warp & 3;                      // TMEM lanes this warp may access
+    const int half = (warp - kFusedEpiWarp0) >> 2;     // columns [128*half, 128*half + 128)
+    const int row = quarter * 32 + lane;
+    const int kblocks = (int)((prm.K + kTK - 1) / kTK), cpm = (kblocks + 15) / 16;
+    uint32_t acc[128];
+    int job = 0;
+    bool ok = true;
+    const int cid = (int)blockIdx.x / 2;
+    for (int k = 0; ok && k < fz.stride; ++k) {
+        const int it = fused_next(fz, cid, k, tmo, abort_flag, prm.err);
+        if (it >= fz.n_items) break;
+        int pid, qlo, qhi, m0, n0;
+        fused_item(prm, it, pid, qlo, qhi);
+        pair_tile_origin(prm, pid, rank, m0, n0);
+        const int gm = m0 + row;
+        for (int q = qlo; q <= qhi && ok; ++q) {
+#pragma unroll
+            for (int x = 0; x < 128; ++x) acc[x] = 0;
+            for (int c = 0; c < cpm; ++c, ++job) {
+                const uint32_t b = job & 1;
+                if (!mbar_wait_bounded(&accf[b], (job >> 1) & 1, tmo, abort_flag, prm.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr =
+                    tmem_base + ((uint32_t)(quarter * 32) << 16) + b * kTN + half * 128;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) tmem_drain32_cvt(taddr + cc * 32, &acc[cc * 32]);
+                tc_fence_before();
+                __syncwarp();
+                // the first epilogue warp forwards block 1's hand-backs
+                if (lane == 0)
+                    hand_back(acce, acce_remote, agg, b, job, warp - kFusedEpiWarp0 + 2, tmo,
+                              abort_flag, prm.err);
+            }
+            if (!ok) break;
+            // plane q receives x = (Q y_q) mod m_q, one byte per column
+            const uint32_t m = crt_modulus(q), magic = crt_magic(m), y = prm.crt_y[q];
+            uint8_t* g = reinterpret_cast<uint8_t*>(prm.G) + (int64_t)q * prm.gplane +
+                         (int64_t)gm * prm.ldg + n0 + half * 128;
+            if (gm < prm.M) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 16 * i + 4 * u;
+                        w[u] = crt_mod(crt_residue((int32_t)acc[c], m, magic) * y, m, magic) |
+                               crt_mod(crt_residue((int32_t)acc[c + 1], m, magic) * y, m, magic)
+                                   << 8 |
+                               crt_mod(crt_residue((int32_t)acc[c + 2], m, magic) * y, m, magic)
+                                   << 16 |
+                               crt_mod(crt_residue((int32_t)acc[c + 3], m, magic) * y, m, magic)
+                                   << 24;
+                    }
+                    *reinterpret_cast<uint4*>(g + 16 * i) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+        if (ok && it < prm.n_full) {
+            // every plane of this whole tile is stored: count it
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) red_release_cta_add(tiles_ready, 1u);
+        }
+    }
+}
+
+// The reconstruction warps (12..15, 128 threads): the whole tiles of this
+// cluster in order, each once all eight epilogue warps have counted it; four
+// columns per thread, 64 threads per row, two rows per step (64 steps for the
+// block's 128 rows), with the lines of the step after next asked of L2.
+__device__ __forceinline__ void fused_reconstruction(const EmulGemmParams& prm, const CrtFuse& fz,
+                                                     const uint32_t* tiles_ready, uint32_t rank,
+                                                     int warp, int lane, uint64_t tmo,
+                                                     volatile int* abort_flag) {
+    const int rt = (int)threadIdx.x - 32 * kFusedRecWarp0;   // 0..127
+    const int w = warp - kFusedRecWarp0;                     // 0..3
+    const int cid = (int)blockIdx.x / 2;
+    uint32_t k = 0;   // whole tiles of this cluster so far
+    for (int x = 0; x < fz.stride; ++x) {
+        const int it = fused_next(fz, cid, x, tmo, abort_flag, prm.err);
+        if (it >= fz.n_items) return;
+        if (it >= prm.n_full) continue;   // a tail piece: reconstructed after the launch
+        ++k;
+        if (!count_wait_bounded(tiles_ready, (uint32_t)(kEpiWarps) * k, tmo, abort_flag, prm.err))
+            return;
+        int m0, n0;
+        pair_tile_origin(prm, it, rank, m0, n0);
+        const int64_t j = (int64_t)n0 + 4 * (rt & 63);
+#pragma unroll 1
+        for (int step = 0; step < 64; ++step) {
+            if (step + 2 < 64 && lane < prm.s) {
+                const int64_t ip = (int64_t)m0 + 2 * (step + 2) + (w >> 1);
+                if (ip < prm.M)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(
+                        reinterpret_cast<const uint8_t*>(prm.G) + (int64_t)lane * prm.gplane +
+                        ip * prm.ldg + n0 + 128 * (w & 1)));
+            }
+            const int64_t i = (int64_t)m0 + 2 * step + (rt >> 6);
+            uint32_t v[16];
+            crt_fused_load(prm, i, j, v);
+            crt_fused_finish(prm, fz, i, j, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    emul_crt_fused_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                               const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm,
+                               CrtFuse fz) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
+    unsigned char* tiles = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPairStages * kPairStageBytes);
+    uint64_t* empty = full + kPairStages;
+    uint64_t* accf = empty + kPairStages;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint64_t* agg = done + 1;    // block 1: its epilogue warps' hand-backs, gathered
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(agg + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint32_t* tiles_ready = tmem_slot + 2;   // whole tiles stored, times kEpiWarps
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPairStages; ++i) {
+            mbar_init(&full[i], 1);    // block 0's producer; bytes of both blocks
+            mbar_init(&empty[i], 1);   // one multicast commit per round
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 2 * kEpiWarps);   // epilogue warps of both blocks
+            mbar_init(&agg[b], kEpiWarps);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        *tiles_ready = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync_all();   // both blocks' barriers and TMEM exist before any signal
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint64_t tmo = prm.timeout_ns;
+    const uint32_t full0 = cluster_addr(full, 0);   // block 0's full barriers
+    const int kblocks = (int)((prm.K + kTK - 1) / kTK), cpm = (kblocks + 15) / 16;
+    const int cid = (int)blockIdx.x / 2;
+
+    // each warpgroup changes its registers once, before its warps part: the
+    // epilogue's (1, 2) take what the others (0, 3) give back
+    const int wg = warp >> 2;
+    if (wg == 1 || wg == 2) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kFusedEpiRegs));
+        fused_epilogue(prm, fz, tmem_base, accf, &acce[0], leader ? 0u : cluster_addr(acce, 0),
+                       agg, tiles_ready, rank, warp, lane, tmo, abort_flag);
+    } else if (wg == 3) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFusedLowRegs));
+        fused_reconstruction(prm, fz, tiles_ready, rank, warp, lane, tmo, abort_flag);
+    } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kFusedLowRegs));
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both blocks) ----------------
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int k = 0; ok && k < fz.stride; ++k) {
+                const int item = leader ? fused_take(fz, cid, k)
+                                        : fused_next(fz, cid, k, tmo, abort_flag, prm.err);
+                if (item >= fz.n_items) break;
+                int pid, qlo, qhi, m0, n0;
+                fused_item(prm, item, pid, qlo, qhi);
+                pair_tile_origin(prm, pid, rank, m0, n0);
+                for (int q = qlo; q <= qhi && ok; ++q) {
+                    for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                        const uint32_t st = it % kPairStages, round = it / kPairStages;
+                        if (it >= (uint32_t)kPairStages &&
+                            !mbar_wait_bounded(&empty[st], (round - 1) & 1, tmo, abort_flag,
+                                               prm.err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (leader) mbar_arrive_expect_tx(&full[st], 2 * kPairStageBytes);
+                        // fault injection: block 0 issues no copy, the stage never fills
+                        if ((int64_t)it == prm.inject_skip_it && blockIdx.x == 0) continue;
+                        unsigned char* a = tiles + st * kPairStageBytes;
+                        tma_load_3d_pair(a, &tmA, full0 + st * 8, kb * kTK, m0, q);
+                        tma_load_3d_pair(a + kATile, &tmB, full0 + st * 8, kb * kTK,
+                                         n0 + (int)rank * (kTN / 2), q);
+                    }
+                }
+            }
+            // as in emul_gemm_pair_kernel: every issued stage consumed and
+            // released before this block leaves (cut to kDrainNs after an abort)
+            const bool aborted =
+                *abort_flag ||
+                (prm.err && *reinterpret_cast<volatile int*>(prm.err) == ALP_ERR_TIMEOUT);
+            const uint64_t drain = aborted && tmo > kDrainNs ? kDrainNs : tmo;
+            for (uint32_t j = it > (uint32_t)kPairStages ? it - kPairStages : 0; j < it; ++j)
+                if (!mbar_wait_bounded(&empty[j % kPairStages], (j / kPairStages) & 1, drain,
+                                       nullptr, prm.err, false) &&
+                    aborted)
+                    break;
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (block 0) ----------------
+            const uint32_t idesc = idesc_bf16_f32(2 * kTM, kTN);
+            uint32_t it = 0;
+            int job = 0;
+            bool ok = true;
+            for (int k = 0; ok && k < fz.stride; ++k) {
+                const int item = fused_next(fz, cid, k, tmo, abort_flag, prm.err);
+                if (item >= fz.n_items) break;
+                int pid, qlo, qhi;
+                fused_item(prm, item, pid, qlo, qhi);
+                for (int q = qlo; q <= qhi && ok; ++q) {
+                    for (int c = 0; c < cpm && ok; ++c, ++job) {
+                        const uint32_t b = job & 1;
+                        if (job >= 2 && !mbar_wait_bounded(&acce[b], ((job >> 1) - 1) & 1, tmo,
+                                                           abort_flag, prm.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + b * kTN;
+                        uint32_t accumulate = 0;
+                        const int ke = 16 * c + 16 < kblocks ? 16 * c + 16 : kblocks;
+                        for (int kb = 16 * c; kb < ke; ++kb, ++it) {
+                            const uint32_t st = it % kPairStages, round = it / kPairStages;
+                            if (!mbar_wait_bounded(&full[st], round & 1, tmo, abort_flag,
+                                                   prm.err)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a_addr = smem_u32(tiles + st * kPairStageBytes);
+                            const uint64_t adesc = sw128_kmajor_desc(a_addr);
+                            const uint64_t bdesc = sw128_kmajor_desc(a_addr + kATile);
+#pragma unroll
+                            for (int kk = 0; kk < kTK / 16; ++kk) {
+                                umma_bf16_pair(d_tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc,
+                                               accumulate);
+                                accumulate = 1;
+                            }
+                            umma_commit_pair(&empty[st], 3);
+                        }
+                        if (!ok) break;
+                        umma_commit_pair(&accf[b], 3);
+                    }
+                }
+            }
+            // as in emul_gemm_pair_kernel: all MMAs complete and both blocks'
+            // hand-backs of the last two chunks arrived
+            umma_commit_pair(done, 1);
+            mbar_wait_bounded(done, 0, tmo, nullptr, prm.err, false);
+            for (int j = job > 2 ? job - 2 : 0; j < job && ok; ++j)
+                mbar_wait_bounded(&acce[j & 1], (j >> 1) & 1, tmo, nullptr, prm.err, false);
+        }
+    }
+    }   // warpgroup 0; warps 2 and 3 have no role
+    tc_fence_before();
+    __syncwarp();
+    cluster_sync_all();   // no block leaves while its peer's MMAs or signals may reach it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, kTmemCols);
+    }
+}
+
+// The tail tiles of a fused launch (pair tiles n_full..): 16 blocks of 256
+// threads per tile, block b holding rows 16 (b % 8) .. + 16 of the tile's
+// half (b / 8) % 2, four rows per step.
+__global__ void __launch_bounds__(256) crt_tail_recombine_kernel(EmulGemmParams prm, CrtFuse fz) {
+    const int b = (int)blockIdx.x;
+    const int strip = b & 7, r = (b >> 3) & 1, pid = prm.n_full + (b >> 4);
+    int m0, n0;
+    pair_tile_origin(prm, pid, (uint32_t)r, m0, n0);
+    const int64_t j = (int64_t)n0 + 4 * (threadIdx.x & 63);
+#pragma unroll 1
+    for (int step = 0; step < 4; ++step) {
+        const int64_t i = (int64_t)m0 + 16 * strip + 4 * step + (threadIdx.x >> 6);
+        uint32_t v[16];
+        crt_fused_load(prm, i, j, v);
+        crt_fused_finish(prm, fz, i, j, v);
     }
 }
 
@@ -787,6 +1297,140 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     lc.numAttrs = 1;
     e = cudaLaunchKernelEx(&lc, emul_gemm_pair_kernel, ta, tb, p);
     return cuda_status(e);
+}
+
+// Clusters of the fused kernel that are resident at once (its persistent
+// grid); half the SMs if the query fails.
+static int fused_active_clusters() {
+    static int c = 0;
+    if (c == 0) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(2 * device_sm_count()));
+        lc.blockDim = dim3(kFusedThreads);
+        lc.dynamicSmemBytes = kFusedSmemBytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, emul_crt_fused_pair_kernel, &lc) != cudaSuccess ||
+            nc < 1) {
+            (void)cudaGetLastError();
+            nc = device_sm_count() / 2;
+        }
+        c = nc > 0 ? nc : 1;
+    }
+    return c;
+}
+
+size_t emul_crt_sched_bytes(int64_t M, int64_t N) {
+    if (M <= 0 || N <= 0) return 0;
+    const int64_t pair_tiles = ((M + 2 * kTM - 1) / (2 * kTM)) * ((N + kTN - 1) / kTN);
+    return (size_t)4 * (1 + (size_t)kMaxFusedClusters * (size_t)(pair_tiles + 7 * kMaxFusedClusters + 1));
+}
+
+alp_status emul_crt_products_recombine(int64_t M, int64_t N, int64_t K, int n,
+                                       const __nv_bfloat16* da, const __nv_bfloat16* db,
+                                       int64_t kpad, uint8_t* G, int64_t ldg, const int32_t* e,
+                                       const int32_t* f, int k, double alpha, double beta,
+                                       double* C, int64_t ldc, int* sched, size_t sched_bytes,
+                                       cudaStream_t stream, int group_m, int cluster, int fuse) {
+    if (n < kCrtMinModuli || n > kCrtMaxModuli || K > kCrtMaxK || k < 1 || k > 60)
+        return ALP_ERR_UNSUPPORTED;
+    const int arr = (cluster == kEmulSingle || cluster == kEmulPair) ? cluster : emul_cluster();
+    const bool fused = fuse > 0 || (fuse < 0 && emul_crt_fuse_on());
+    if (arr != kEmulPair || !fused || !sched || sched_bytes < emul_crt_sched_bytes(M, N)) {
+        alp_status st = emul_slice_gemm(M, N, K, n, da, db, kpad, reinterpret_cast<int32_t*>(G),
+                                        ldg, stream, group_m, arr, kDigitBits, false, true);
+        if (st != ALP_OK) return st;
+        return launch_recombine_crt(n, k, recombine_grid(M, N), stream, G, M * ldg, ldg, e, f, M,
+                                    N, alpha, beta, C, ldc);
+    }
+    if ((K + kTK - 1) / kTK > 1023) return ALP_ERR_UNSUPPORTED;
+    CUtensorMap ta, tb;
+    alp_status st = make_tmap_3d_bf16(&ta, da, (uint64_t)kpad, (uint64_t)M, (uint64_t)n, kTK, kTM);
+    if (st != ALP_OK) return st;
+    st = make_tmap_3d_bf16(&tb, db, (uint64_t)kpad, (uint64_t)N, (uint64_t)n, kTK, kTN / 2);
+    if (st != ALP_OK) return st;
+    EmulGemmParams p;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.s = n;
+    p.digit_bits = kDigitBits;
+    p.trim = 0;
+    p.crt = 1;
+    for (int l = 0; l < kCrtMaxModuli; ++l) p.crt_y[l] = l < n ? crt_weight(n, l) : 0;
+    p.G = reinterpret_cast<int32_t*>(G);
+    p.ldg = ldg;
+    p.gplane = M * ldg;
+    const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
+    const int64_t pair_tiles = ((tiles_m + 1) / 2) * tiles_n;
+    if (pair_tiles * 16 > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
+    p.tiles_m = (int)tiles_m;
+    p.tiles_n = (int)tiles_n;
+    p.group_m = group_m > 0 ? group_m : emul_group_m(true);
+    p.timeout_ns = wait_timeout_ns();
+    p.err = device_error_word();
+    p.inject_skip_it = inject_skip_kt();
+    cudaError_t ce = cudaFuncSetAttribute(emul_crt_fused_pair_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kFusedSmemBytes);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    const int P = fused_active_clusters() < kMaxFusedClusters ? fused_active_clusters()
+                                                               : kMaxFusedClusters;
+    p.n_full = (int)pair_tiles;
+    p.pieces = 1;
+    p.t_ranges = (uint64_t)(n - 1) << 4;
+    if (emul_tail_split_on()) {   // whole tiles fill the waves of P clusters
+        const TailSplit ts = tail_split((int)pair_tiles, n, P, false, true);
+        p.n_full = ts.n_full;
+        p.pieces = ts.pieces;
+        p.t_ranges = 0;
+        for (int i = 0; i < ts.pieces; ++i)
+            p.t_ranges |= (uint64_t)((ts.t_lo[i] - 2) | (ts.t_hi[i] - 2) << 4) << (8 * i);
+    }
+    const int64_t items = p.n_full + (pair_tiles - p.n_full) * p.pieces;
+    CrtFuse fz;
+    fz.e = e;
+    fz.f = f;
+    fz.alpha = alpha;
+    fz.beta = beta;
+    fz.C = C;
+    fz.ldc = ldc;
+    fz.amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
+    fz.bmode = beta != 0.0 ? 1 : 0;
+    fz.n_items = (int)items;
+    fz.sched = sched;
+    fz.stride = (int)items + 1;
+    fz.cc = crt_rec_consts(n, k);
+    const int64_t clusters = items < P ? items : P;
+    // the counter and every cluster's list start at all ones (-1: not yet taken)
+    ce = cudaMemsetAsync(sched, 0xff, (size_t)4 * (1 + (size_t)clusters * fz.stride), stream);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(2 * clusters));
+    lc.blockDim = dim3(kFusedThreads);
+    lc.dynamicSmemBytes = kFusedSmemBytes;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    ce = cudaLaunchKernelEx(&lc, emul_crt_fused_pair_kernel, ta, tb, p, fz);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (p.n_full < pair_tiles) {
+        crt_tail_recombine_kernel<<<(unsigned)((pair_tiles - p.n_full) * 16), 256, 0, stream>>>(
+            p, fz);
+        ce = cudaGetLastError();
+    }
+    return cuda_status(ce);
 }
 
 }  // namespace alp

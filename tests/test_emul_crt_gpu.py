@@ -379,6 +379,79 @@ def test_crt_gemm_call_matches_its_stages(alp, orc, cfg, M, N, K, n):
     assert np.array_equal(got, dC.cpu().numpy())
 
 
+@pytest.mark.parametrize("M,N,K,n,alpha,beta", [
+    (2560, 2560, 300, 15, 1.0, 0.0),      # one whole tile per CTA pair, then a tail piece
+    (4096, 4100, 200, 16, -1.0, 0.5),     # several whole tiles per pair, ragged columns
+    (3000, 1500, 1100, 13, 0.75, -2.0),   # ragged rows, chunks of two lengths
+    (300, 200, 700, 4, 1.0, 1.0),         # every tile in the tail
+    (256 * 76, 256, 64, 14, 1.0, 0.0)])   # one tile per pair, no tail when 76 pairs fit
+def test_crt_products_recombine_matches_the_two_stages(alp, orc, M, N, K, n, alpha, beta):
+    """alp_emul_products_recombine_crt (the tensor-core stage with the
+    reconstruction of each tile in its epilogue, the persistent launch and
+    the tail tiles' launch) writes the same byte planes and the same C as
+    alp_emul_slice_products followed by alp_emul_recombine_crt, element for
+    element, and C matches the oracle on rows across tile edges."""
+    import torch
+    A, B, C = inputs.gemm_operands(6100 + M + N + n, M, N, K, kind="scaled", phi=2)
+    kpad = (K + 63) // 64 * 64
+    ldg = (N + 255) // 256 * 256
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    de = torch.empty(M, dtype=torch.int32, device="cuda")
+    df = torch.empty(N, dtype=torch.int32, device="cuda")
+    alp.alp_emul_exponents(M, K, dA, K, 0, de)
+    alp.alp_emul_exponents(N, K, dB, N, 1, df)
+    da = torch.empty((n, M, kpad), dtype=torch.bfloat16, device="cuda")
+    db = torch.empty((n, N, kpad), dtype=torch.bfloat16, device="cuda")
+    alp.alp_emul_split(M, K, dA, K, 0, de, n, CRT, da, kpad)
+    alp.alp_emul_split(N, K, dB, N, 1, df, n, CRT, db, kpad)
+    G1 = torch.full((n, M, ldg), 255, dtype=torch.uint8, device="cuda")
+    C1 = torch.from_numpy(C.copy()).cuda()
+    wsb = alp.alp_emul_products_recombine_crt_workspace(M, N)
+    work = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    alp.alp_emul_products_recombine_crt(M, N, K, n, da, db, kpad, G1, ldg, de, df, alpha, beta,
+                                        C1, N, work, wsb)
+    G2 = torch.full((n, M, ldg), 255, dtype=torch.uint8, device="cuda")
+    C2 = torch.from_numpy(C.copy()).cuda()
+    alp.alp_emul_slice_products(M, N, K, n, CRT, da, db, kpad, G2, ldg)
+    alp.alp_emul_recombine_crt(M, N, K, n, G2, ldg, de, df, alpha, beta, C2, N)
+    torch.cuda.synchronize()
+    assert alp.alp_get_device_error() == alp.ALP_OK
+    assert torch.equal(G1[:, :, :N], G2[:, :, :N])
+    got = C1.cpu().numpy()
+    assert np.array_equal(got, C2.cpu().numpy())
+    rows = np.unique(np.clip([0, 127, 128, 255, 256, 511, 512, M // 2, M - 1], 0, M - 1))
+    ref, rc = orc.crt_gemm(alpha, A, B, beta, C, crt_k(K, n), rows=rows)
+    assert rc == 0 and np.array_equal(got[rows], ref)
+
+
+def test_crt_products_recombine_argument_errors(alp):
+    """The fused stage rejects what the two stages reject, and K < 1, and a
+    missing or short schedule workspace, before any launch."""
+    import torch
+    # every buffer holds what a 64 x 300 x 128 call with 16 moduli would touch
+    d = torch.zeros(1 << 18, dtype=torch.float64, device="cuda")
+    e = torch.zeros(512, dtype=torch.int32, device="cuda")
+    wsb = alp.alp_emul_products_recombine_crt_workspace(64, 300)
+    assert wsb > 0 and alp.alp_emul_products_recombine_crt_workspace(0, 64) == 0
+    w = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    bad = [(64, 64, 0, 15, 64, 256), (64, 64, 64, 3, 64, 256), (64, 64, 64, 17, 64, 256),
+           (64, 64, 64, 15, 32, 256), (64, 64, 100, 15, 100, 256), (64, 64, 64, 15, 64, 128),
+           (64, 300, 64, 15, 64, 256)]
+    for M, N, K, n, kpad, ldg in bad:
+        st = alp.alp_emul_products_recombine_crt(M, N, K, n, d, d, kpad, d, ldg, e, e, 1.0, 0.0,
+                                                 d, max(N, 1), w, wsb, raise_on_error=False)
+        assert st == alp.ALP_ERR_INVALID_ARG, (M, N, K, n, kpad, ldg)
+    st = alp.alp_emul_products_recombine_crt(64, 64, 64, 15, d, d, 64, None, 256, e, e, 1.0, 0.0,
+                                             d, 64, w, wsb, raise_on_error=False)
+    assert st == alp.ALP_ERR_INVALID_ARG
+    need = alp.alp_emul_products_recombine_crt_workspace(64, 64)
+    for work, nb in ((None, need), (w, need - 4)):
+        st = alp.alp_emul_products_recombine_crt(64, 64, 64, 15, d, d, 64, d, 256, e, e, 1.0, 0.0,
+                                                 d, 64, work, nb, raise_on_error=False)
+        assert st == alp.ALP_ERR_WORKSPACE
+    assert alp.alp_get_device_error() == alp.ALP_OK
+
+
 @pytest.mark.parametrize("n", list(range(4, 17)))
 def test_crt_recombine_rounding(alp, n):
     """alp_emul_recombine_crt on crafted residues: P anywhere in [-L, L],
