@@ -194,23 +194,30 @@ __global__ void __launch_bounds__(THREADS, MINB) scan_split_rows4_kernel(
         const double* xr = X + r * ldx;
         const bool xvec = (reinterpret_cast<uintptr_t>(xr) & 15) == 0;
         uint64_t mx = 0;
+        // four strides of the row per iteration, all their loads issued
+        // before the first comparison (the scan is bound by load latency)
 #pragma unroll 1
-        for (int64_t k = 4 * (int64_t)threadIdx.x; k < K; k += 4 * THREADS) {
-            uint64_t b[4];
-            if (xvec && k + 3 < K) {
-                const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(xr + k));
-                const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(xr + k + 2));
-                b[0] = ((uint64_t)p0.y << 32) | p0.x;
-                b[1] = ((uint64_t)p0.w << 32) | p0.z;
-                b[2] = ((uint64_t)p1.y << 32) | p1.x;
-                b[3] = ((uint64_t)p1.w << 32) | p1.z;
-            } else {
+        for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < K; k0 += 16 * THREADS) {
+            uint64_t b[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    b[u] = k + u < K ? (uint64_t)__double_as_longlong(__ldg(xr + k + u)) : 0ull;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t k = k0 + (int64_t)q * 4 * THREADS;
+                if (xvec && k + 3 < K) {
+                    const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(xr + k));
+                    const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(xr + k + 2));
+                    b[4 * q] = ((uint64_t)p0.y << 32) | p0.x;
+                    b[4 * q + 1] = ((uint64_t)p0.w << 32) | p0.z;
+                    b[4 * q + 2] = ((uint64_t)p1.y << 32) | p1.x;
+                    b[4 * q + 3] = ((uint64_t)p1.w << 32) | p1.z;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        b[4 * q + u] =
+                            k + u < K ? (uint64_t)__double_as_longlong(__ldg(xr + k + u)) : 0ull;
+                }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const uint64_t a = b[u] & 0x7FFFFFFFFFFFFFFFull;
                 mx = a > mx ? a : mx;
             }
@@ -230,9 +237,9 @@ __global__ void __launch_bounds__(THREADS, MINB) scan_split_rows4_kernel(
             e[r] = er;
             if (mx >= 0x7FF0000000000000ull) set_device_error(err, ALP_ERR_UNSUPPORTED);
         }
-#pragma unroll 1
-        for (int64_t k = 4 * (int64_t)threadIdx.x; k < kpad; k += 4 * THREADS) {
-            double a[4];
+        // the split: the next stride's four values loaded before this
+        // stride's residues are formed (the row comes back from L2)
+        auto load4 = [&](int64_t k, double (&a)[4]) {
             if (xvec && k + 3 < K) {
                 const double2 p0 = __ldg(reinterpret_cast<const double2*>(xr + k));
                 const double2 p1 = __ldg(reinterpret_cast<const double2*>(xr + k + 2));
@@ -244,6 +251,13 @@ __global__ void __launch_bounds__(THREADS, MINB) scan_split_rows4_kernel(
 #pragma unroll
                 for (int u = 0; u < 4; ++u) a[u] = k + u < K ? __ldg(xr + k + u) : 0.0;
             }
+        };
+        double an[4];
+        if (4 * (int64_t)threadIdx.x < kpad) load4(4 * (int64_t)threadIdx.x, an);
+#pragma unroll 1
+        for (int64_t k = 4 * (int64_t)threadIdx.x; k < kpad; k += 4 * THREADS) {
+            const double a[4] = {an[0], an[1], an[2], an[3]};
+            if (k + 4 * THREADS < kpad) load4(k + 4 * THREADS, an);
             uint32_t w01[S];
             {
                 int d0[S], d1[S];
