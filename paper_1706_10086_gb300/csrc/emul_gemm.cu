@@ -14,7 +14,9 @@
 //               thread, committing each stage back to the producer and each
 //               finished chunk to the epilogue;
 //   warps 2-9   drain a finished chunk from TMEM (tcgen05.ld) while the other
-//               accumulator fills, and add it exactly into int32 registers.
+//               accumulator fills, and add it exactly into int32 registers
+//               (the CTA-pair kernels: warps 4-11 of 16, with more registers
+//               each; kPairThreads).
 //
 // Jobs (build_jobs): the digit schemes multiply the digit pairs (p, q) of
 // each group t = p + q <= s + 1 (groups ascending, p ascending); the modular
@@ -226,9 +228,12 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
                                               int njobs, uint32_t tmem_base, uint64_t* accf,
                                               uint64_t* acce, uint32_t acce_remote, uint64_t* agg,
                                               int m0, int n0, int warp, int lane, uint64_t tmo,
-                                              volatile int* abort_flag) {
-    const int quarter = warp & 3;          // TMEM lanes this warp may access
-    const int half = (warp - 2) >> 2;      // columns [128*half, 128*half + 128)
+                                              volatile int* abort_flag, int ew) {
+    // ew: this warp's index among the eight epilogue warps (the first one
+    // forwards block 1's hand-backs); warp: its index in the block, whose
+    // value modulo 4 fixes the TMEM lanes it may access
+    const int quarter = warp & 3;
+    const int half = ew >> 2;              // columns [128*half, 128*half + 128)
     const int row = quarter * 32 + lane;
     const int gm = m0 + row;
     uint32_t acc[128];
@@ -245,7 +250,7 @@ __device__ __forceinline__ void epilogue_role(const EmulGemmParams& prm, const u
         for (int c = 0; c < 4; ++c) tmem_drain32_cvt(taddr + c * 32, &acc[c * 32]);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) hand_back(acce, acce_remote, agg, b, job, warp, tmo, abort_flag, prm.err);
+        if (lane == 0) hand_back(acce, acce_remote, agg, b, job, ew + 2, tmo, abort_flag, prm.err);
         const uint32_t jd = jobs[job];
         if (job_last(jd) && prm.crt) {
             // modular scheme: plane l of modulus m_l receives x = (Q y_l) mod
@@ -434,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0], 0u, nullptr, m0, n0, warp,
-                      lane, tmo, abort_flag);
+                      lane, tmo, abort_flag, warp - 2);
     }
     tc_fence_before();
     __syncwarp();
@@ -456,6 +461,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 // stages and chunks in both blocks by multicast commits; block 1's epilogue
 // hands accumulators back on block 0's "acce" barriers.
 constexpr int kPairStages = 6;
+// Sixteen warps: 0 the TMA producer, 1 the MMA issuer, 4-11 the epilogue;
+// the epilogue's warpgroups take 176 registers per thread from the others'
+// (setmaxnreg: 2 x 128 x 176 + 2 x 128 x 80 = 65536, the launch's 512 x 128),
+// so that its 128 running sums per thread fit without spilling.
+constexpr int kPairThreads = 512;
+constexpr int kPairEpiRegs = 176, kPairLowRegs = 80;
+static_assert(2 * 128 * kPairEpiRegs + 2 * 128 * kPairLowRegs == kPairThreads * 128,
+              "register split of the CTA-pair kernel");
 // Limit of the pair producer's final waits once the launch has aborted (2 ms).
 constexpr uint64_t kDrainNs = 2000000ull;
 constexpr uint32_t kPairBTile = kBTile / 2;
@@ -479,7 +492,7 @@ __device__ __forceinline__ void pair_tile_origin(const EmulGemmParams& prm, int 
     n0 = (local / gsz) * kTN;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kPairThreads, 1)
     emul_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                           const __grid_constant__ CUtensorMap tmB, EmulGemmParams prm) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -543,7 +556,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const uint64_t tmo = prm.timeout_ns;
     const uint32_t full0 = cluster_addr(full, 0);   // block 0's full barriers
-
+    // each warpgroup changes its registers once, before its warps part: the
+    // epilogue's (warps 4-11) take what warps 0-3 and 12-15 give back
+    const int wg = warp >> 2;
+    if (wg == 1 || wg == 2) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPairEpiRegs));
+        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0],
+                      leader ? 0u : cluster_addr(acce, 0), agg, m0, n0, warp, lane, tmo,
+                      abort_flag, warp - 4);
+    } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPairLowRegs));
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer (both blocks) ----------------
@@ -632,11 +654,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int job = njobs > 2 ? njobs - 2 : 0; job < njobs && ok; ++job)
                 mbar_wait_bounded(&acce[job & 1], (job >> 1) & 1, tmo, nullptr, prm.err, false);
         }
-    } else {
-        epilogue_role(prm, jobs, njobs, tmem_base, accf, &acce[0],
-                      leader ? 0u : cluster_addr(acce, 0), agg, m0, n0, warp, lane, tmo,
-                      abort_flag);
     }
+    }   // warps 2, 3 and 12-15 have no role
     tc_fence_before();
     __syncwarp();
     cluster_sync_all();   // no block leaves while its peer's MMAs or signals may reach it
@@ -1285,7 +1304,7 @@ alp_status emul_slice_gemm(int64_t M, int64_t N, int64_t K, int s, const __nv_bf
     if (grid > 0x7fffffff) return ALP_ERR_UNSUPPORTED;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)grid);
-    lc.blockDim = dim3(kThreads);
+    lc.blockDim = dim3(kPairThreads);
     lc.dynamicSmemBytes = smem_bytes;
     lc.stream = stream;
     cudaLaunchAttribute attr[1];
