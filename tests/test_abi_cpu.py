@@ -230,6 +230,28 @@ def test_emul_tail_split_modular_scheme(alp):
 CRT_MODULI = [256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193]
 
 
+
+def test_fused_schedule_workspace_covers_every_launch(alp):
+    """alp_emul_products_recombine_crt_workspace (and the GEMM's workspace)
+    holds the fused launch's schedule for any number of resident CTA pairs up
+    to 128: the counter and, for each pair, one entry per item plus the end
+    marker, with the items the tail split makes (whole tiles, then every
+    tail tile's pieces)."""
+    CRT = alp.ALP_SLICE_BF16_CRT
+    for M, N in [(1, 1), (256, 256), (300, 200), (2560, 2560), (8192, 8192), (4096, 4100),
+                 (19456, 256), (65536, 300)]:
+        pair_tiles = ((M + 255) // 256) * ((N + 255) // 256)
+        need_max = 0
+        for P in (1, 2, 7, 64, 74, 76, 100, 128):
+            for n in (4, 13, 15, 16):
+                n_full, pieces = alp.alp_emul_tail_split(pair_tiles, n, CRT, P)
+                items = n_full + (pair_tiles - n_full) * len(pieces)
+                clusters = min(items, P)
+                need_max = max(need_max, 4 * (1 + clusters * (items + 1)))
+        ws = alp.alp_emul_products_recombine_crt_workspace(M, N)
+        assert ws >= need_max, (M, N, ws, need_max)
+        assert alp.alp_gemm_f64_emul_workspace(M, N, 64, 15, CRT) >= ws
+
 def test_crt_moduli_and_bits_rule(alp):
     """The documented moduli are pairwise coprime, and alp_emul_crt_bits is the
     largest k <= 60 with K 2^(2k+1) <= Mn (1 - 2^-18), Mn their product (so
