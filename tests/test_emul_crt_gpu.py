@@ -424,6 +424,40 @@ def test_crt_products_recombine_matches_the_two_stages(alp, orc, M, N, K, n, alp
     assert rc == 0 and np.array_equal(got[rows], ref)
 
 
+_FUSE_CHILD = """
+import sys, numpy as np, torch
+from paper_1706_10086_gb300 import alp, inputs
+M, N, K, n = 1300, 900, 700, 15
+A, B, C = inputs.gemm_operands(6400, M, N, K, kind="scaled", phi=3)
+dA, dB, dC = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C))
+ws = alp.alp_gemm_f64_emul_workspace(M, N, K, n, alp.ALP_SLICE_BF16_CRT)
+work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+alp.alp_gemm_f64_emul(M, N, K, -0.5, dA, K, dB, N, 2.0, dC, N, n, alp.ALP_SLICE_BF16_CRT, work, ws)
+torch.cuda.synchronize()
+assert alp.alp_get_device_error() == alp.ALP_OK
+np.save(sys.argv[1], dC.cpu().numpy())
+"""
+
+
+def test_crt_fuse_switch_gives_the_same_result(tmp_path):
+    """alp_gemm_f64_emul's modular scheme with ALP_EMUL_CRT_FUSE=0 (the
+    products, then the reconstruction kernel) and with the default fused
+    launch write the same C, element for element (child processes: the switch
+    is read once per process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for fuse in ("1", "0"):
+        path = str(tmp_path / f"c_{fuse}.npy")
+        env = dict(os.environ, ALP_EMUL_CRT_FUSE=fuse)
+        subprocess.run([sys.executable, "-c", _FUSE_CHILD, path], cwd=root, env=env,
+                       check=True, timeout=600)
+        out[fuse] = np.load(path)
+    assert np.array_equal(out["1"], out["0"])
+
+
 def test_crt_products_recombine_argument_errors(alp):
     """The fused stage rejects what the two stages reject, and K < 1, and a
     missing or short schedule workspace, before any launch."""
